@@ -1,0 +1,202 @@
+"""Seeded synthetic workloads for the SCSF eigenvalue-dataset pipeline.
+
+This module is shared by the CPU oracle, the tests and the benchmark. It only
+*defines the inputs* (coefficient fields sampled on the grid); it holds none of
+the method's arithmetic (no discretisation, no DFT, no sort, no eigensolver).
+
+The paper's datasets (App. D.2: generalized Poisson -div(K grad h) = lambda h
+with K from a Gaussian random field; Helmholtz-type operators) are not
+available, so smooth random fields of the same kind stand in for them:
+
+    f(x, y) = sum_{p<M} sum_{q<M} xi_pq cos(p pi x) cos(q pi y),  xi_pq ~ N(0, 1)
+
+drawn p-major from ``numpy.random.default_rng(seed)`` one operator after the
+other, with the (0, 0) mode included and no decay weighting.
+
+* div-a-grad workloads (generalized Poisson, App. D.2 item 1):
+  a = exp(0.5 f / M) with M = 8. The mode sum is normalised by 1/M: the
+  plain sum of 64 unit-variance modes has a standard deviation of about 4,
+  which makes a span 10^5-10^6 (far outside the moderate-contrast random
+  fields of the paper's Poisson data); with the 1/M factor f/M has a standard
+  deviation of about 0.5 and a spans a factor of about 4-6.
+* Laplacian-plus-potential workloads (stand-in for the Helmholtz family,
+  App. D.2 item 3): V = 10 f with M = 12.
+
+Grid convention (Sec. 2.1, row-major node order): the unit square holds an
+n x n interior grid with spacing h = 1/(n+1); node (i, j) sits at
+x = (i+1) h, y = (j+1) h and has linear index I = i*n + j (j fastest).
+Face coefficients are the field evaluated at face midpoints:
+
+* ``ax[f, j]`` = a((f + 1/2) h, (j+1) h), f = 0..n   (the x-face between
+  node (f-1, j) and node (f, j); f = 0 and f = n touch the boundary)
+* ``ay[i, g]`` = a((i+1) h, (g + 1/2) h), g = 0..n
+
+The sort's parameter matrix P (Alg. 2) is the field at the n x n nodes.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+__all__ = [
+    "DivAGradOp", "LapPlusVOp", "mode_coefficients", "cosine_field",
+    "div_a_grad_chain", "lap_plus_v_chain", "constant_div_a_grad",
+    "separable_div_a_grad", "gaussian_block", "batched_chain_specs",
+    "WORKLOADS",
+]
+
+
+@dataclass
+class DivAGradOp:
+    """-div(a grad u) on the n x n interior grid, Dirichlet boundary."""
+    n: int
+    ax: np.ndarray  # [n+1, n] float64
+    ay: np.ndarray  # [n, n+1] float64
+    P: np.ndarray   # [n, n]   float64, a at the nodes (sort input)
+
+    @property
+    def N(self) -> int:
+        return self.n * self.n
+
+
+@dataclass
+class LapPlusVOp:
+    """-Lap u + V u on the n x n interior grid, Dirichlet boundary."""
+    n: int
+    V: np.ndarray   # [n, n] float64, V at the nodes (also the sort input)
+
+    @property
+    def N(self) -> int:
+        return self.n * self.n
+
+    @property
+    def P(self) -> np.ndarray:
+        return self.V
+
+
+def mode_coefficients(rng: np.random.Generator, M: int) -> np.ndarray:
+    """xi[p, q] ~ N(0, 1), drawn p-major (q fastest)."""
+    return rng.standard_normal((M, M))
+
+
+def cosine_field(xi: np.ndarray, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """f(x_r, y_s) = sum_pq xi_pq cos(p pi x_r) cos(q pi y_s) on a tensor grid."""
+    M = xi.shape[0]
+    cx = np.cos(np.pi * np.outer(x, np.arange(M)))  # [len(x), M]
+    cy = np.cos(np.pi * np.outer(y, np.arange(M)))  # [len(y), M]
+    return cx @ xi @ cy.T
+
+
+def _grids(n: int):
+    h = 1.0 / (n + 1)
+    nodes = (np.arange(n) + 1.0) * h
+    faces = (np.arange(n + 1) + 0.5) * h
+    return nodes, faces
+
+
+def _div_a_grad_from_xi(n: int, xi: np.ndarray, scale: float | None = None) -> DivAGradOp:
+    """a = exp(scale * f); the default scale is 0.5 / M (normalised mode sum)."""
+    if scale is None:
+        scale = 0.5 / xi.shape[0]
+    nodes, faces = _grids(n)
+    ax = np.exp(scale * cosine_field(xi, faces, nodes))
+    ay = np.exp(scale * cosine_field(xi, nodes, faces))
+    P = np.exp(scale * cosine_field(xi, nodes, nodes))
+    return DivAGradOp(n, np.ascontiguousarray(ax), np.ascontiguousarray(ay),
+                      np.ascontiguousarray(P))
+
+
+def div_a_grad_chain(n: int, n_ops: int, seed: int, M: int = 8) -> List[DivAGradOp]:
+    """n_ops operators -div(a grad u), a = exp(0.5 f / M), f with M x M modes."""
+    rng = np.random.default_rng(seed)
+    return [_div_a_grad_from_xi(n, mode_coefficients(rng, M)) for _ in range(n_ops)]
+
+
+def lap_plus_v_chain(n: int, n_ops: int, seed: int, M: int = 12,
+                     amplitude: float = 10.0) -> List[LapPlusVOp]:
+    """n_ops operators -Lap u + V u, V = amplitude * f, f with M x M modes."""
+    rng = np.random.default_rng(seed)
+    nodes, _ = _grids(n)
+    out = []
+    for _ in range(n_ops):
+        xi = mode_coefficients(rng, M)
+        out.append(LapPlusVOp(n, np.ascontiguousarray(amplitude * cosine_field(xi, nodes, nodes))))
+    return out
+
+
+def constant_div_a_grad(n: int, value: float = 1.0) -> DivAGradOp:
+    """a == value everywhere (the Dirichlet Laplacian when value == 1)."""
+    return DivAGradOp(n, np.full((n + 1, n), value), np.full((n, n + 1), value),
+                      np.full((n, n), value))
+
+
+def separable_div_a_grad(n: int, seed: int, M: int = 8) -> DivAGradOp:
+    """a = a(x) only: a = exp(0.5 g(x) / M), g = sum_p xi_p cos(p pi x)."""
+    rng = np.random.default_rng(seed)
+    xi = rng.standard_normal(M)
+    nodes, faces = _grids(n)
+    gx_faces = np.cos(np.pi * np.outer(faces, np.arange(M))) @ xi
+    gx_nodes = np.cos(np.pi * np.outer(nodes, np.arange(M))) @ xi
+    s = 0.5 / M
+    ax = np.repeat(np.exp(s * gx_faces)[:, None], n, axis=1)
+    ay = np.repeat(np.exp(s * gx_nodes)[:, None], n + 1, axis=1)
+    P = np.repeat(np.exp(s * gx_nodes)[:, None], n, axis=1)
+    return DivAGradOp(n, ax, ay, P)
+
+
+def gaussian_block(N: int, k: int, seed: int) -> np.ndarray:
+    """A seeded N x k block of N(0, 1) entries, row-major (k fastest)."""
+    return np.random.default_rng(seed).standard_normal((N, k))
+
+
+@dataclass
+class ChainSpec:
+    n: int
+    k: int
+    seed: int
+    n_ops: int
+
+
+def batched_chain_specs(n_chains: int, n_ops: int, seed: int, n_lo: int = 64,
+                        n_hi: int = 192, k_lo: int = 32, k_hi: int = 256) -> List[ChainSpec]:
+    """Per-chain grid side and k drawn uniformly (inclusive), one seed per chain."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for c in range(n_chains):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        k = int(rng.integers(k_lo, k_hi + 1))
+        specs.append(ChainSpec(n=n, k=k, seed=int(seed * 1000 + c), n_ops=n_ops))
+    return specs
+
+
+@dataclass
+class Workload:
+    name: str
+    kind: str           # "div_a_grad" | "lap_plus_v"
+    n: int
+    n_ops: int
+    k: int
+    degree: int
+    tol: float
+    seed: int
+    p0: int = 8
+    extra: dict = field(default_factory=dict)
+
+    def operators(self, n_ops: int | None = None):
+        cnt = self.n_ops if n_ops is None else n_ops
+        if self.kind == "div_a_grad":
+            return div_a_grad_chain(self.n, cnt, self.seed)
+        return lap_plus_v_chain(self.n, cnt, self.seed)
+
+
+# The five workload laws: shapes, sizes and seeds.
+WORKLOADS = {
+    "poisson32_k20": Workload("poisson32_k20", "div_a_grad", n=32, n_ops=16, k=20,
+                              degree=16, tol=1e-8, seed=0),
+    "poisson128_k100": Workload("poisson128_k100", "div_a_grad", n=128, n_ops=200, k=100,
+                                degree=20, tol=1e-8, seed=1),
+    "lapv256_k400": Workload("lapv256_k400", "lap_plus_v", n=256, n_ops=1000, k=400,
+                             degree=20, tol=1e-8, seed=2),
+}
