@@ -1,0 +1,192 @@
+/*
+ * scsf.h - C ABI of the GB300 (sm_103a) SCSF library: sorting Chebyshev
+ * subspace filter for sequences of discretised symmetric eigenvalue problems.
+ *
+ * Problem statement (paper Sec. 2.1, Eq. (eq:eq_basic)): for a sequence of
+ * symmetric matrices A^(i), i = 1..n_ops, find the k algebraically smallest
+ * eigenpairs A^(i) v_j = lambda_j v_j. The library
+ *   - orders the problems by the truncated-FFT greedy sort (Alg. 2), and
+ *   - solves them in that order by Chebyshev filtered subspace iteration
+ *     (Alg. 1, Alg. 3), each warm-started from the previous problem's block.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers on the context's device unless a
+ *     comment says "host". The caller owns every buffer; the library never
+ *     frees or retains caller memory beyond the call.
+ *   - Work is enqueued on the context's stream in stream order. Outputs are
+ *     valid once that stream has been synchronised. Entry points that need a
+ *     host decision (the solver's lock/stop test) synchronise the stream
+ *     internally and return after their last kernel has finished.
+ *   - Dense blocks are row-major with the column index fastest:
+ *     element (row r, column c) of an R x C block with leading dimension ld is
+ *     at p[r*ld + c]. Grid nodes are numbered I = i*n + j (Sec. 2.1, row-major).
+ *   - Errors are returned as scsf_status; scsf_last_error() gives a message.
+ *     No exceptions cross the ABI and there is no CPU fallback: a missing or
+ *     unusable GPU is an error (SCSF_ERR_CUDA).
+ *   - Contexts are not thread-safe; use one context per host thread.
+ */
+#ifndef SCSF_H
+#define SCSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCSF_OK = 0,
+  SCSF_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range        */
+  SCSF_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed         */
+  SCSF_ERR_NOT_CONVERGED = 3, /* max_iter reached before k pairs met the tolerance   */
+  SCSF_ERR_BREAKDOWN = 4,     /* Cholesky QR met a non-positive pivot twice          */
+  SCSF_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                  */
+  SCSF_ERR_NO_MEMORY = 6      /* the caller's workspace is smaller than required     */
+} scsf_status;
+
+typedef struct scsf_ctx scsf_ctx;
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). *out receives the
+ * handle. The context owns only small pinned host staging buffers. */
+scsf_status scsf_create(scsf_ctx** out, int device, void* cuda_stream);
+void scsf_destroy(scsf_ctx* ctx);
+/* Message for the last failing call on this context; valid until the next call. */
+const char* scsf_last_error(const scsf_ctx* ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int scsf_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Truncated-FFT greedy sort (Alg. 2, Sec. 3.1).
+ *
+ * fields   : [n_ops][p][p] FP64, the parameter matrix P^(i) of each problem.
+ * p0       : kept low-frequency block, 1 <= p0 <= p. Features are the DFT
+ *            coefficients F[k1][k2] = (1/p) sum_{x,y} P[x][y]
+ *            exp(-2 pi i (k1 x + k2 y)/p) for 0 <= k1, k2 < p0 (unshifted
+ *            indices, unitary scaling; App. F).
+ * start    : index of the first problem of the chain (Alg. 2 uses problem 1;
+ *            indices here are 0-based).
+ * workspace: device scratch of at least scsf_sort_workspace_size(n_ops, p0)
+ *            bytes, 256-byte aligned.
+ * perm_out : [n_ops] int32, the visiting order. Each step appends the
+ *            remaining problem with the smallest squared Frobenius distance
+ *            between feature blocks (FP64, fixed summation order); equal
+ *            distances go to the smaller index.
+ * Limits: 1 <= n_ops <= 65536, 1 <= p0 <= min(p, 64), p <= 1024 and
+ * (2 p + 2 p p0) * 8 bytes <= 220 KiB (one CTA per problem holds a p x p0 block). */
+size_t scsf_sort_workspace_size(int64_t n_ops, int p0);
+scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                      int start, void* workspace, size_t workspace_bytes, int32_t* perm_out);
+
+/* ---------------------------------------------------------------------------
+ * Operators (App. D.2), Dirichlet boundary, n x n interior grid, h = 1/(n+1).
+ *
+ * SCSF_OP_DIV_A_GRAD: -div(a grad u), conservative 5-point form
+ *   (A u)_ij = [a_{i+1/2,j}(u_ij-u_{i+1,j}) + a_{i-1/2,j}(u_ij-u_{i-1,j})
+ *             + a_{i,j+1/2}(u_ij-u_{i,j+1}) + a_{i,j-1/2}(u_ij-u_{i,j-1})]/h^2
+ *   ax: [n+1][n] FP64, ax[f][j] = a on the x-face between nodes (f-1, j), (f, j)
+ *   ay: [n][n+1] FP64, ay[i][g] = a on the y-face between nodes (i, g-1), (i, g)
+ * SCSF_OP_LAP_PLUS_V: -Lap u + V u (same stencil with a == 1, plus diag V)
+ *   v : [n][n] FP64
+ * Unused pointers may be NULL. */
+typedef enum { SCSF_OP_DIV_A_GRAD = 0, SCSF_OP_LAP_PLUS_V = 1 } scsf_op_kind;
+
+typedef struct {
+  int kind;          /* scsf_op_kind                   */
+  int n;             /* interior grid side, N = n*n    */
+  const double* ax;
+  const double* ay;
+  const double* v;
+} scsf_operator;
+
+typedef enum { SCSF_FP64 = 0, SCSF_MIXED = 1 } scsf_precision;
+
+typedef struct {
+  int k;             /* wanted eigenpairs (L in the paper), >= 1                          */
+  int nex;           /* extra block columns; < 0 selects ceil(0.2 k) (App. D.4)            */
+  int degree;        /* Chebyshev degree m >= 1 (Alg. 1)                                  */
+  double tol;        /* relative residual ||A v - lambda v|| / ||A v|| to lock (App. D.5) */
+  int max_iter;      /* outer iterations per problem (Alg. 3 repeat loop), >= 1           */
+  int precision;     /* scsf_precision                                                    */
+  uint64_t seed;     /* Philox seed of the random head block (Sec. 3.2, first problem)    */
+} scsf_params;
+
+typedef struct {
+  int iters;             /* outer iterations (Alg. 3 repeat loop)            */
+  int converged;         /* 1 if k pairs met tol                             */
+  int filter_steps;      /* stencil SpMM steps applied in the filter         */
+  int locked;            /* pairs locked at exit                             */
+  double flops_fp64;     /* algorithmic FP64 flops issued                    */
+  double filter_bytes;   /* algorithmic filter bytes (3 blocks per step)     */
+} scsf_stats;
+
+/* Largest block width (k + nex) the solver accepts. */
+int scsf_max_block_width(void);
+
+/* Device workspace (bytes) for problems with grid side <= n_max under params. */
+size_t scsf_solve_workspace_size(const scsf_params* params, int n_max);
+
+/* ---------------------------------------------------------------------------
+ * Chain solve (Alg. 3 applied along a sorted sequence, Sec. 3.2).
+ *
+ * A chain keeps the previous problem's final block (N x k_b, k_b = k + nex)
+ * and its Ritz values in the workspace as the warm start of the next problem.
+ * The first problem of a chain starts from a Philox-normal block (seeded by
+ * params->seed) with filter bounds lambda = Gershgorin lower bound,
+ * alpha = lo + 2 (k_b/N)(hi - lo), beta = Gershgorin upper bound.
+ *
+ * scsf_chain_create: allocates only a small host-side handle; `workspace`
+ *   (device, >= scsf_solve_workspace_size(params, n) bytes, 256-byte aligned)
+ *   must stay alive and untouched by the caller until scsf_chain_destroy.
+ * scsf_chain_seed: replaces the warm start by a caller block (device
+ *   [N][k_b] FP64, row-major) and its Ritz values (host [k_b] FP64); both are
+ *   copied. Used to resume a chain or to inject a proposed subspace.
+ * scsf_chain_step: solves one problem whose grid side equals the chain's n.
+ *   evals  : [k] FP64 ascending eigenvalues
+ *   resid  : [k] FP64 relative residuals (App. D.5)
+ *   evecs  : [N][k] FP64 row-major (column j is eigenvector j) or NULL
+ *   stats  : host pointer or NULL
+ *   On SCSF_ERR_NOT_CONVERGED the locked pairs come first, the other
+ *   eigenvalue slots hold NaN, and the warm start is kept for the next step. */
+typedef struct scsf_chain scsf_chain;
+scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n,
+                              void* workspace, size_t workspace_bytes, scsf_chain** out);
+scsf_status scsf_chain_seed(scsf_chain* chain, const double* block, const double* ritz_host);
+scsf_status scsf_chain_step(scsf_chain* chain, const scsf_operator* op, double* evals,
+                            double* resid, double* evecs, scsf_stats* stats);
+void scsf_chain_destroy(scsf_chain* chain);
+
+/* Solve n_ops problems (same n) in the given order as one chain.
+ * ops    : host array of n_ops operator descriptors (device pointers inside)
+ * evals  : [n_ops][k], resid: [n_ops][k], evecs: [n_ops][N][k] or NULL,
+ * stats  : host [n_ops] or NULL. Returns the first non-OK status, after
+ *          finishing the remaining problems. */
+scsf_status scsf_solve(scsf_ctx* ctx, const scsf_operator* ops, int64_t n_ops,
+                       const scsf_params* params, void* workspace, size_t workspace_bytes,
+                       double* evals, double* resid, double* evecs, scsf_stats* stats);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks exported for kernel-level parity tests. Same conventions.
+ *
+ * scsf_cheb_filter: Y = C_m(Abar) X / C_m(t_lambda) by the scaled recurrence of
+ *   Alg. 1 (Abar = (A - cI)/e, t_lambda = (lambda - c)/e) for the operator `op`.
+ *   X, Y: [N][ncols] FP64 with leading dimensions ldx, ldy (>= ncols);
+ *   scratch: device, >= 2 * N * ncols * 8 bytes. X and Y must not overlap.
+ * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}).
+ * scsf_small_eigh: all eigenpairs of a symmetric k x k FP64 matrix S
+ *   (row-major, k <= scsf_max_block_width()): evals [k] ascending, Z [k][k]
+ *   with eigenvector j in column j. scratch >= scsf_small_eigh_scratch(k). */
+scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                             int ncols, int degree, double lambda, double c, double e,
+                             double* Y, int ldy, void* scratch, size_t scratch_bytes);
+scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double* bounds_host,
+                                 void* scratch, size_t scratch_bytes);
+size_t scsf_small_eigh_scratch(int k);
+scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
+                            void* scratch, size_t scratch_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCSF_H */

@@ -1,0 +1,387 @@
+"""GB300-native SCSF: sorting Chebyshev subspace filter for eigenvalue datasets.
+
+Python binding of the C ABI in ``include/scsf.h`` (``libscsf.so``, built in-tree
+for sm_103a by ``paper_2510_23215_gb300.build``). This module only marshals
+arguments: every step of the sort and of the solver runs in the library's CUDA
+kernels. PyTorch provides device memory and the CUDA stream. There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+
+Paper: "Accelerating Eigenvalue Dataset Generation via Chebyshev Subspace
+Filter" - truncated-FFT greedy sort (Alg. 2) and warm-started Chebyshev
+filtered subspace iteration (Alg. 1, Alg. 3) over a sorted sequence of
+discretised symmetric operators (Sec. 2.1, Eq. (eq:eq_basic)).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+__all__ = [
+    "ScsfError", "Operator", "Params", "Context", "Chain", "library", "lib_path",
+    "sort", "solve", "cheb_filter", "assemble_bounds", "small_eigh", "block_width",
+    "FP64", "MIXED", "DIV_A_GRAD", "LAP_PLUS_V", "EXPORTED_SYMBOLS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libscsf.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NO_MEMORY = range(7)
+DIV_A_GRAD, LAP_PLUS_V = 0, 1
+FP64, MIXED = 0, 1
+
+EXPORTED_SYMBOLS = [
+    "scsf_create", "scsf_destroy", "scsf_last_error", "scsf_version",
+    "scsf_sort_workspace_size", "scsf_sort", "scsf_max_block_width",
+    "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
+    "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
+    "scsf_small_eigh_scratch", "scsf_small_eigh",
+]
+
+
+class ScsfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"scsf status {status}: {message}")
+        self.status = status
+
+
+class _COperator(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("ax", ctypes.c_void_p),
+                ("ay", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("nex", ctypes.c_int), ("degree", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class _CStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("filter_steps", ctypes.c_int), ("locked", ctypes.c_int),
+                ("flops_fp64", ctypes.c_double), ("filter_bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Loads libscsf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise ImportError(f"{lib_path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(lib_path)
+    vp, i32, i64, dbl, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    L.scsf_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    L.scsf_destroy.argtypes = [vp]
+    L.scsf_destroy.restype = None
+    L.scsf_last_error.argtypes = [vp]
+    L.scsf_last_error.restype = ctypes.c_char_p
+    L.scsf_sort_workspace_size.argtypes = [i64, i32]
+    L.scsf_sort_workspace_size.restype = sz
+    L.scsf_sort.argtypes = [vp, vp, i64, i32, i32, i32, vp, sz, vp]
+    L.scsf_max_block_width.restype = i32
+    L.scsf_solve_workspace_size.argtypes = [ctypes.POINTER(_CParams), i32]
+    L.scsf_solve_workspace_size.restype = sz
+    L.scsf_chain_create.argtypes = [vp, ctypes.POINTER(_CParams), i32, vp, sz, ctypes.POINTER(vp)]
+    L.scsf_chain_seed.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+    L.scsf_chain_step.argtypes = [vp, ctypes.POINTER(_COperator), vp, vp, vp, ctypes.POINTER(_CStats)]
+    L.scsf_chain_destroy.argtypes = [vp]
+    L.scsf_chain_destroy.restype = None
+    L.scsf_solve.argtypes = [vp, ctypes.POINTER(_COperator), i64, ctypes.POINTER(_CParams), vp, sz,
+                             vp, vp, vp, ctypes.POINTER(_CStats)]
+    L.scsf_cheb_filter.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, i32, i32, dbl, dbl, dbl,
+                                   vp, i32, vp, sz]
+    L.scsf_assemble_bounds.argtypes = [vp, ctypes.POINTER(_COperator), ctypes.POINTER(dbl), vp, sz]
+    L.scsf_small_eigh_scratch.argtypes = [i32]
+    L.scsf_small_eigh_scratch.restype = sz
+    L.scsf_small_eigh.argtypes = [vp, vp, i32, vp, vp, vp, sz]
+    for name in EXPORTED_SYMBOLS:
+        fn = getattr(L, name)
+        if fn.restype is ctypes.c_int or name in (
+                "scsf_create", "scsf_sort", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
+                "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds", "scsf_small_eigh"):
+            fn.restype = ctypes.c_int
+    L.scsf_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _check(t: torch.Tensor, name: str, dtype=torch.float64, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device (the library has no CPU path)")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def block_width(k: int, nex: int = -1) -> int:
+    """k_b = k + nex, nex = ceil(0.2 k) by default (App. D.4)."""
+    return k + (nex if nex >= 0 else int(math.ceil(0.2 * k)))
+
+
+@dataclass
+class Operator:
+    """One discretised operator on the n x n interior grid (device FP64 tensors)."""
+    kind: int
+    n: int
+    ax: Optional[torch.Tensor] = None   # [n+1, n]
+    ay: Optional[torch.Tensor] = None   # [n, n+1]
+    v: Optional[torch.Tensor] = None    # [n, n]
+
+    @staticmethod
+    def from_workload(op, device="cuda") -> "Operator":
+        """Uploads an ``scsf_inputs`` operator (numpy) to the device."""
+        if hasattr(op, "ax"):
+            return Operator(DIV_A_GRAD, op.n,
+                            ax=torch.as_tensor(op.ax, dtype=torch.float64, device=device).contiguous(),
+                            ay=torch.as_tensor(op.ay, dtype=torch.float64, device=device).contiguous())
+        return Operator(LAP_PLUS_V, op.n,
+                        v=torch.as_tensor(op.V, dtype=torch.float64, device=device).contiguous())
+
+    def _c(self) -> _COperator:
+        if self.kind == DIV_A_GRAD:
+            _check(self.ax, "ax")
+            _check(self.ay, "ay", device=self.ax.device)
+            if tuple(self.ax.shape) != (self.n + 1, self.n) or tuple(self.ay.shape) != (self.n, self.n + 1):
+                raise ValueError("ax must be [n+1, n] and ay [n, n+1]")
+        elif self.kind == LAP_PLUS_V:
+            _check(self.v, "v")
+            if tuple(self.v.shape) != (self.n, self.n):
+                raise ValueError("v must be [n, n]")
+        else:
+            raise ValueError(f"unknown operator kind {self.kind}")
+        return _COperator(self.kind, self.n, _ptr(self.ax), _ptr(self.ay), _ptr(self.v))
+
+    @property
+    def device(self):
+        return (self.ax if self.kind == DIV_A_GRAD else self.v).device
+
+
+@dataclass
+class Params:
+    k: int
+    degree: int = 20
+    tol: float = 1e-8
+    max_iter: int = 100
+    nex: int = -1
+    precision: int = FP64
+    seed: int = 0
+
+    def _c(self) -> _CParams:
+        return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
+                        self.seed & 0xFFFFFFFFFFFFFFFF)
+
+    @property
+    def kb(self) -> int:
+        return block_width(self.k, self.nex)
+
+
+class Context:
+    """An scsf_ctx bound to one device and a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        L = library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the SCSF library has no CPU path")
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = L.scsf_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
+        if st != OK:
+            raise ScsfError(st, "scsf_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, status: int):
+        if status != OK:
+            msg = library().scsf_last_error(self._h).decode(errors="replace")
+            raise ScsfError(status, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().scsf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx: dict = {}
+
+
+def _ctx(ctx: Optional[Context], device) -> Context:
+    if ctx is not None:
+        return ctx
+    idx = torch.device(device).index or 0
+    stream = torch.cuda.current_stream(idx)
+    key = (idx, stream.cuda_stream)
+    if key not in _default_ctx:
+        _default_ctx[key] = Context(idx, stream)
+    return _default_ctx[key]
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] = None) -> torch.Tensor:
+    """Alg. 2: visiting order of the problems (int32 [n_ops]) from fields [n_ops, p, p] FP64."""
+    _check(fields, "fields")
+    if fields.dim() != 3 or fields.shape[1] != fields.shape[2]:
+        raise ValueError("fields must be [n_ops, p, p]")
+    c = _ctx(ctx, fields.device)
+    L = library()
+    n_ops, p = int(fields.shape[0]), int(fields.shape[1])
+    ws = _workspace(L.scsf_sort_workspace_size(n_ops, p0), fields.device)
+    perm = torch.empty(n_ops, dtype=torch.int32, device=fields.device)
+    c.check(L.scsf_sort(c.handle, fields.data_ptr(), n_ops, p, p0, start, ws.data_ptr(),
+                        ws.numel(), perm.data_ptr()))
+    return perm
+
+
+def _stats_dict(s: _CStats) -> dict:
+    return {"iters": s.iters, "converged": bool(s.converged), "filter_steps": s.filter_steps,
+            "locked": s.locked, "flops_fp64": s.flops_fp64, "filter_bytes": s.filter_bytes}
+
+
+class Chain:
+    """A warm-started sequence of solves on one grid size (Alg. 3 along a sorted chain)."""
+
+    def __init__(self, params: Params, n: int, device="cuda", ctx: Optional[Context] = None):
+        self.ctx = _ctx(ctx, device)
+        self.params = params
+        self.n = n
+        L = library()
+        cp = params._c()
+        nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), n)
+        if nbytes == 0:
+            raise ValueError("unsupported parameters (block width or grid)")
+        self.workspace = _workspace(nbytes, self.ctx.device)
+        h = ctypes.c_void_p()
+        self.ctx.check(L.scsf_chain_create(self.ctx.handle, ctypes.byref(cp), n,
+                                           self.workspace.data_ptr(), self.workspace.numel(),
+                                           ctypes.byref(h)))
+        self._h = h
+
+    def seed(self, block: torch.Tensor, ritz: Sequence[float]):
+        _check(block, "block", device=self.ctx.device)
+        kb = self.params.kb
+        if tuple(block.shape) != (self.n * self.n, kb) or len(ritz) != kb:
+            raise ValueError("block must be [N, k_b] with k_b Ritz values")
+        arr = (ctypes.c_double * kb)(*[float(x) for x in ritz])
+        self.ctx.check(library().scsf_chain_seed(self._h, block.data_ptr(), arr))
+
+    def step(self, op: Operator, want_vectors: bool = True, raise_on_nonconvergence: bool = True):
+        k, N = self.params.k, self.n * self.n
+        dev = self.ctx.device
+        evals = torch.empty(k, dtype=torch.float64, device=dev)
+        resid = torch.empty(k, dtype=torch.float64, device=dev)
+        evecs = torch.empty((N, k), dtype=torch.float64, device=dev) if want_vectors else None
+        stats = _CStats()
+        cop = op._c()
+        st = library().scsf_chain_step(self._h, ctypes.byref(cop), evals.data_ptr(), resid.data_ptr(),
+                                       _ptr(evecs), ctypes.byref(stats))
+        if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            self.ctx.check(st)
+        return evals, resid, evecs, _stats_dict(stats)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().scsf_chain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(ops: List[Operator], params: Params, want_vectors: bool = False,
+          ctx: Optional[Context] = None):
+    """scsf_solve over ops (already in solve order). Returns (evals, resid, evecs|None, stats)."""
+    if not ops:
+        raise ValueError("no operators")
+    c = _ctx(ctx, ops[0].device)
+    L = library()
+    n = ops[0].n
+    cp = params._c()
+    nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), n)
+    if nbytes == 0:
+        raise ValueError("unsupported parameters (block width or grid)")
+    ws = _workspace(nbytes, c.device)
+    n_ops, k, N = len(ops), params.k, n * n
+    evals = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
+    resid = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
+    evecs = torch.empty((n_ops, N, k), dtype=torch.float64, device=c.device) if want_vectors else None
+    cops = (_COperator * n_ops)(*[o._c() for o in ops])
+    stats = (_CStats * n_ops)()
+    c.check(L.scsf_solve(c.handle, cops, n_ops, ctypes.byref(cp), ws.data_ptr(), ws.numel(),
+                         evals.data_ptr(), resid.data_ptr(), _ptr(evecs), stats))
+    return evals, resid, evecs, [_stats_dict(s) for s in stats]
+
+
+def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float, e: float,
+                ctx: Optional[Context] = None) -> torch.Tensor:
+    """Alg. 1: C_m(Abar) X / C_m(t_lambda) for X [N, ncols] FP64."""
+    _check(X, "X")
+    cx = _ctx(ctx, X.device)
+    N, ncols = int(X.shape[0]), int(X.shape[1])
+    if N != op.n * op.n:
+        raise ValueError("X must have n*n rows")
+    Y = torch.empty_like(X)
+    ws = _workspace(8 * (2 * N * ncols + 3 * N + 2 * 2048) + 8192, X.device)
+    cop = op._c()
+    cx.check(library().scsf_cheb_filter(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, ncols,
+                                        degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
+                                        ws.numel()))
+    return Y
+
+
+def assemble_bounds(op: Operator, ctx: Optional[Context] = None):
+    """Gershgorin bounds (lo, hi) of the assembled operator."""
+    cx = _ctx(ctx, op.device)
+    N = op.n * op.n
+    ws = _workspace(8 * (3 * N + 2 * 2048) + 8192, op.device)
+    out = (ctypes.c_double * 2)()
+    cop = op._c()
+    cx.check(library().scsf_assemble_bounds(cx.handle, ctypes.byref(cop), out, ws.data_ptr(),
+                                            ws.numel()))
+    return float(out[0]), float(out[1])
+
+
+def small_eigh(S: torch.Tensor, ctx: Optional[Context] = None):
+    """All eigenpairs of a small symmetric FP64 matrix (ascending), via the reduced eigensolver."""
+    _check(S, "S")
+    k = int(S.shape[0])
+    cx = _ctx(ctx, S.device)
+    L = library()
+    ws = _workspace(L.scsf_small_eigh_scratch(k), S.device)
+    evals = torch.empty(k, dtype=torch.float64, device=S.device)
+    Z = torch.empty((k, k), dtype=torch.float64, device=S.device)
+    cx.check(L.scsf_small_eigh(cx.handle, S.data_ptr(), k, evals.data_ptr(), Z.data_ptr(),
+                               ws.data_ptr(), ws.numel()))
+    return evals, Z

@@ -1,0 +1,524 @@
+// C ABI of the SCSF library: contexts, the sort entry point, and the chain
+// driver that runs Chebyshev filtered subspace iteration (Alg. 3) on each
+// problem of a sorted sequence, warm-started from the previous problem.
+//
+// The driver is host code issuing stream-ordered kernels; the only device ->
+// host traffic per outer iteration is the Ritz values and residual norms of
+// the active block (2-3 k_b doubles), which decide locking and termination.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/scsf.h"
+#include "kernels.cuh"
+
+using namespace scsf;
+
+struct scsf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double* pinned = nullptr;  // host staging
+  size_t pinned_count = 0;
+};
+
+namespace {
+
+constexpr size_t kPinnedDoubles = 4 * kMaxBlockWidth + 64;
+
+scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define SCSF_CUDA(ctx, expr)                                                              \
+  do {                                                                                    \
+    cudaError_t _e = (expr);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail((ctx), SCSF_ERR_CUDA,                                                   \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                    \
+  } while (0)
+
+int block_width(const scsf_params* p) {
+  const int nex = (p->nex >= 0) ? p->nex : (int)std::ceil(0.2 * p->k);
+  return p->k + nex;
+}
+
+bool op_ok(const scsf_operator* op) {
+  if (!op || op->n < 2) return false;
+  if (op->kind == SCSF_OP_DIV_A_GRAD) return op->ax && op->ay;
+  if (op->kind == SCSF_OP_LAP_PLUS_V) return op->v != nullptr;
+  return false;
+}
+
+// Device buffers of one chain, carved from the caller's workspace.
+struct ChainBufs {
+  double *V, *B0, *B1, *B2;        // N x kb blocks (row-major, ld = kb)
+  double *d, *we, *wn;             // stencil coefficients
+  double *asm_partials, *bounds;   // Gershgorin reduction
+  double *G, *Rinv, *H, *Z, *C;    // kb x kb small matrices
+  double *theta, *res2;            // kb, 2*kb
+  double *gemm_partials, *res_partials;
+  void* eigh_scratch;
+  int* status;
+  int* cols;
+};
+
+template <typename Cv>
+void carve_chain(Cv& c, int n, int kb, ChainBufs& b) {
+  const size_t N = (size_t)n * n;
+  const size_t blk = N * kb;
+  const size_t kk = (size_t)kb * kb;
+  const int T = (kb + kGemmTile - 1) / kGemmTile;
+  b.V = c.template take<double>(blk);
+  b.B0 = c.template take<double>(blk);
+  b.B1 = c.template take<double>(blk);
+  b.B2 = c.template take<double>(blk);
+  b.d = c.template take<double>(N);
+  b.we = c.template take<double>(N);
+  b.wn = c.template take<double>(N);
+  b.asm_partials = c.template take<double>(2 * (size_t)assemble_blocks(n));
+  b.bounds = c.template take<double>(2);
+  b.G = c.template take<double>(kk);
+  b.Rinv = c.template take<double>(kk);
+  b.H = c.template take<double>(kk);
+  b.Z = c.template take<double>(kk);
+  b.C = c.template take<double>(kk);
+  b.theta = c.template take<double>(kb);
+  b.res2 = c.template take<double>(2 * (size_t)kb);
+  b.gemm_partials = c.template take<double>((size_t)(kSplitTarget + T * T) * kGemmTile * kGemmTile);
+  b.res_partials = c.template take<double>((size_t)resid_blocks(n) * 2 * kb);
+  b.eigh_scratch = c.template take<char>(small_eigh_scratch_bytes(kb));
+  b.status = c.template take<int>(4);
+  b.cols = c.template take<int>(kb);
+}
+
+struct SizeCarve {
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    used += align256(count * sizeof(T));
+    return nullptr;
+  }
+};
+
+Stencil stencil_of(const ChainBufs& b, int n) { return Stencil{b.d, b.we, b.wn, n}; }
+
+// Alg. 1 on an N x ncols block: Y_m = C_m(Abar) Y_0 / C_m(t_lambda).
+// Y_i is written to bufs[(i - 1) % 3]; returns the buffer that holds Y_m.
+cudaError_t run_filter(const Stencil& A, const double* Y0, int ld0, int ncols, int degree,
+                       double lam, double c, double e, double* const bufs[3], const int lds[3],
+                       int* which, cudaStream_t st) {
+  const double sigma1 = e / (lam - c);
+  // Y_1 = sigma_1 Abar Y_0 = (sigma_1/e) A Y_0 - (sigma_1 c/e) Y_0
+  cudaError_t err = launch_cheb_step_f64(A, Y0, ld0, nullptr, 0, bufs[0], lds[0], ncols,
+                                         sigma1 / e, -sigma1 * c / e, 0.0, st);
+  if (err != cudaSuccess) return err;
+  double sigma = sigma1;
+  const double* prev = Y0;
+  int ldp = ld0;
+  int cur = 0;
+  for (int i = 1; i < degree; ++i) {
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    const int nxt = i % 3;
+    // Y_{i+1} = 2 sigma_{i+1} Abar Y_i - sigma_{i+1} sigma_i Y_{i-1}
+    err = launch_cheb_step_f64(A, bufs[cur], lds[cur], prev, ldp, bufs[nxt], lds[nxt], ncols,
+                               2.0 * sigma_next / e, -2.0 * sigma_next * c / e,
+                               -sigma_next * sigma, st);
+    if (err != cudaSuccess) return err;
+    prev = bufs[cur];
+    ldp = lds[cur];
+    cur = nxt;
+    sigma = sigma_next;
+  }
+  *which = cur;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+struct scsf_chain {
+  scsf_ctx* ctx = nullptr;
+  scsf_params p{};
+  int n = 0, N = 0, kb = 0;
+  ChainBufs b{};
+  bool has_block = false;
+  std::vector<double> ritz;  // Ritz values of the kept block (warm start)
+};
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int scsf_version(void) { return 100; }
+int scsf_max_block_width(void) { return kMaxBlockWidth; }
+
+scsf_status scsf_create(scsf_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SCSF_ERR_INVALID_ARG;
+  *out = nullptr;
+  scsf_ctx* ctx = new (std::nothrow) scsf_ctx();
+  if (!ctx) return SCSF_ERR_NO_MEMORY;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) {
+    delete ctx;
+    return SCSF_ERR_CUDA;
+  }
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaMallocHost(&ctx->pinned, kPinnedDoubles * sizeof(double)) != cudaSuccess) {
+    delete ctx;
+    return SCSF_ERR_CUDA;
+  }
+  ctx->pinned_count = kPinnedDoubles;
+  *out = ctx;
+  return SCSF_OK;
+}
+
+void scsf_destroy(scsf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+const char* scsf_last_error(const scsf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t scsf_sort_workspace_size(int64_t n_ops, int p0) {
+  if (n_ops <= 0 || p0 <= 0) return 0;
+  return sort_workspace_bytes(n_ops, p0);
+}
+
+scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0, int start,
+                      void* workspace, size_t workspace_bytes, int32_t* perm_out) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!fields || !perm_out || !workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  if (n_ops < 1 || n_ops > 65536) return fail(ctx, SCSF_ERR_INVALID_ARG, "n_ops out of [1, 65536]");
+  if (p < 1 || p > 1024 || p0 < 1 || p0 > p)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= p0 <= p <= 1024");
+  if ((size_t)(2 * p + 2 * p * p0) * sizeof(double) > 220 * 1024)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "p * p0 too large for one CTA's shared memory");
+  if (p0 > 64) return fail(ctx, SCSF_ERR_INVALID_ARG, "p0 > 64 is not supported");
+  if (start < 0 || start >= n_ops) return fail(ctx, SCSF_ERR_INVALID_ARG, "start out of range");
+  if (workspace_bytes < sort_workspace_bytes(n_ops, p0))
+    return fail(ctx, SCSF_ERR_NO_MEMORY, "sort workspace too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, launch_sort(fields, n_ops, p, p0, start, workspace, perm_out, ctx->stream));
+  return SCSF_OK;
+}
+
+size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
+  if (!params || n_max < 2) return 0;
+  const int kb = block_width(params);
+  if (kb < 1 || kb > kMaxBlockWidth) return 0;
+  SizeCarve c;
+  ChainBufs b;
+  carve_chain(c, n_max, kb, b);
+  return c.used;
+}
+
+scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, void* workspace,
+                              size_t workspace_bytes, scsf_chain** out) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!params || !out || !workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  *out = nullptr;
+  const int kb = block_width(params);
+  if (params->k < 1 || kb > kMaxBlockWidth)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "need 1 <= k and k + nex <= " + std::to_string(kMaxBlockWidth));
+  if (n < 2 || (long long)n * n < kb)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "grid too small for the block width");
+  if (params->degree < 1 || !(params->tol > 0.0) || params->max_iter < 1)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need degree >= 1, tol > 0, max_iter >= 1");
+  if (params->precision != SCSF_FP64)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "only SCSF_FP64 is available in this build");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  scsf_chain* ch = new (std::nothrow) scsf_chain();
+  if (!ch) return fail(ctx, SCSF_ERR_NO_MEMORY, "host allocation failed");
+  ch->ctx = ctx;
+  ch->p = *params;
+  ch->n = n;
+  ch->N = n * n;
+  ch->kb = kb;
+  Carve c(workspace, workspace_bytes);
+  carve_chain(c, n, kb, ch->b);
+  if (!c.ok) {
+    delete ch;
+    return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
+  }
+  ch->ritz.assign(kb, 0.0);
+  *out = ch;
+  return SCSF_OK;
+}
+
+void scsf_chain_destroy(scsf_chain* chain) { delete chain; }
+
+scsf_status scsf_chain_seed(scsf_chain* ch, const double* block, const double* ritz_host) {
+  if (!ch) return SCSF_ERR_INVALID_ARG;
+  scsf_ctx* ctx = ch->ctx;
+  if (!block || !ritz_host) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(ch->b.V, block, (size_t)ch->N * ch->kb * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+  ch->ritz.assign(ritz_host, ritz_host + ch->kb);
+  ch->has_block = true;
+  return SCSF_OK;
+}
+
+scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* evals, double* resid,
+                            double* evecs, scsf_stats* stats) {
+  if (!ch) return SCSF_ERR_INVALID_ARG;
+  scsf_ctx* ctx = ch->ctx;
+  cudaStream_t st = ctx->stream;
+  if (!op_ok(op)) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad operator descriptor");
+  if (op->n != ch->n) return fail(ctx, SCSF_ERR_INVALID_ARG, "operator grid differs from the chain's");
+  if (!evals || !resid) return fail(ctx, SCSF_ERR_INVALID_ARG, "null output pointer");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int n = ch->n, N = ch->N, kb = ch->kb, k = ch->p.k, m = ch->p.degree;
+  ChainBufs& b = ch->b;
+  const Stencil A = stencil_of(b, n);
+  double* h = ctx->pinned;
+
+  // operator coefficients and Gershgorin bounds
+  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, b.d, b.we, b.wn,
+                                 b.asm_partials, b.bounds, st));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+  const double lo = h[0], hi = h[1];
+  const double beta = hi;
+  double lam, alpha;
+  if (!ch->has_block) {  // head of the chain: random block (Sec. 3.2)
+    SCSF_CUDA(ctx, launch_philox_normal(b.V, N, kb, kb, ch->p.seed, st));
+    lam = lo;
+    alpha = lo + 2.0 * ((double)kb / N) * (hi - lo);
+  } else {               // warm start: previous block and Ritz values (Alg. 3 line 1)
+    lam = *std::min_element(ch->ritz.begin(), ch->ritz.end());
+    alpha = *std::max_element(ch->ritz.begin(), ch->ritz.end());
+  }
+
+  std::vector<double> locked_val, locked_res;
+  std::vector<double> theta_h(kb), r_h(kb);
+  int nl = 0, it = 0, filter_steps = 0;
+  double flops = 0.0, fbytes = 0.0;
+  bool converged = false;
+  for (it = 1; it <= ch->p.max_iter; ++it) {
+    const int ka = kb - nl;
+    if (!(alpha < beta)) alpha = lam + 0.5 * (beta - lam);
+    if (!(lam < alpha)) lam = alpha - 1e-3 * (beta - alpha);
+    const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
+    // line 3: Chebyshev filter on the active columns
+    double* bufs[3] = {b.B0, b.B1, b.B2};
+    const int lds[3] = {kb, kb, kb};
+    int which = 0;
+    SCSF_CUDA(ctx, run_filter(A, b.V + nl, kb, ka, m, lam, c, e, bufs, lds, &which, st));
+    filter_steps += m;
+    fbytes += (double)m * N * ka * 24.0;
+    flops += (double)m * N * ka * 14.0;
+    double* Y = bufs[which];
+    double* F1 = bufs[(which + 1) % 3];
+    double* F2 = bufs[(which + 2) % 3];
+    // line 4: orthonormalise [locked | active]: CGS2 against the locked block, then CholQR2
+    if (nl > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        SCSF_CUDA(ctx, launch_gemm_tn(N, nl, ka, b.V, kb, Y, kb, b.C, ka, false, b.gemm_partials, st));
+        SCSF_CUDA(ctx, launch_gemm_nn(N, nl, ka, -1.0, b.V, kb, b.C, ka, 1.0, Y, kb, false, st));
+      }
+      flops += 8.0 * N * nl * ka;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+      SCSF_CUDA(ctx, launch_chol_inv(ka, b.G, ka, b.Rinv, b.status + pass, st));
+      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
+      std::swap(Y, F1);
+      flops += 2.0 * N * ka * ka;
+    }
+    // line 5: Rayleigh quotient G = Q^T A Q on the active columns
+    SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
+    SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+    // line 6: reduced eigenproblem and rotation back
+    SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+    SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
+    // line 7: residuals of the new Ritz pairs (App. D.5), then lock a converged prefix
+    SCSF_CUDA(ctx, launch_residual_norms(A, b.V + nl, kb, ka, b.theta, b.res_partials, b.res2, st));
+    flops += (double)N * ka * (2.0 * ka * 2 + 12.0) + 2.0 * N * ka * ka;
+    SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, ka * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * ka * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    SCSF_CUDA(ctx, cudaMemcpyAsync(h + 3 * kMaxBlockWidth, b.status, 2 * sizeof(int),
+                                   cudaMemcpyDeviceToHost, st));
+    SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+    int chol_status[2];
+    std::memcpy(chol_status, h + 3 * kMaxBlockWidth, sizeof(chol_status));
+    if (chol_status[0] >= 1000 || chol_status[1] >= 1000)
+      return fail(ctx, SCSF_ERR_BREAKDOWN, "Cholesky QR broke down even with a shift");
+    for (int j = 0; j < ka; ++j) {
+      theta_h[j] = h[j];
+      const double rr = h[kMaxBlockWidth + j], aa = h[kMaxBlockWidth + ka + j];
+      r_h[j] = (aa > 0.0) ? std::sqrt(rr / aa) : (rr > 0.0 ? INFINITY : 0.0);
+    }
+    int nconv = 0;
+    while (nconv < ka && r_h[nconv] <= ch->p.tol) ++nconv;
+    for (int j = 0; j < nconv; ++j) {
+      locked_val.push_back(theta_h[j]);
+      locked_res.push_back(r_h[j]);
+    }
+    for (int j = 0; j < ka; ++j) ch->ritz[nl + j] = theta_h[j];
+    nl += nconv;
+    if (nl >= k) {
+      converged = true;
+      break;
+    }
+    if (nl >= kb) break;
+    lam = theta_h[nconv];
+    alpha = theta_h[ka - 1];
+  }
+  if (it > ch->p.max_iter) it = ch->p.max_iter;
+  ch->has_block = true;
+
+  // outputs: the k smallest locked pairs in ascending order
+  std::vector<int> order(locked_val.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int c2) { return locked_val[a] < locked_val[c2]; });
+  const int nout = std::min<int>(k, (int)order.size());
+  std::vector<double> ev(k, NAN), rs(k, NAN);
+  std::vector<int> cols(k, 0);
+  for (int j = 0; j < nout; ++j) {
+    ev[j] = locked_val[order[j]];
+    rs[j] = locked_res[order[j]];
+    cols[j] = order[j];
+  }
+  if (!converged) {  // report the best active pairs after the locked ones
+    for (int j = nout; j < k; ++j) {
+      const int a = j - nout;
+      if (a < kb - nl) rs[j] = r_h[a];
+      cols[j] = std::min(nl + a, kb - 1);
+    }
+  }
+  std::memcpy(h, ev.data(), k * sizeof(double));
+  std::memcpy(h + kMaxBlockWidth, rs.data(), k * sizeof(double));
+  std::memcpy(h + 2 * kMaxBlockWidth, cols.data(), k * sizeof(int));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(evals, h, k * sizeof(double), cudaMemcpyHostToDevice, st));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(resid, h + kMaxBlockWidth, k * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+  if (evecs) {
+    SCSF_CUDA(ctx, cudaMemcpyAsync(b.cols, h + 2 * kMaxBlockWidth, k * sizeof(int),
+                                   cudaMemcpyHostToDevice, st));
+    SCSF_CUDA(ctx, launch_gather_cols(N, k, b.V, kb, b.cols, evecs, k, st));
+  }
+  SCSF_CUDA(ctx, cudaStreamSynchronize(st));  // staging buffer is reused by the next call
+  if (stats) {
+    stats->iters = it;
+    stats->converged = converged ? 1 : 0;
+    stats->filter_steps = filter_steps;
+    stats->locked = nl;
+    stats->flops_fp64 = flops;
+    stats->filter_bytes = fbytes;
+  }
+  if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
+  return SCSF_OK;
+}
+
+scsf_status scsf_solve(scsf_ctx* ctx, const scsf_operator* ops, int64_t n_ops,
+                       const scsf_params* params, void* workspace, size_t workspace_bytes,
+                       double* evals, double* resid, double* evecs, scsf_stats* stats) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!ops || n_ops < 1) return fail(ctx, SCSF_ERR_INVALID_ARG, "no operators");
+  scsf_chain* ch = nullptr;
+  scsf_status s = scsf_chain_create(ctx, params, ops[0].n, workspace, workspace_bytes, &ch);
+  if (s != SCSF_OK) return s;
+  const int k = params->k;
+  const size_t N = (size_t)ops[0].n * ops[0].n;
+  scsf_status first = SCSF_OK;
+  std::string first_msg;
+  for (int64_t i = 0; i < n_ops; ++i) {
+    s = scsf_chain_step(ch, &ops[i], evals + i * k, resid + i * k, evecs ? evecs + i * N * k : nullptr,
+                        stats ? stats + i : nullptr);
+    if (s != SCSF_OK && first == SCSF_OK) {
+      first = s;
+      first_msg = "problem " + std::to_string(i) + ": " + ctx->err;
+      if (s != SCSF_ERR_NOT_CONVERGED) break;
+    }
+  }
+  scsf_chain_destroy(ch);
+  if (first != SCSF_OK) ctx->err = first_msg;
+  return first;
+}
+
+// ---- building blocks ------------------------------------------------------
+scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double* bounds_host,
+                                 void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!op_ok(op) || !bounds_host || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  const size_t N = (size_t)op->n * op->n;
+  Carve c(scratch, scratch_bytes);
+  double* d = c.take<double>(N);
+  double* we = c.take<double>(N);
+  double* wn = c.take<double>(N);
+  double* part = c.take<double>(2 * (size_t)assemble_blocks(op->n));
+  double* bnd = c.take<double>(2);
+  if (!c.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, launch_assemble(op->kind, op->n, op->ax, op->ay, op->v, d, we, wn, part, bnd,
+                                 ctx->stream));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, bnd, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  SCSF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  bounds_host[0] = ctx->pinned[0];
+  bounds_host[1] = ctx->pinned[1];
+  return SCSF_OK;
+}
+
+scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                             int ncols, int degree, double lambda, double c, double e, double* Y,
+                             int ldy, void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  if (ncols < 1 || ldx < ncols || ldy < ncols || degree < 1 || !(e > 0.0) || lambda == c)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "bad sizes or filter parameters");
+  const int n = op->n;
+  const size_t N = (size_t)n * n;
+  Carve cv(scratch, scratch_bytes);
+  double* s0 = cv.take<double>(N * ncols);
+  double* s1 = cv.take<double>(N * ncols);
+  double* d = cv.take<double>(N);
+  double* we = cv.take<double>(N);
+  double* wn = cv.take<double>(N);
+  double* part = cv.take<double>(2 * (size_t)assemble_blocks(n));
+  double* bnd = cv.take<double>(2);
+  if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
+  const Stencil A{d, we, wn, n};
+  double* bufs[3] = {s0, s1, Y};
+  const int lds[3] = {ncols, ncols, ldy};
+  int which = 0;
+  SCSF_CUDA(ctx, run_filter(A, X, ldx, ncols, degree, lambda, c, e, bufs, lds, &which, st));
+  if (bufs[which] != Y)
+    SCSF_CUDA(ctx, launch_copy2d((int)N, ncols, bufs[which], lds[which], Y, ldy, st));
+  return SCSF_OK;
+}
+
+size_t scsf_small_eigh_scratch(int k) {
+  if (k < 1 || k > kMaxBlockWidth) return 0;
+  return small_eigh_scratch_bytes(k);
+}
+
+scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
+                            void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!S || !evals || !Z || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  if (k < 1 || k > kMaxBlockWidth) return fail(ctx, SCSF_ERR_INVALID_ARG, "k out of range");
+  if (scratch_bytes < small_eigh_scratch_bytes(k))
+    return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, launch_small_eigh(k, S, k, evals, Z, k, scratch, ctx->stream));
+  return SCSF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,335 @@
+// FP64 block kernels for the plain path: tall-skinny Gram / projection
+// products (Alg. 3 lines 4-6), block rotation, Cholesky + triangular inverse.
+//
+// GB300 executes FP64 at about 2 FMA/clk/SM, so these kernels are bound by
+// the FP64 pipe, not by memory: they spread the work over all SMs (split-K
+// for the N-long reductions) and skip the zero half of triangular operands.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace scsf {
+namespace {
+
+constexpr int TS = kGemmTile;  // 32
+
+// ---- C = A^T B, split over rows into chunks --------------------------------
+__device__ __forceinline__ void sym_tile_from_index(int t, int T, int& ti, int& tj) {
+  ti = 0;
+  while (t >= T - ti) {
+    t -= T - ti;
+    ++ti;
+  }
+  tj = ti + t;
+}
+
+__global__ void __launch_bounds__(256)
+gemm_tn_partial_kernel(int rows, int m, int n, const double* __restrict__ A, int lda,
+                       const double* __restrict__ B, int ldb, bool symmetric, int chunk_rows,
+                       double* __restrict__ partials) {
+  __shared__ double As[TS][TS + 1];
+  __shared__ double Bs[TS][TS + 1];
+  int ti, tj;
+  if (symmetric) {
+    sym_tile_from_index(blockIdx.x, (m + TS - 1) / TS, ti, tj);
+  } else {
+    const int tn = (n + TS - 1) / TS;
+    ti = blockIdx.x / tn;
+    tj = blockIdx.x - ti * tn;
+  }
+  const int i0 = ti * TS, j0 = tj * TS;
+  const int r_begin = blockIdx.y * chunk_rows;
+  const int r_end = min(rows, r_begin + chunk_rows);
+  const int t = threadIdx.x;
+  const int ty = t >> 4, tx = t & 15;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int r0 = r_begin; r0 < r_end; r0 += TS) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + 256 * q;       // 0..1023
+      const int rr = e >> 5, cc = e & 31;
+      const int r = r0 + rr;
+      const bool rin = r < r_end;
+      As[rr][cc] = (rin && i0 + cc < m) ? A[(size_t)r * lda + i0 + cc] : 0.0;
+      Bs[rr][cc] = (rin && j0 + cc < n) ? B[(size_t)r * ldb + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < TS; ++rr) {
+      const double a0 = As[rr][2 * ty], a1 = As[rr][2 * ty + 1];
+      const double b0 = Bs[rr][2 * tx], b1 = Bs[rr][2 * tx + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double* P = partials + (size_t)blockIdx.y * m * n;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + 2 * ty + a, j = j0 + 2 * tx + b;
+      if (i < m && j < n) P[(size_t)i * n + j] = acc[a][b];
+    }
+}
+
+__global__ void gemm_tn_reduce_kernel(int m, int n, int nchunk, bool symmetric,
+                                      const double* __restrict__ partials, double* __restrict__ C,
+                                      int ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  int i = e / n, j = e - (e / n) * n;
+  int si = i, sj = j;
+  if (symmetric && i > j) { si = j; sj = i; }
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += partials[(size_t)c * m * n + (size_t)si * n + sj];
+  C[(size_t)i * ldc + j] = s;
+}
+
+struct TnPlan {
+  int ntiles, nchunk, chunk_rows;
+};
+
+TnPlan plan_tn(int rows, int m, int n, bool symmetric) {
+  TnPlan p;
+  const int tm = (m + TS - 1) / TS, tn = (n + TS - 1) / TS;
+  p.ntiles = symmetric ? tm * (tm + 1) / 2 : tm * tn;
+  const int max_chunks = std::max(1, (rows + TS - 1) / TS);
+  int want = (kSplitTarget + p.ntiles - 1) / p.ntiles;
+  want = std::max(1, std::min(want, max_chunks));
+  int cr = (rows + want - 1) / want;
+  cr = ((cr + TS - 1) / TS) * TS;
+  p.chunk_rows = std::max(cr, TS);
+  p.nchunk = (rows + p.chunk_rows - 1) / p.chunk_rows;
+  if (p.nchunk < 1) p.nchunk = 1;
+  return p;
+}
+
+// ---- C = alpha A M + beta C -------------------------------------------------
+template <int BM, int BN>
+__global__ void __launch_bounds__(256)
+gemm_nn_kernel(int rows, int K, int n, double alpha, const double* __restrict__ A, int lda,
+               const double* __restrict__ M, int ldm, double beta, double* C, int ldc,
+               bool upper) {
+  constexpr int BK = 32;
+  constexpr int RM = BM / 16, RN = BN / 16;  // outputs per thread
+  __shared__ double As[BM][BK + 1];
+  __shared__ double Ms[BK][BN + 1];
+  const int r0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  double acc[RM][RN];
+#pragma unroll
+  for (int a = 0; a < RM; ++a)
+#pragma unroll
+    for (int b = 0; b < RN; ++b) acc[a][b] = 0.0;
+  const int k_end = upper ? min(K, j0 + BN) : K;
+  for (int k0 = 0; k0 < k_end; k0 += BK) {
+    for (int e = t; e < BM * BK; e += 256) {
+      const int rr = e / BK, kk = e - (e / BK) * BK;
+      const int r = r0 + rr, kc = k0 + kk;
+      As[rr][kk] = (r < rows && kc < K) ? A[(size_t)r * lda + kc] : 0.0;
+    }
+    for (int e = t; e < BK * BN; e += 256) {
+      const int kk = e / BN, jj = e - (e / BN) * BN;
+      const int kc = k0 + kk, j = j0 + jj;
+      Ms[kk][jj] = (kc < K && j < n) ? M[(size_t)kc * ldm + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[RM], mv[RN];
+#pragma unroll
+      for (int a = 0; a < RM; ++a) av[a] = As[ty + 16 * a][kk];
+#pragma unroll
+      for (int b = 0; b < RN; ++b) mv[b] = Ms[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+#pragma unroll
+        for (int b = 0; b < RN; ++b) acc[a][b] = fma(av[a], mv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < RM; ++a)
+#pragma unroll
+    for (int b = 0; b < RN; ++b) {
+      const int r = r0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      if (r < rows && j < n) {
+        double* c = C + (size_t)r * ldc + j;
+        *c = (beta == 0.0) ? alpha * acc[a][b] : fma(alpha, acc[a][b], beta * (*c));
+      }
+    }
+}
+
+// ---- Cholesky G = L L^T (R = L^T) and R^{-1} = (L^{-1})^T -----------------
+// Shared layout: lower triangle + diagonal of S hold L; the strict upper
+// triangle holds L^{-1} transposed (S[j][i] = Linv[i][j], i > j); dinv[i] =
+// 1/L[i][i] = Linv[i][i]. On a non-positive pivot the factorisation restarts
+// on G + s I (shifted Cholesky QR) with s growing 100x per retry, starting
+// at 1e-14 k trace(G); status = number of shifted restarts, or 1000 if the
+// last attempt still failed.
+__global__ void __launch_bounds__(1024)
+chol_inv_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ Rinv,
+                int* __restrict__ status) {
+  extern __shared__ double S[];  // k*k
+  __shared__ double dinv[kMaxBlockWidth];
+  __shared__ int bad;
+  __shared__ double trace;
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (t == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]);
+    trace = tr;
+  }
+  __syncthreads();
+  int attempt = 0;
+  for (; attempt < 4; ++attempt) {
+    const double shift = (attempt == 0) ? 0.0 : 1e-14 * k * trace * pow(100.0, attempt - 1);
+    for (int e = t; e < k * k; e += nt) {
+      const int i = e / k, j = e - (e / k) * k;
+      S[e] = (j <= i) ? G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0) : 0.0;
+    }
+    if (t == 0) bad = 0;
+    __syncthreads();
+    // right-looking Cholesky, one column at a time
+    for (int j = 0; j < k; ++j) {
+      if (t == 0) {
+        const double p = S[j * k + j];
+        if (!(p > 0.0)) {
+          if (bad == 0) bad = j + 1;
+          S[j * k + j] = 1.0;
+          dinv[j] = 1.0;
+        } else {
+          const double l = sqrt(p);
+          S[j * k + j] = l;
+          dinv[j] = 1.0 / l;
+        }
+      }
+      __syncthreads();
+      const double inv = dinv[j];
+      for (int i = j + 1 + t; i < k; i += nt) S[i * k + j] *= inv;
+      __syncthreads();
+      const int m = k - j - 1;  // trailing size
+      for (int e = t; e < m * m; e += nt) {
+        const int ii = e / m, cc = e - (e / m) * m;
+        if (cc <= ii) {
+          const int i = j + 1 + ii, c = j + 1 + cc;
+          S[i * k + c] = fma(-S[i * k + j], S[c * k + j], S[i * k + c]);
+        }
+      }
+      __syncthreads();
+    }
+    if (bad == 0) break;
+    __syncthreads();
+  }
+  // L^{-1} row by row: Linv[i][j] = -dinv[i] * sum_{c=j}^{i-1} L[i][c] Linv[c][j]
+  for (int i = 1; i < k; ++i) {
+    for (int j = t; j < i; j += nt) {
+      double s0 = S[i * k + j] * dinv[j], s1 = 0.0;
+      int c = j + 1;
+      for (; c + 1 < i; c += 2) {
+        s0 = fma(S[i * k + c], S[j * k + c], s0);
+        s1 = fma(S[i * k + c + 1], S[j * k + c + 1], s1);
+      }
+      if (c < i) s0 = fma(S[i * k + c], S[j * k + c], s0);
+      S[j * k + i] = -dinv[i] * (s0 + s1);
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < k * k; e += nt) {
+    const int i = e / k, j = e - (e / k) * k;  // Rinv[i][j], upper: j >= i
+    double v = 0.0;
+    if (j > i) v = S[i * k + j];
+    else if (j == i) v = dinv[i];
+    Rinv[e] = v;
+  }
+  if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
+}
+
+__global__ void copy2d_kernel(int rows, int cols, const double* __restrict__ in, int ld_in,
+                              double* __restrict__ out, int ld_out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e - (e / cols) * cols);
+  out[(size_t)r * ld_out + c] = in[(size_t)r * ld_in + c];
+}
+
+__global__ void gather_cols_kernel(int rows, int ncols, const double* __restrict__ in, int ld_in,
+                                   const int* __restrict__ cols, double* __restrict__ out,
+                                   int ld_out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * ncols) return;
+  const int r = (int)(e / ncols), c = (int)(e - (e / ncols) * ncols);
+  out[(size_t)r * ld_out + c] = in[(size_t)r * ld_in + cols[c]];
+}
+
+}  // namespace
+
+size_t gemm_tn_partials(int rows, int m, int n, bool symmetric) {
+  TnPlan p = plan_tn(rows, m, n, symmetric);
+  return (size_t)p.nchunk * m * n;
+}
+
+cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, const double* B,
+                           int ldb, double* C, int ldc, bool symmetric, double* partials,
+                           cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (symmetric && m != n) return cudaErrorInvalidValue;
+  TnPlan p = plan_tn(rows, m, n, symmetric);
+  dim3 grid(p.ntiles, p.nchunk);
+  gemm_tn_partial_kernel<<<grid, 256, 0, st>>>(rows, m, n, A, lda, B, ldb, symmetric,
+                                               p.chunk_rows, partials);
+  const int tot = m * n;
+  gemm_tn_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(m, n, p.nchunk, symmetric, partials,
+                                                           C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A, int lda,
+                           const double* M, int ldm, double beta, double* C, int ldc, bool upper,
+                           cudaStream_t st) {
+  if (rows <= 0 || n <= 0) return cudaSuccess;
+  const long long big_tiles = (long long)((rows + 31) / 32) * ((n + 31) / 32);
+  if (big_tiles >= 152) {
+    dim3 grid((n + 31) / 32, (rows + 31) / 32);
+    gemm_nn_kernel<32, 32><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
+                                                 upper);
+  } else {
+    dim3 grid((n + 15) / 16, (rows + 15) / 16);
+    gemm_nn_kernel<16, 16><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
+                                                 upper);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_inv(int k, const double* G, int ldg, double* Rinv, int* status,
+                            cudaStream_t st) {
+  if (k <= 0 || k > kMaxBlockWidth) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)k * k * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  chol_inv_kernel<<<1, 1024, smem, st>>>(k, G, ldg, Rinv, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, double* out, int ld_out,
+                          cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  copy2d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, in, ld_in, out, ld_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in, const int* cols,
+                               double* out, int ld_out, cudaStream_t st) {
+  const long long tot = (long long)rows * ncols;
+  if (tot <= 0) return cudaSuccess;
+  gather_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, ncols, in, ld_in, cols,
+                                                                     out, ld_out);
+  return cudaGetLastError();
+}
+
+}  // namespace scsf

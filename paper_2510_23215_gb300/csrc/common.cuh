@@ -1,0 +1,54 @@
+// Shared device/host helpers for the SCSF CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace scsf {
+
+// Largest block width k_b = k + nex accepted by the solver. The reduced
+// eigensolve keeps two k_b x k_b FP32 matrices in one CTA's shared memory.
+constexpr int kMaxBlockWidth = 160;
+
+constexpr int kGemmTile = 32;     // output tile side of the FP64 block GEMMs
+constexpr int kSplitTarget = 304; // CTAs targeted by split-K Gram launches (2 per SM)
+
+// Stencil coefficients of the 5-point operator in row-major node order.
+//   (A y)_I = d[I] y_I - we[I] y_{I+n} - we[I-n] y_{I-n} - wn[I] y_{I+1} - wn[I-1] y_{I-1}
+// we[I] is the coupling of node I to its +i neighbour (zero on the last i row),
+// wn[I] the coupling to its +j neighbour (zero on the last j column).
+struct Stencil {
+  const double* d;
+  const double* we;
+  const double* wn;
+  int n;
+};
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bump allocator over a caller-owned device workspace.
+struct Carve {
+  char* base;
+  size_t cap;
+  size_t used = 0;
+  bool ok = true;
+  Carve(void* p, size_t c) : base(static_cast<char*>(p)), cap(c) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = align256(count * sizeof(T));
+    if (used + bytes > cap) { ok = false; return nullptr; }
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+// Sizing-only twin of Carve.
+struct CarveSize {
+  size_t used = 0;
+  template <typename T>
+  void take(size_t count) { used += align256(count * sizeof(T)); }
+};
+
+}  // namespace scsf

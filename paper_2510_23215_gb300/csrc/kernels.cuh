@@ -1,0 +1,68 @@
+// Host-side launchers of the SCSF kernels (all enqueue on `st`, return the
+// launch error). Layouts: row-major blocks, column index fastest.
+#pragma once
+
+#include "common.cuh"
+
+namespace scsf {
+
+// ---- operator assembly (stencil.cu) -------------------------------------
+// Builds d/we/wn for -div(a grad u) (ax, ay) or -Lap u + V u (v), and writes
+// the Gershgorin bounds {lo, hi} to bounds[0..1] (device). `partials` holds
+// 2 * assemble_blocks(n) doubles.
+int assemble_blocks(int n);
+cudaError_t launch_assemble(int kind, int n, const double* ax, const double* ay, const double* v,
+                            double* d, double* we, double* wn, double* partials, double* bounds,
+                            cudaStream_t st);
+
+// One scaled three-term step on an N x ncols block (Alg. 1 recurrence):
+//   out = s1 * (A cur) + s2 * cur + s3 * prev       (prev may be null when s3 == 0)
+cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, const double* prev,
+                                 int ldp, double* out, int ldo, int ncols, double s1, double s2,
+                                 double s3, cudaStream_t st);
+
+// Column sums of r_j = ||(A X)_j - theta_j X_j||^2 and ||(A X)_j||^2 without
+// storing A X. partials: [resid_blocks(n)][2][ncols]; out2: [2][ncols].
+int resid_blocks(int n);
+cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
+                                  const double* theta, double* partials, double* out2,
+                                  cudaStream_t st);
+
+// ---- FP64 block BLAS (blas64.cu) ----------------------------------------
+// C[m x n] = A^T B over `rows` rows, A: rows x m (lda), B: rows x n (ldb).
+// symmetric: A == B and only the upper tiles are computed, then mirrored.
+size_t gemm_tn_partials(int rows, int m, int n, bool symmetric);
+cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, const double* B,
+                           int ldb, double* C, int ldc, bool symmetric, double* partials,
+                           cudaStream_t st);
+// C[rows x n] = alpha * A[rows x k] M[k x n] + beta * C; upper: M upper triangular.
+// C may alias nothing but itself (in-place update is safe).
+cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A, int lda,
+                           const double* M, int ldm, double beta, double* C, int ldc, bool upper,
+                           cudaStream_t st);
+// Single-CTA FP64 Cholesky G = R^T R (G: k x k) and Rinv = R^{-1} (upper, k x k, ld k).
+// status[0] != 0 on a non-positive pivot (index + 1).
+cudaError_t launch_chol_inv(int k, const double* G, int ldg, double* Rinv, int* status,
+                            cudaStream_t st);
+// out[i*ld_out + j] = in[i*ld_in + j], i < rows, j < cols.
+cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, double* out, int ld_out,
+                          cudaStream_t st);
+// Gathers columns: out[r][j] = in[r][cols[j]] (cols: device int32 [ncols]).
+cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in, const int* cols,
+                               double* out, int ld_out, cudaStream_t st);
+
+// ---- reduced eigensolve (eig.cu) ----------------------------------------
+size_t small_eigh_scratch_bytes(int k);
+cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, double* Z, int ldz,
+                              void* scratch, cudaStream_t st);
+
+// ---- random head block (rng.cu) -----------------------------------------
+cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64_t seed,
+                                 cudaStream_t st);
+
+// ---- sort (sort.cu) ------------------------------------------------------
+size_t sort_workspace_bytes(int64_t n_ops, int p0);
+cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int start,
+                        void* workspace, int32_t* perm, cudaStream_t st);
+
+}  // namespace scsf

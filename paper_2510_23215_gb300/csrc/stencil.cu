@@ -1,0 +1,240 @@
+// Operator assembly and the fused 5-point stencil kernels (FP64 path).
+//
+// Sec. 2.1 / App. D.2: the operator is the conservative central-difference
+// discretisation of -div(a grad u) (or -Lap u + V u) on the n x n interior grid
+// with Dirichlet boundaries; it is never formed as a sparse matrix. Each kernel
+// reads the three coefficient arrays d/we/wn and the block rows it needs.
+#include "kernels.cuh"
+
+namespace scsf {
+namespace {
+
+constexpr int kAsmThreads = 256;
+constexpr int kRowsPerBlock = 8;   // nodes per CTA in the stencil kernels (blockDim.y)
+constexpr int kMaxColChunks = kMaxBlockWidth / 32;
+
+__global__ void assemble_kernel(int kind, int n, const double* __restrict__ ax,
+                                const double* __restrict__ ay, const double* __restrict__ v,
+                                double* __restrict__ d, double* __restrict__ we,
+                                double* __restrict__ wn, double* __restrict__ partials) {
+  const int N = n * n;
+  const double h = 1.0 / (n + 1);
+  const double inv_h2 = 1.0 / (h * h);
+  double lo = INFINITY, hi = -INFINITY;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
+    const int i = I / n, j = I - (I / n) * n;
+    double a_w, a_e, a_s, a_n, extra;
+    if (kind == 0) {
+      a_w = ax[(size_t)i * n + j];            // face between (i-1, j) and (i, j)
+      a_e = ax[(size_t)(i + 1) * n + j];      // face between (i, j) and (i+1, j)
+      a_s = ay[(size_t)i * (n + 1) + j];      // face between (i, j-1) and (i, j)
+      a_n = ay[(size_t)i * (n + 1) + j + 1];  // face between (i, j) and (i, j+1)
+      extra = 0.0;
+    } else {
+      a_w = a_e = a_s = a_n = 1.0;
+      extra = v[I];
+    }
+    const double dI = (a_w + a_e + a_s + a_n) * inv_h2 + extra;
+    const double cE = (i < n - 1) ? a_e * inv_h2 : 0.0;
+    const double cW = (i > 0) ? a_w * inv_h2 : 0.0;
+    const double cN = (j < n - 1) ? a_n * inv_h2 : 0.0;
+    const double cS = (j > 0) ? a_s * inv_h2 : 0.0;
+    d[I] = dI;
+    we[I] = cE;
+    wn[I] = cN;
+    const double radius = cE + cW + cN + cS;
+    lo = fmin(lo, dI - radius);
+    hi = fmax(hi, dI + radius);
+  }
+  __shared__ double slo[kAsmThreads], shi[kAsmThreads];
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = slo[0];
+    partials[gridDim.x + blockIdx.x] = shi[0];
+  }
+}
+
+__global__ void bounds_reduce_kernel(const double* __restrict__ partials, int nb,
+                                     double* __restrict__ bounds) {
+  __shared__ double slo[256], shi[256];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    lo = fmin(lo, partials[b]);
+    hi = fmax(hi, partials[nb + b]);
+  }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    bounds[0] = slo[0];
+    bounds[1] = shi[0];
+  }
+}
+
+// (A y)_I for one column: y points at row I of the block (element c).
+struct NodeCoeffs {
+  double d, wE, wW, wN, wS;
+  int i, j;
+};
+
+__device__ __forceinline__ NodeCoeffs load_coeffs(const Stencil& A, int I) {
+  NodeCoeffs k;
+  const int n = A.n;
+  k.i = I / n;
+  k.j = I - k.i * n;
+  k.d = A.d[I];
+  k.wE = A.we[I];
+  k.wW = (k.i > 0) ? A.we[I - n] : 0.0;
+  k.wN = A.wn[I];
+  k.wS = (k.j > 0) ? A.wn[I - 1] : 0.0;
+  return k;
+}
+
+// Off-diagonal part sum_nb w_nb y_nb for column c of the row at `row` (ld elements per row).
+__device__ __forceinline__ double offdiag_sum(const NodeCoeffs& k, int n, const double* row,
+                                              size_t ld, int c) {
+  double acc = 0.0;
+  if (k.i < n - 1) acc = fma(k.wE, row[(size_t)n * ld + c], acc);
+  if (k.i > 0) acc = fma(k.wW, row[-(ptrdiff_t)((size_t)n * ld) + c], acc);
+  if (k.j < n - 1) acc = fma(k.wN, row[ld + c], acc);
+  if (k.j > 0) acc = fma(k.wS, row[-(ptrdiff_t)ld + c], acc);
+  return acc;
+}
+
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+cheb_step_f64_kernel(Stencil A, const double* __restrict__ cur, int ldc,
+                     const double* __restrict__ prev, int ldp, double* __restrict__ out, int ldo,
+                     int ncols, double s1, double s2, double s3) {
+  const int N = A.n * A.n;
+  const int I = blockIdx.x * kRowsPerBlock + threadIdx.y;
+  if (I >= N) return;
+  const NodeCoeffs k = load_coeffs(A, I);
+  const double diag = fma(s1, k.d, s2);
+  const double* row = cur + (size_t)I * ldc;
+  const double* prow = prev ? prev + (size_t)I * ldp : nullptr;
+  double* orow = out + (size_t)I * ldo;
+  for (int c = threadIdx.x; c < ncols; c += 32) {
+    const double acc = offdiag_sum(k, A.n, row, (size_t)ldc, c);
+    double r = fma(-s1, acc, diag * row[c]);
+    if (prow) r = fma(s3, prow[c], r);
+    orow[c] = r;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncols,
+                      const double* __restrict__ theta, double* __restrict__ partials) {
+  const int N = A.n * A.n;
+  double rr[kMaxColChunks], aa[kMaxColChunks];
+#pragma unroll
+  for (int q = 0; q < kMaxColChunks; ++q) rr[q] = aa[q] = 0.0;
+  for (int I = blockIdx.x * kRowsPerBlock + threadIdx.y; I < N; I += gridDim.x * kRowsPerBlock) {
+    const NodeCoeffs k = load_coeffs(A, I);
+    const double* row = X + (size_t)I * ldx;
+#pragma unroll
+    for (int q = 0; q < kMaxColChunks; ++q) {
+      const int c = threadIdx.x + 32 * q;
+      if (c < ncols) {
+        const double x = row[c];
+        const double ax = fma(k.d, x, -offdiag_sum(k, A.n, row, (size_t)ldx, c));
+        const double r = fma(-theta[c], x, ax);
+        rr[q] = fma(r, r, rr[q]);
+        aa[q] = fma(ax, ax, aa[q]);
+      }
+    }
+  }
+  __shared__ double s_r[kRowsPerBlock][kMaxBlockWidth];
+  __shared__ double s_a[kRowsPerBlock][kMaxBlockWidth];
+#pragma unroll
+  for (int q = 0; q < kMaxColChunks; ++q) {
+    const int c = threadIdx.x + 32 * q;
+    if (c < ncols) {
+      s_r[threadIdx.y][c] = rr[q];
+      s_a[threadIdx.y][c] = aa[q];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int c = threadIdx.x; c < ncols; c += 32) {
+      double sr = 0.0, sa = 0.0;
+      for (int y = 0; y < kRowsPerBlock; ++y) {
+        sr += s_r[y][c];
+        sa += s_a[y][c];
+      }
+      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c] = sr;
+      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c] = sa;
+    }
+  }
+}
+
+__global__ void column_partials_reduce_kernel(const double* __restrict__ partials, int nb,
+                                              int ncols, double* __restrict__ out2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ncols) return;
+  const int which = t / ncols, c = t - which * ncols;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partials[((size_t)b * 2 + which) * ncols + c];
+  out2[t] = s;
+}
+
+}  // namespace
+
+int assemble_blocks(int n) {
+  const long long N = (long long)n * n;
+  long long b = (N + kAsmThreads - 1) / kAsmThreads;
+  return (int)(b < 304 ? b : 304);
+}
+
+cudaError_t launch_assemble(int kind, int n, const double* ax, const double* ay, const double* v,
+                            double* d, double* we, double* wn, double* partials, double* bounds,
+                            cudaStream_t st) {
+  const int nb = assemble_blocks(n);
+  assemble_kernel<<<nb, kAsmThreads, 0, st>>>(kind, n, ax, ay, v, d, we, wn, partials);
+  bounds_reduce_kernel<<<1, 256, 0, st>>>(partials, nb, bounds);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, const double* prev,
+                                 int ldp, double* out, int ldo, int ncols, double s1, double s2,
+                                 double s3, cudaStream_t st) {
+  const int N = A.n * A.n;
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid((N + kRowsPerBlock - 1) / kRowsPerBlock);
+  cheb_step_f64_kernel<<<grid, block, 0, st>>>(A, cur, ldc, (s3 != 0.0) ? prev : nullptr, ldp, out,
+                                               ldo, ncols, s1, s2, s3);
+  return cudaGetLastError();
+}
+
+int resid_blocks(int n) {
+  const long long N = (long long)n * n;
+  long long b = (N + kRowsPerBlock - 1) / kRowsPerBlock;
+  return (int)(b < 304 ? b : 304);
+}
+
+cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
+                                  const double* theta, double* partials, double* out2,
+                                  cudaStream_t st) {
+  if (ncols > kMaxBlockWidth) return cudaErrorInvalidValue;
+  const int nb = resid_blocks(A.n);
+  residual_norms_kernel<<<nb, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta, partials);
+  column_partials_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
+  return cudaGetLastError();
+}
+
+}  // namespace scsf

@@ -1,0 +1,106 @@
+"""Kernel-level parity: assembly bounds, Chebyshev filter, reduced eigensolve (GPU vs oracle)."""
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as npcheb
+
+import scsf_inputs as si
+from oracle import chebyshev, operators, sturm
+from tests.gpu_util import host, need_gpu, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", ["div", "lapv"])
+def test_gershgorin_bounds(kind):
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op = si.div_a_grad_chain(33, 1, seed=2)[0] if kind == "div" else si.lap_plus_v_chain(33, 1, seed=2)[0]
+    lo, hi = scsf.assemble_bounds(to_dev([op], dev)[0])
+    rlo, rhi = operators.gershgorin_bounds(operators.assemble(op))
+    assert lo == pytest.approx(rlo, rel=1e-13, abs=1e-9 * abs(rhi))
+    assert hi == pytest.approx(rhi, rel=1e-13)
+
+
+@pytest.mark.parametrize("n,ncols,degree", [(20, 37, 1), (20, 37, 2), (33, 24, 7), (17, 120, 16),
+                                            (40, 5, 20)])
+def test_filter_matches_oracle(n, ncols, degree):
+    """Alg. 1 on a random block: GPU recurrence vs oracle recurrence (FP64)."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op = si.div_a_grad_chain(n, 1, seed=n)[0]
+    A = operators.assemble(op)
+    lo, hi = operators.gershgorin_bounds(A)
+    lam, alpha = lo + 0.001 * (hi - lo), lo + 0.05 * (hi - lo)
+    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+    X = si.gaussian_block(n * n, ncols, seed=3)
+    ref = chebyshev.chebyshev_filter(A, X, degree, lam, c, e)
+    Y = scsf.cheb_filter(to_dev([op], dev)[0], torch.as_tensor(X, device=dev), degree, lam, c, e)
+    got = host(Y)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * scale
+
+
+def test_filter_exact_eigenvector_closed_form():
+    """Laplacian sine mode v: filter(v) = C_m(t_v)/C_m(t_lambda) v (library Chebyshev values)."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, m = 24, 16
+    op = si.constant_div_a_grad(n)
+    h = 1.0 / (n + 1)
+    lam_min = 8.0 / h**2 * np.sin(np.pi * h / 2) ** 2
+    alpha, beta = 400.0, 8.0 / h**2
+    c, e = 0.5 * (alpha + beta), 0.5 * (beta - alpha)
+    modes = [(1, 1), (2, 3), (7, 7)]
+    X = np.stack([sturm.laplacian_2d_mode(n, p, q) for p, q in modes], axis=1)
+    Y = host(scsf.cheb_filter(to_dev([op], dev)[0], torch.as_tensor(X.copy(), device=dev), m,
+                              lam_min, c, e))
+    coef = np.zeros(m + 1)
+    coef[m] = 1.0
+    for col, (p, q) in enumerate(modes):
+        lv = 4.0 / h**2 * (np.sin(p * np.pi * h / 2) ** 2 + np.sin(q * np.pi * h / 2) ** 2)
+        expect = npcheb.chebval((lv - c) / e, coef) / npcheb.chebval((lam_min - c) / e, coef)
+        np.testing.assert_allclose(Y[:, col], expect * X[:, col], rtol=1e-11, atol=1e-13)
+
+
+def _random_sym(k, seed, spread=1.0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    w = np.sort(rng.uniform(-spread, spread, k)) * 100.0
+    return (Q * w) @ Q.T
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 24, 37, 120, 160])
+def test_small_eigh_random(k):
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    S = _random_sym(k, seed=k)
+    S = 0.5 * (S + S.T)
+    w, Z = scsf.small_eigh(torch.as_tensor(S, device=dev))
+    w, Z = host(w), host(Z)
+    ref = np.linalg.eigvalsh(S)
+    nrm = np.max(np.abs(ref))
+    assert np.max(np.abs(w - ref)) <= 1e-13 * nrm * max(1, k) ** 0.5
+    assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-13
+    assert np.max(np.abs(S @ Z - Z * w[None, :])) <= 1e-12 * nrm
+    assert np.all(np.diff(w) >= 0)
+
+
+def test_small_eigh_degenerate_and_near_diagonal():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(0)
+    k = 48
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    w0 = np.repeat(np.arange(1.0, 13.0), 4)  # exact 4-fold clusters
+    S = (Q * w0) @ Q.T
+    S = 0.5 * (S + S.T)
+    w, Z = scsf.small_eigh(torch.as_tensor(S, device=dev))
+    w, Z = host(w), host(Z)
+    np.testing.assert_allclose(w, w0, rtol=0, atol=1e-12 * 12)
+    assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-13
+    assert np.max(np.abs(S @ Z - Z * w[None, :])) <= 1e-12 * 12
+    D = np.diag(np.linspace(1.0, 50.0, 120)) + 1e-7 * _random_sym(120, 5)
+    D = 0.5 * (D + D.T)
+    w, Z = scsf.small_eigh(torch.as_tensor(D, device=dev))
+    np.testing.assert_allclose(host(w), np.linalg.eigvalsh(D), rtol=1e-14, atol=1e-12)

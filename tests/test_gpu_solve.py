@@ -1,0 +1,160 @@
+"""End-to-end parity of the warm-started chain solve (Alg. 3 along a sorted chain)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import scsf_inputs as si
+from oracle import chfsi, compare, dense, inertia, operators, sturm
+from oracle import sort as osort
+from tests.gpu_util import host, need_gpu, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EIG_RTOL = 1e-10   # eigenvalue relative error at residual <= 1e-8
+RES_TOL = 1e-8
+
+
+def _check_result(op, evals, resid, evecs, k, ref_vals=None, ref_vecs=None):
+    A = operators.assemble(op)
+    assert np.all(np.isfinite(evals)) and np.all(np.diff(evals) >= 0)
+    assert np.max(resid) <= RES_TOL
+    r_cpu = operators.relative_residuals(A, evecs, evals)
+    assert np.max(r_cpu) <= 1.05 * RES_TOL
+    assert compare.orthonormality_error(evecs) <= 1e-12
+    if ref_vals is not None:
+        assert compare.max_rel_eig_error(ref_vals, evals) <= EIG_RTOL
+    if ref_vecs is not None:
+        assert compare.max_cluster_angle(ref_vals, ref_vecs, evecs) <= 1e-5
+
+
+def test_poisson32_chain_matches_dense_definition():
+    """16 problems, 32 x 32, k = 20, degree 16, sorted with p0 = 8, vs dense eigh of each."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(32, 16, seed=0)
+    perm = host(scsf.sort(torch.as_tensor(np.stack([o.P for o in ops]), device=dev), p0=8))
+    ordered = [ops[i] for i in perm]
+    ev, rs, vec, stats = scsf.solve(to_dev(ordered, dev), scsf.Params(k=20, degree=16, tol=1e-8),
+                                    want_vectors=True)
+    ev, rs, vec = host(ev), host(rs), host(vec)
+    for j, op in enumerate(ordered):
+        w, V = dense.smallest_eigenpairs(operators.assemble(op), 20)
+        _check_result(op, ev[j], rs[j], vec[j], 20, w, V)
+    assert all(s["converged"] for s in stats)
+    # warm starts pay: later problems need fewer outer iterations than the head
+    assert np.mean([s["iters"] for s in stats[1:]]) < stats[0]["iters"]
+
+
+def test_laplacian_closed_form_with_degenerate_pairs():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, k = 24, 12
+    ev, rs, vec, _ = scsf.solve(to_dev([si.constant_div_a_grad(n)], dev),
+                                scsf.Params(k=k, degree=16, tol=1e-9), want_vectors=True)
+    ref = sturm.laplacian_2d_eigenvalues(n)[:k]
+    assert compare.max_rel_eig_error(ref, host(ev)[0]) <= 1e-11
+    assert compare.orthonormality_error(host(vec)[0]) <= 1e-12
+
+
+def test_separable_grid128_k100():
+    """a = a(x): the spectrum is the union of n tridiagonal spectra (library tridiagonal solver)."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, k = 128, 100
+    op = si.separable_div_a_grad(n, seed=4)
+    ev, rs, vec, stats = scsf.solve(to_dev([op], dev), scsf.Params(k=k, degree=20, tol=1e-8),
+                                    want_vectors=True)
+    vals = []
+    for d, e in sturm.separable_tridiagonals(n, op.ax[:, 0], op.P[:, 0]):
+        vals.append(sla.eigh_tridiagonal(d, e, eigvals_only=True, select="i", select_range=(0, k - 1)))
+    ref = np.sort(np.concatenate(vals))[:k]
+    assert compare.max_rel_eig_error(ref, host(ev)[0]) <= EIG_RTOL
+    assert np.max(host(rs)) <= RES_TOL
+
+
+def test_lap_plus_v_operator():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.lap_plus_v_chain(24, 3, seed=2)
+    ev, rs, vec, _ = scsf.solve(to_dev(ops, dev), scsf.Params(k=16, degree=16, tol=1e-8),
+                                want_vectors=True)
+    for j, op in enumerate(ops):
+        w, V = dense.smallest_eigenpairs(operators.assemble(op), 16)
+        _check_result(op, host(ev)[j], host(rs)[j], host(vec)[j], 16, w, V)
+
+
+def test_poisson128_full_chain_sampled():
+    """The full 200-problem, 128 x 128, k = 100, degree 20 chain as the benchmark runs it;
+    sampled problems are checked on the CPU (residuals, orthonormality, inertia, oracle ChFSI)."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, k, n_ops = 128, 100, 200
+    ops = si.div_a_grad_chain(n, n_ops, seed=1)
+    perm = host(scsf.sort(torch.as_tensor(np.stack([o.P for o in ops]), device=dev), p0=8))
+    ordered = [ops[i] for i in perm]
+    chain = scsf.Chain(scsf.Params(k=k, degree=20, tol=1e-8), n, device=dev)
+    sample = {0, 1, 57, 199}
+    kept = {}
+    iters = []
+    for j, op in enumerate(ordered):
+        ev, rs, vec, st = chain.step(to_dev([op], dev)[0], want_vectors=j in sample)
+        iters.append(st["iters"])
+        assert st["converged"]
+        assert float(rs.max()) <= RES_TOL
+        if j in sample:
+            kept[j] = (host(ev), host(rs), host(vec))
+    for j, (ev, rs, vec) in kept.items():
+        op = ordered[j]
+        _check_result(op, ev, rs, vec, k)
+        A = operators.assemble(op)
+        sigma = ev[-1] * (1 + 1e-9)
+        assert inertia.count_below(A, sigma, n) == k
+    # the oracle's own ChFSI on the head problem
+    ref = chfsi.solve_chain([ordered[0]], k=k, degree=20, tol=1e-8, head_seed=11)[0]
+    assert ref.converged
+    assert compare.max_rel_eig_error(ref.evals, kept[0][0]) <= EIG_RTOL
+    assert np.mean(iters[1:]) < iters[0]
+
+
+def test_identical_problem_warm_start_converges_in_two():
+    """Seeding the chain with an exact solution: the same problem converges in <= 2 iterations."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, k = 32, 20
+    op = si.div_a_grad_chain(n, 1, seed=9)[0]
+    dop = to_dev([op], dev)[0]
+    p = scsf.Params(k=k, degree=16, tol=1e-8)
+    chain = scsf.Chain(p, n, device=dev)
+    ev0, _, _, st0 = chain.step(dop)
+    ev1, _, _, st1 = chain.step(dop)
+    assert st0["iters"] > 2 and st1["iters"] <= 2
+    np.testing.assert_allclose(host(ev1), host(ev0), rtol=1e-10)
+    # explicit seed path: eigenvectors plus extra dense columns
+    w, V = dense.smallest_eigenpairs(operators.assemble(op), p.kb)
+    fresh = scsf.Chain(p, n, device=dev)
+    fresh.seed(torch.as_tensor(np.ascontiguousarray(V), device=dev), w.tolist())
+    ev2, _, _, st2 = fresh.step(dop)
+    assert st2["iters"] <= 2
+    assert compare.max_rel_eig_error(w[:k], host(ev2)) <= EIG_RTOL
+
+
+def test_not_converged_and_invalid_arguments():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op = to_dev(si.div_a_grad_chain(16, 1, seed=1), dev)[0]
+    chain = scsf.Chain(scsf.Params(k=10, degree=2, tol=1e-14, max_iter=1), 16, device=dev)
+    ev, rs, _, st = chain.step(op, raise_on_nonconvergence=False)
+    assert not st["converged"] and st["iters"] == 1
+    assert np.isnan(host(ev)).any()
+    with pytest.raises(scsf.ScsfError) as ei:
+        chain.step(op)
+    assert ei.value.status == scsf.ERR_NOT_CONVERGED
+    with pytest.raises(ValueError):
+        scsf.Chain(scsf.Params(k=200), 32, device=dev)
+    other = to_dev(si.div_a_grad_chain(20, 1, seed=1), dev)[0]
+    with pytest.raises(scsf.ScsfError):
+        chain.step(other)
+    with pytest.raises(ValueError):
+        scsf.solve([scsf.Operator(scsf.DIV_A_GRAD, 16, ax=op.ax.cpu(), ay=op.ay.cpu())],
+                   scsf.Params(k=4))

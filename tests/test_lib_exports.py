@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every declared symbol."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    with open(os.path.join(ROOT, "include", "scsf.h")) as f:
+        text = f.read()
+    for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(scsf_\w+)\s*\(", text, re.M):
+        names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("scsf_sort", "scsf_solve", "scsf_chain_step", "scsf_create"):
+        assert required in names
+
+
+def test_library_loads_and_exports_every_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    import ctypes
+    import paper_2510_23215_gb300 as scsf
+    lib = ctypes.CDLL(scsf.lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(scsf.EXPORTED_SYMBOLS) <= declared_functions()
+    L = scsf.library()
+    assert L.scsf_version() >= 100
+    assert L.scsf_max_block_width() == 160
+
+
+def test_workspace_queries_without_gpu():
+    import ctypes
+    import paper_2510_23215_gb300 as scsf
+    L = scsf.library()
+    p = scsf.Params(k=100, degree=20)._c()
+    ws = L.scsf_solve_workspace_size(ctypes.byref(p), 128)
+    assert ws >= 4 * 128 * 128 * 120 * 8
+    too_big = scsf.Params(k=200)._c()
+    assert L.scsf_solve_workspace_size(ctypes.byref(too_big), 128) == 0
+    assert L.scsf_sort_workspace_size(200, 8) >= 200 * 8 * 8 * 16
+
+
+def test_context_creation_fails_loudly_without_gpu():
+    import torch
+    import paper_2510_23215_gb300 as scsf
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError):
+        scsf.Context(0)
