@@ -8,9 +8,13 @@
 //   2. Ogita-Aishima iterative refinement in FP64 (X' = X + X E with
 //      R = I - X^T X, S = X^T G X, lambda_i = s_ii/(1 - r_ii), E_ij =
 //      (s_ij + lambda_j r_ij)/(lambda_j - lambda_i), or r_ij/2 for pairs closer
-//      than delta = 2(||S - D|| + ||G|| ||R||)); each step squares the error.
-//      The k^3 products run on the FP64 block kernels spread over all SMs;
-//   3. ascending sort of the pairs.
+//      than delta = max(2(||S - D|| + ||G|| ||R||), 3e-3 ||G||)); each step squares
+//      the error. The k^3 products run on the FP64 block kernels spread over all SMs;
+//   3. exact FP64 Jacobi rotations for the pairs left coupled in step 2 (close
+//      pairs, where the first-order update does not converge from FP32 accuracy);
+//      only significant off-diagonal entries rotate, so this is one scan when
+//      nothing is left;
+//   4. ascending sort of the pairs.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -19,6 +23,7 @@ namespace scsf {
 namespace {
 
 constexpr int kOaSteps = 3;
+constexpr double kClusterFloor = 3e-3;  // relative gap below which pairs go to FP64 Jacobi
 constexpr int kJacobiSweeps = 30;
 
 // Pair (p < q) handled by slot `pr` in round `round` of the circle method over
@@ -73,8 +78,10 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
         so += red_off[w];
         sa += red_all[w];
       }
-      // converged to FP32 resolution, or no longer improving
-      stop = (so <= 1e-12f * sa || so > 0.25f * prev_off) ? 1 : 0;
+      // converged to FP32 resolution, or stalled at the rounding floor (Jacobi converges
+      // linearly at first, so a stall only counts once the off-diagonal part is tiny).
+      // The refinement's cluster threshold scales with this residue, so it must be small.
+      stop = (so <= 1e-13f * sa || (so < 1e-10f * sa && so > 0.5f * prev_off)) ? 1 : 0;
       prev_off = so;
     }
     __syncthreads();
@@ -136,7 +143,7 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
 // P = Z^T S Z, Q = Z^T Z (k x k, compact); writes E (k x k) and lam (k).
 __global__ void __launch_bounds__(1024)
 oa_update_kernel(int k, const double* __restrict__ P, const double* __restrict__ Q,
-                 double* __restrict__ E, double* __restrict__ lam) {
+                 double* __restrict__ E, double* __restrict__ lam, double cluster_floor) {
   __shared__ double s_lam[kMaxBlockWidth];
   __shared__ double red[3][32];
   __shared__ double delta;
@@ -170,7 +177,9 @@ oa_update_kernel(int k, const double* __restrict__ P, const double* __restrict__
       b += red[1][w];
       c = fmax(c, red[2][w]);
     }
-    delta = 2.0 * (sqrt(a) + c * sqrt(b));
+    // pairs closer than cluster_floor * ||S|| are left to the FP64 Jacobi pass:
+    // the first-order update only converges when the error is below gap/||S||
+    delta = fmax(2.0 * (sqrt(a) + c * sqrt(b)), cluster_floor * c);
   }
   __syncthreads();
   const double dl = delta;
@@ -181,6 +190,97 @@ oa_update_kernel(int k, const double* __restrict__ P, const double* __restrict__
     E[e] = (i != j && fabs(gap) > dl) ? (P[e] + s_lam[j] * r) / gap : 0.5 * r;
   }
   for (int i = t; i < k; i += nt) lam[i] = s_lam[i];
+}
+
+// Exact FP64 Jacobi on P = Z^T S Z after the refinement, for the pairs it left
+// coupled (clusters closer than the refinement's floor). Only rotations with
+// |P_pq| > max(1e-14 |P_pp - P_qq|, 1e-15 ||S||) are applied, so a resolved P
+// costs one scan. Rotations are applied to P (shared memory) and to the
+// columns of Z (global). Writes lam = diag(P).
+__global__ void __launch_bounds__(1024)
+jacobi_f64_cleanup_kernel(int k, const double* __restrict__ Pin, double* __restrict__ Z,
+                          double* __restrict__ lam, int max_sweeps) {
+  extern __shared__ double P[];  // k*k
+  __shared__ double cs[kMaxBlockWidth + 1], sn[kMaxBlockWidth + 1];
+  __shared__ int active[kMaxBlockWidth + 1];
+  __shared__ int nsig;
+  __shared__ double nrm;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < k * k; e += nt) P[e] = Pin[e];
+  if (t == 0) {
+    double m = 0.0;
+    for (int i = 0; i < k; ++i) m = fmax(m, fabs(Pin[i * k + i]));
+    nrm = m;
+  }
+  __syncthreads();
+  const int kp = (k + 1) & ~1;
+  const int npairs = kp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (t == 0) nsig = 0;
+    __syncthreads();
+    int local = 0;
+    for (int e = t; e < k * k; e += nt) {
+      const int i = e / k, j = e - (e / k) * k;
+      if (j > i) {
+        const double apq = fabs(P[e]);
+        if (apq > fmax(1e-14 * fabs(P[i * k + i] - P[j * k + j]), 1e-15 * nrm)) ++local;
+      }
+    }
+    if (local) atomicAdd(&nsig, local);
+    __syncthreads();
+    if (nsig == 0) break;
+    for (int round = 0; round < kp - 1; ++round) {
+      if (t < npairs) {
+        int p, q;
+        circle_pair(t, round, kp, p, q);
+        double c = 1.0, s = 0.0;
+        int act = 0;
+        if (q < k) {
+          const double apq = P[p * k + q];
+          const double app = P[p * k + p], aqq = P[q * k + q];
+          if (fabs(apq) > fmax(1e-14 * fabs(app - aqq), 1e-15 * nrm)) {
+            const double theta = (aqq - app) / (2.0 * apq);
+            const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(tt * tt + 1.0);
+            s = tt * c;
+            act = 1;
+          }
+        }
+        cs[p] = c;
+        sn[p] = s;
+        active[p] = act;
+      }
+      __syncthreads();
+      for (int e = t; e < npairs * k; e += nt) {
+        const int pr = e / k, col = e - (e / k) * k;
+        int p, q;
+        circle_pair(pr, round, kp, p, q);
+        if (q < k && active[p]) {
+          const double c = cs[p], s = sn[p];
+          const double ap = P[p * k + col], aq = P[q * k + col];
+          P[p * k + col] = c * ap - s * aq;
+          P[q * k + col] = s * ap + c * aq;
+        }
+      }
+      __syncthreads();
+      for (int e = t; e < npairs * k; e += nt) {
+        const int pr = e / k, row = e - (e / k) * k;
+        int p, q;
+        circle_pair(pr, round, kp, p, q);
+        if (q < k && active[p]) {
+          const double c = cs[p], s = sn[p];
+          const double ap = P[row * k + p], aq = P[row * k + q];
+          P[row * k + p] = c * ap - s * aq;
+          P[row * k + q] = s * ap + c * aq;
+          const double zp = Z[row * k + p], zq = Z[row * k + q];
+          Z[row * k + p] = c * zp - s * zq;
+          Z[row * k + q] = s * zp + c * zq;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = t; i < k; i += nt) lam[i] = P[i * k + i];
 }
 
 // S_out = (S + S^T)/2 (compact k x k): the projected matrix is symmetric only up to rounding.
@@ -278,7 +378,7 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
       return e;
     if ((e = launch_gemm_tn(k, k, k, Z, k, Z, k, w.Q, k, true, w.partials, st)) != cudaSuccess)
       return e;
-    oa_update_kernel<<<1, 1024, 0, st>>>(k, w.P, w.Q, w.E, w.lam);
+    oa_update_kernel<<<1, 1024, 0, st>>>(k, w.P, w.Q, w.E, w.lam, kClusterFloor);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Z2 = Z + Z E
     if ((e = launch_copy2d(k, k, Z, k, Z2, k, st)) != cudaSuccess) return e;
@@ -286,6 +386,18 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
       return e;
     std::swap(Z, Z2);
   }
+  // exact FP64 rotations for the pairs the refinement treated as clusters
+  if ((e = launch_gemm_nn(k, k, k, 1.0, w.S, k, Z, k, 0.0, w.T, k, false, st)) != cudaSuccess)
+    return e;
+  if ((e = launch_gemm_tn(k, k, k, Z, k, w.T, k, w.P, k, false, w.partials, st)) != cudaSuccess)
+    return e;
+  symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, w.P, k, w.Q);
+  const size_t smem64 = (size_t)k * k * sizeof(double);
+  if ((e = cudaFuncSetAttribute(jacobi_f64_cleanup_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64)) != cudaSuccess)
+    return e;
+  jacobi_f64_cleanup_kernel<<<1, 1024, smem64, st>>>(k, w.Q, Z, w.lam, 6);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, Z, evals, Zout, ldz);
   return cudaGetLastError();
 }

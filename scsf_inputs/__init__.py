@@ -114,6 +114,14 @@ def div_a_grad_chain(n: int, n_ops: int, seed: int, M: int = 8) -> List[DivAGrad
     return [_div_a_grad_from_xi(n, mode_coefficients(rng, M)) for _ in range(n_ops)]
 
 
+def perturbed_div_a_grad_chain(n: int, n_ops: int, seed: int, eps: float, M: int = 8) -> List[DivAGradOp]:
+    """Operators whose mode coefficients are xi0 + eps * xi_i: a family of similar
+    problems around one base field (the shape of the paper's perturbation study)."""
+    rng = np.random.default_rng(seed)
+    xi0 = mode_coefficients(rng, M)
+    return [_div_a_grad_from_xi(n, xi0 + eps * mode_coefficients(rng, M)) for _ in range(n_ops)]
+
+
 def lap_plus_v_chain(n: int, n_ops: int, seed: int, M: int = 12,
                      amplitude: float = 10.0) -> List[LapPlusVOp]:
     """n_ops operators -Lap u + V u, V = amplitude * f, f with M x M modes."""
