@@ -1,0 +1,347 @@
+"""Benchmark: eigenpairs/s of the SCSF hot path (truncated-FFT sort + warm-started
+Chebyshev filtered subspace iteration) on GB300, at relative residual <= 1e-8.
+
+One step = the whole path over one batch: sort 200 synthetic -div(a grad u)
+operators on a 128 x 128 grid (p0 = 8), then solve them in sorted order as one
+warm-started chain for the k = 100 smallest eigenpairs (degree 20, tol 1e-8).
+Each rank runs its own batch (weak scaling, no data-path collective).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scsf_inputs as si  # noqa: E402
+
+METRIC = "eigenpairs/s at rel. residual <=1e-8 (SCSF sort + warm-started ChFSI chain)"
+UNIT = "eigenpairs/s"
+WORKLOAD = dict(name="poisson128_k100", n=128, n_ops=200, k=100, degree=20, p0=8, tol=1e-8, seed=1)
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA core) rate: 152 SMs x 2 FMA/clk x 2 flop x ~2.06 GHz
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_ops(rank: int):
+    w = WORKLOAD
+    return si.div_a_grad_chain(w["n"], w["n_ops"], seed=w["seed"] + 1000 * rank)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_23215_gb300 as scsf
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the SCSF library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scsf.library()  # fails loudly when the extension is missing
+    w = WORKLOAD
+    n, k, n_ops = w["n"], w["k"], w["n_ops"]
+    params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank)
+    ops = _workload_ops(rank)
+    # host copies (pinned) for the end-to-end leg; device copies resident for the kernel leg
+    h_fields = torch.from_numpy(np.stack([o.P for o in ops])).pin_memory()
+    h_ax = torch.from_numpy(np.stack([o.ax for o in ops])).pin_memory()
+    h_ay = torch.from_numpy(np.stack([o.ay for o in ops])).pin_memory()
+    d_fields, d_ax, d_ay = h_fields.to(dev), h_ax.to(dev), h_ay.to(dev)
+    ctx = scsf.Context(local, torch.cuda.current_stream(dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    h_evals = torch.empty((n_ops, k), dtype=torch.float64).pin_memory()
+    h_resid = torch.empty((n_ops, k), dtype=torch.float64).pin_memory()
+
+    def step(fields, ax, ay):
+        perm = scsf.sort(fields, p0=w["p0"], start=0, ctx=ctx).cpu().tolist()
+        dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i]) for i in perm]
+        ev, rs, _, stats = scsf.solve(dops, params, ctx=ctx)
+        return ev, rs, stats
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(d_fields, d_ax, d_ay)
+    barrier()
+
+    ctx.set_timing(True)
+    st = torch.cuda.current_stream(dev)
+    times, all_stats, good = [], [], 0
+    launches0 = scsf.launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ev, rs, stats = step(d_fields, d_ax, d_ay)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+            all_stats.extend(stats)
+            good += int((rs <= w["tol"]).sum().item())
+    launches = scsf.launch_count() - launches0
+    ctx.set_timing(False)
+    clocks = clk.summary()
+    total_ms = sum(times)
+
+    # end to end through the public API with host buffers
+    e2e_times = []
+    h2d = (h_fields.numel() + h_ax.numel() + h_ay.numel()) * 8
+    d2h = 2 * n_ops * k * 8
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        f = h_fields.to(dev, non_blocking=True)
+        a = h_ax.to(dev, non_blocking=True)
+        b = h_ay.to(dev, non_blocking=True)
+        ev, rs, _ = step(f, a, b)
+        h_evals.copy_(ev, non_blocking=True)
+        h_resid.copy_(rs, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(e0.elapsed_time(e1))
+
+    t_max = torch.tensor([total_ms, sum(e2e_times)], dtype=torch.float64, device=dev)
+    good_t = torch.tensor([float(good)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(good_t, op=dist.ReduceOp.SUM)
+    total_ms, e2e_ms = float(t_max[0]), float(t_max[1])
+    pairs = float(good_t[0])
+    value = pairs / (total_ms * 1e-3)
+    e2e_value = pairs / (e2e_ms * 1e-3)
+
+    # live per-kernel rooflines from the CUDA-event phase timings of the timed steps
+    filt_ms = sum(s["t_filter_ms"] for s in all_stats)
+    filt_launch = sum(s["filter_steps"] for s in all_stats)
+    filt_elems = sum(s["filter_elems"] for s in all_stats)
+    rot_ms = sum(s["t_rot_ms"] for s in all_stats)
+    rot_launch = sum(s["rot_launches"] for s in all_stats)
+    rot_flops = sum(s["rot_flops"] for s in all_stats)
+    phase_ms = {p: sum(s[f"t_{p}_ms"] for s in all_stats) for p in
+                ("filter", "orth", "rr", "eig", "rot", "resid")}
+    peaks, peak_kind = _measured_peaks()
+    fp64_peak = FP64_PEAK_TFLOPS
+    # cheb step: 13 flop per (node, column) (4 neighbour FMA, centre FMA + mul, recurrence FMA)
+    filt_avg_s = filt_ms * 1e-3 / max(filt_launch, 1)
+    filt_flops_launch = 13.0 * filt_elems / max(filt_launch, 1)
+    filt_bytes_launch = 24.0 * filt_elems / max(filt_launch, 1)
+    rot_avg_s = rot_ms * 1e-3 / max(rot_launch, 1)
+    rot_flops_launch = rot_flops / max(rot_launch, 1)
+    kernels = {
+        "cheb_step_f64": {
+            "bound": "alu", "launches": filt_launch, "avg_us": filt_avg_s * 1e6,
+            "achieved": filt_flops_launch / filt_avg_s / 1e12 if filt_avg_s else None,
+            "peak": fp64_peak, "unit": "TFLOP/s",
+            "hbm_gbs_equiv": filt_bytes_launch / filt_avg_s / 1e9 if filt_avg_s else None},
+        "gemm_nn_f64 (rotation X = Q Z)": {
+            "bound": "alu", "launches": rot_launch, "avg_us": rot_avg_s * 1e6,
+            "achieved": rot_flops_launch / rot_avg_s / 1e12 if rot_avg_s else None,
+            "peak": fp64_peak, "unit": "TFLOP/s"},
+    }
+    dom = kernels["cheb_step_f64"]
+    roofline = {"bound": "alu", "kernel": "cheb_step_f64", "achieved": dom["achieved"],
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (dom["achieved"] / fp64_peak) if dom["achieved"] else None,
+                "traffic": None,
+                "peak_source": "FP64 ALU rate derived from unit counts and clocks (not in MEASURED_PEAKS.json)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ops, args.cpu_sample_ops)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "grid": f"{n}x{n}", "N": n * n, "n_ops_per_gpu": n_ops,
+                   "k": k, "block_width": params.kb, "degree": w["degree"], "p0": w["p0"],
+                   "tol": w["tol"], "form": "plain FP64 (sort + chain solve)",
+                   "field_law": "a = exp(0.5 f/8), f = sum of 8x8 cosine modes, N(0,1) coefficients",
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": f"replicas over chains x{ws}"},
+        "eigenpairs_per_step": pairs / args.steps / ws,
+        "iters_per_op_mean": float(np.mean([s["iters"] for s in all_stats])),
+        "phase_ms_per_step": {p: v / args.steps for p, v in phase_ms.items()},
+        "roofline": roofline,
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "peaks_source": peak_kind,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(ops, sample_ops: int):
+    """The CPU oracle as it stands (numpy FP64, Householder-QR ChFSI) on a bounded sample:
+    the sort of the whole batch plus the chain solve of its first `sample_ops` problems."""
+    from oracle import chfsi
+    from oracle import sort as osort
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    perm, _ = osort.scsf_sort(np.stack([o.P for o in ops]), w["p0"], 0)
+    t_sort = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = chfsi.solve_chain([ops[i] for i in perm[:sample_ops]], k=w["k"], degree=w["degree"],
+                            tol=w["tol"], head_seed=3, keep_vectors=False)
+    t_solve = time.perf_counter() - t0
+    pairs = sum(int(np.sum(r.resid <= w["tol"])) for r in res)
+    t = t_solve + t_sort * sample_ops / len(ops)
+    return {"value": pairs / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"sort of all {len(ops)} problems (prorated) + chain solve of the first "
+                      f"{sample_ops} sorted problem(s); numpy/LAPACK default thread pool",
+            "seconds": t_sort + t_solve, "iters": [r.iters for r in res]}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    ops = _workload_ops(0)
+    vals, secs = [], []
+    cb = None
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(ops, args.cpu_sample_ops)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    value = float(np.mean(vals))
+    w = WORKLOAD
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "grid": f"{w['n']}x{w['n']}", "k": w["k"],
+                   "degree": w["degree"], "p0": w["p0"], "tol": w["tol"],
+                   "form": "CPU FP64 oracle (Householder-QR ChFSI)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cb["cores"],
+                         "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample-ops", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-ops", type=int, default=None,
+                    help="problems per batch (default 200; smaller only for profiler captures)")
+    args = ap.parse_args()
+    if args.n_ops is not None:
+        WORKLOAD["n_ops"] = args.n_ops
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -119,7 +119,24 @@ typedef struct {
   int locked;            /* pairs locked at exit                             */
   double flops_fp64;     /* algorithmic FP64 flops issued                    */
   double filter_bytes;   /* algorithmic filter bytes (3 blocks per step)     */
+  double filter_elems;   /* sum over filter steps of N * active columns      */
+  double rot_flops;      /* algorithmic flops of the block rotations X = Q Z */
+  int rot_launches;      /* block-rotation GEMM launches                     */
+  int launches;          /* kernels launched by this call                    */
+  /* Per-phase device time in ms (CUDA events on the context stream), filled
+   * only after scsf_set_timing(ctx, 1); zero otherwise. */
+  double t_filter_ms;    /* Alg. 3 line 3: Chebyshev filter                  */
+  double t_orth_ms;      /* line 4: deflation + Cholesky QR                  */
+  double t_rr_ms;        /* line 5: A Q and Q^T A Q                          */
+  double t_eig_ms;       /* line 6: reduced eigensolve                       */
+  double t_rot_ms;       /* line 6: rotation X = Q Z (one GEMM launch)       */
+  double t_resid_ms;     /* line 7: residual norms                           */
 } scsf_stats;
+
+/* Enables (1) or disables (0) per-phase CUDA-event timing in scsf_stats. */
+scsf_status scsf_set_timing(scsf_ctx* ctx, int enable);
+/* Number of kernels this library has launched in this process so far. */
+long long scsf_launch_count(void);
 
 /* Largest block width (k + nex) the solver accepts. */
 int scsf_max_block_width(void);

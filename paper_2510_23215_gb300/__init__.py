@@ -24,7 +24,7 @@ import torch
 __all__ = [
     "ScsfError", "Operator", "Params", "Context", "Chain", "library", "lib_path",
     "sort", "solve", "cheb_filter", "assemble_bounds", "small_eigh", "block_width",
-    "FP64", "MIXED", "DIV_A_GRAD", "LAP_PLUS_V", "EXPORTED_SYMBOLS",
+    "FP64", "MIXED", "DIV_A_GRAD", "LAP_PLUS_V", "EXPORTED_SYMBOLS", "launch_count",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,7 +39,7 @@ EXPORTED_SYMBOLS = [
     "scsf_sort_workspace_size", "scsf_sort", "scsf_max_block_width",
     "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
-    "scsf_small_eigh_scratch", "scsf_small_eigh",
+    "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
 ]
 
 
@@ -63,7 +63,12 @@ class _CParams(ctypes.Structure):
 class _CStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("filter_steps", ctypes.c_int), ("locked", ctypes.c_int),
-                ("flops_fp64", ctypes.c_double), ("filter_bytes", ctypes.c_double)]
+                ("flops_fp64", ctypes.c_double), ("filter_bytes", ctypes.c_double),
+                ("filter_elems", ctypes.c_double), ("rot_flops", ctypes.c_double),
+                ("rot_launches", ctypes.c_int), ("launches", ctypes.c_int),
+                ("t_filter_ms", ctypes.c_double), ("t_orth_ms", ctypes.c_double),
+                ("t_rr_ms", ctypes.c_double), ("t_eig_ms", ctypes.c_double),
+                ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -103,6 +108,10 @@ def library() -> ctypes.CDLL:
     L.scsf_small_eigh_scratch.argtypes = [i32]
     L.scsf_small_eigh_scratch.restype = sz
     L.scsf_small_eigh.argtypes = [vp, vp, i32, vp, vp, vp, sz]
+    L.scsf_set_timing.argtypes = [vp, i32]
+    L.scsf_set_timing.restype = ctypes.c_int
+    L.scsf_launch_count.argtypes = []
+    L.scsf_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED_SYMBOLS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int or name in (
@@ -212,6 +221,10 @@ class Context:
     def handle(self):
         return self._h
 
+    def set_timing(self, enable: bool = True):
+        """Per-phase CUDA-event timing in the returned stats (adds event records, no syncs)."""
+        self.check(library().scsf_set_timing(self._h, 1 if enable else 0))
+
     def check(self, status: int):
         if status != OK:
             msg = library().scsf_last_error(self._h).decode(errors="replace")
@@ -263,8 +276,14 @@ def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] =
 
 
 def _stats_dict(s: _CStats) -> dict:
-    return {"iters": s.iters, "converged": bool(s.converged), "filter_steps": s.filter_steps,
-            "locked": s.locked, "flops_fp64": s.flops_fp64, "filter_bytes": s.filter_bytes}
+    out = {name: getattr(s, name) for name, _ in _CStats._fields_}
+    out["converged"] = bool(s.converged)
+    return out
+
+
+def launch_count() -> int:
+    """Kernels launched by libscsf.so in this process so far."""
+    return int(library().scsf_launch_count())
 
 
 class Chain:

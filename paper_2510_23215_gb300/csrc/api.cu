@@ -6,6 +6,7 @@
 // host traffic per outer iteration is the Ritz values and residual norms of
 // the active block (2-3 k_b doubles), which decide locking and termination.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,7 +25,14 @@ struct scsf_ctx {
   std::string err;
   double* pinned = nullptr;  // host staging
   size_t pinned_count = 0;
+  bool timing = false;
+  cudaEvent_t ev[7] = {};
 };
+
+namespace scsf {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace scsf
 
 namespace {
 
@@ -154,6 +162,16 @@ struct scsf_chain {
 extern "C" {
 
 int scsf_version(void) { return 100; }
+long long scsf_launch_count(void) { return scsf::g_launches.load(); }
+
+scsf_status scsf_set_timing(scsf_ctx* ctx, int enable) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (enable && !ctx->ev[0])
+    for (auto& e : ctx->ev) SCSF_CUDA(ctx, cudaEventCreate(&e));
+  ctx->timing = enable != 0;
+  return SCSF_OK;
+}
 int scsf_max_block_width(void) { return kMaxBlockWidth; }
 
 scsf_status scsf_create(scsf_ctx** out, int device, void* cuda_stream) {
@@ -182,6 +200,8 @@ scsf_status scsf_create(scsf_ctx** out, int device, void* cuda_stream) {
 void scsf_destroy(scsf_ctx* ctx) {
   if (!ctx) return;
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -302,8 +322,14 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
 
   std::vector<double> locked_val, locked_res;
   std::vector<double> theta_h(kb), r_h(kb);
-  int nl = 0, it = 0, filter_steps = 0;
-  double flops = 0.0, fbytes = 0.0;
+  int nl = 0, it = 0, filter_steps = 0, rot_launches = 0;
+  double flops = 0.0, fbytes = 0.0, felems = 0.0, rot_flops = 0.0;
+  double tms[6] = {0, 0, 0, 0, 0, 0};
+  const long long launches0 = scsf_launch_count();
+  const bool timing = ctx->timing;
+  auto mark = [&](int i) -> cudaError_t {
+    return timing ? cudaEventRecord(ctx->ev[i], st) : cudaSuccess;
+  };
   bool converged = false;
   for (it = 1; it <= ch->p.max_iter; ++it) {
     const int ka = kb - nl;
@@ -314,8 +340,11 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     double* bufs[3] = {b.B0, b.B1, b.B2};
     const int lds[3] = {kb, kb, kb};
     int which = 0;
+    SCSF_CUDA(ctx, mark(0));
     SCSF_CUDA(ctx, run_filter(A, b.V + nl, kb, ka, m, lam, c, e, bufs, lds, &which, st));
+    SCSF_CUDA(ctx, mark(1));
     filter_steps += m;
+    felems += (double)m * N * ka;
     fbytes += (double)m * N * ka * 24.0;
     flops += (double)m * N * ka * 14.0;
     double* Y = bufs[which];
@@ -336,14 +365,21 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       std::swap(Y, F1);
       flops += 2.0 * N * ka * ka;
     }
+    SCSF_CUDA(ctx, mark(2));
     // line 5: Rayleigh quotient G = Q^T A Q on the active columns
     SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
     SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+    SCSF_CUDA(ctx, mark(3));
     // line 6: reduced eigenproblem and rotation back
     SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+    SCSF_CUDA(ctx, mark(4));
     SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
+    SCSF_CUDA(ctx, mark(5));
+    rot_launches += 1;
+    rot_flops += 2.0 * N * ka * ka;
     // line 7: residuals of the new Ritz pairs (App. D.5), then lock a converged prefix
     SCSF_CUDA(ctx, launch_residual_norms(A, b.V + nl, kb, ka, b.theta, b.res_partials, b.res2, st));
+    SCSF_CUDA(ctx, mark(6));
     flops += (double)N * ka * (2.0 * ka * 2 + 12.0) + 2.0 * N * ka * ka;
     SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, ka * sizeof(double), cudaMemcpyDeviceToHost, st));
     SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * ka * sizeof(double),
@@ -351,6 +387,13 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, cudaMemcpyAsync(h + 3 * kMaxBlockWidth, b.status, 2 * sizeof(int),
                                    cudaMemcpyDeviceToHost, st));
     SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (timing) {
+      for (int i = 0; i < 6; ++i) {
+        float ms = 0.f;
+        SCSF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        tms[i] += ms;
+      }
+    }
     int chol_status[2];
     std::memcpy(chol_status, h + 3 * kMaxBlockWidth, sizeof(chol_status));
     if (chol_status[0] >= 1000 || chol_status[1] >= 1000)
@@ -418,6 +461,16 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     stats->locked = nl;
     stats->flops_fp64 = flops;
     stats->filter_bytes = fbytes;
+    stats->filter_elems = felems;
+    stats->rot_flops = rot_flops;
+    stats->rot_launches = rot_launches;
+    stats->launches = (int)(scsf_launch_count() - launches0);
+    stats->t_filter_ms = tms[0];
+    stats->t_orth_ms = tms[1];
+    stats->t_rr_ms = tms[2];
+    stats->t_eig_ms = tms[3];
+    stats->t_rot_ms = tms[4];
+    stats->t_resid_ms = tms[5];
   }
   if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
   return SCSF_OK;

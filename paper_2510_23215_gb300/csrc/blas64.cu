@@ -281,9 +281,11 @@ cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, con
   dim3 grid(p.ntiles, p.nchunk);
   gemm_tn_partial_kernel<<<grid, 256, 0, st>>>(rows, m, n, A, lda, B, ldb, symmetric,
                                                p.chunk_rows, partials);
+  note_launch();
   const int tot = m * n;
   gemm_tn_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(m, n, p.nchunk, symmetric, partials,
                                                            C, ldc);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -296,10 +298,12 @@ cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A
     dim3 grid((n + 31) / 32, (rows + 31) / 32);
     gemm_nn_kernel<32, 32><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
                                                  upper);
+  note_launch();
   } else {
     dim3 grid((n + 15) / 16, (rows + 15) / 16);
     gemm_nn_kernel<16, 16><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
                                                  upper);
+  note_launch();
   }
   return cudaGetLastError();
 }
@@ -312,6 +316,7 @@ cudaError_t launch_chol_inv(int k, const double* G, int ldg, double* Rinv, int* 
                                        (int)smem);
   if (e != cudaSuccess) return e;
   chol_inv_kernel<<<1, 1024, smem, st>>>(k, G, ldg, Rinv, status);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -320,6 +325,7 @@ cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, doubl
   const long long tot = (long long)rows * cols;
   if (tot <= 0) return cudaSuccess;
   copy2d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, in, ld_in, out, ld_out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -329,6 +335,7 @@ cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in,
   if (tot <= 0) return cudaSuccess;
   gather_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, ncols, in, ld_in, cols,
                                                                      out, ld_out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -25,6 +25,9 @@ struct Stencil {
   int n;
 };
 
+// Process-wide count of kernels this library has launched (for benchmarks).
+void note_launch();
+
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Bump allocator over a caller-owned device workspace.

@@ -361,12 +361,14 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
   if (!c.ok) return cudaErrorInvalidValue;
   cudaError_t e;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, S, lds, w.S);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = 2 * (size_t)k * k * sizeof(float);
   if ((e = cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
     return e;
   jacobi_f32_kernel<<<1, 1024, smem, st>>>(k, w.S, w.Z, kJacobiSweeps);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   double* Z = w.Z;
   double* Z2 = w.Z2;
@@ -379,6 +381,7 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
     if ((e = launch_gemm_tn(k, k, k, Z, k, Z, k, w.Q, k, true, w.partials, st)) != cudaSuccess)
       return e;
     oa_update_kernel<<<1, 1024, 0, st>>>(k, w.P, w.Q, w.E, w.lam, kClusterFloor);
+  note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Z2 = Z + Z E
     if ((e = launch_copy2d(k, k, Z, k, Z2, k, st)) != cudaSuccess) return e;
@@ -392,13 +395,16 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
   if ((e = launch_gemm_tn(k, k, k, Z, k, w.T, k, w.P, k, false, w.partials, st)) != cudaSuccess)
     return e;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, w.P, k, w.Q);
+  note_launch();
   const size_t smem64 = (size_t)k * k * sizeof(double);
   if ((e = cudaFuncSetAttribute(jacobi_f64_cleanup_kernel,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64)) != cudaSuccess)
     return e;
   jacobi_f64_cleanup_kernel<<<1, 1024, smem64, st>>>(k, w.Q, Z, w.lam, 6);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, Z, evals, Zout, ldz);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64
   const long long pairs = ((long long)rows * cols + 1) / 2;
   if (pairs <= 0) return cudaSuccess;
   philox_normal_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(out, rows, cols, ld, seed);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -157,10 +157,12 @@ cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int 
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dft_features_kernel<<<(unsigned)n_ops, kFeatThreads, smem, st>>>(fields, p, p0, feats);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int flen = 2 * p0 * p0;
   greedy_chain_kernel<<<1, kChainThreads, flen * sizeof(double), st>>>(feats, (int)n_ops, flen,
                                                                        start, visited, perm);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -206,7 +206,9 @@ cudaError_t launch_assemble(int kind, int n, const double* ax, const double* ay,
                             cudaStream_t st) {
   const int nb = assemble_blocks(n);
   assemble_kernel<<<nb, kAsmThreads, 0, st>>>(kind, n, ax, ay, v, d, we, wn, partials);
+  note_launch();
   bounds_reduce_kernel<<<1, 256, 0, st>>>(partials, nb, bounds);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -218,6 +220,7 @@ cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, c
   dim3 grid((N + kRowsPerBlock - 1) / kRowsPerBlock);
   cheb_step_f64_kernel<<<grid, block, 0, st>>>(A, cur, ldc, (s3 != 0.0) ? prev : nullptr, ldp, out,
                                                ldo, ncols, s1, s2, s3);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -233,7 +236,9 @@ cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, in
   if (ncols > kMaxBlockWidth) return cudaErrorInvalidValue;
   const int nb = resid_blocks(A.n);
   residual_norms_kernel<<<nb, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta, partials);
+  note_launch();
   column_partials_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
+  note_launch();
   return cudaGetLastError();
 }
 
