@@ -79,6 +79,24 @@ size_t scsf_sort_workspace_size(int64_t n_ops, int p0);
 scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
                       int start, void* workspace, size_t workspace_bytes, int32_t* perm_out);
 
+/* scsf_sort without a caller workspace, for callers that cannot allocate device
+ * memory where they sort (a host framework that owns all device memory through
+ * its own fixed pool, or a latency-critical loop that must not enter the
+ * allocator). The paper has no counterpart: this is a deployment convenience.
+ * Same arguments, results and validation as scsf_sort; the scratch lives in a
+ * static device array of scsf_sort_noalloc_capacity() bytes (8 MiB) that every
+ * GPU loading this library reserves until the process exits. Sizes with
+ * scsf_sort_workspace_size(n_ops, p0) above the capacity (n_ops > 8184 at
+ * p0 = 8) return SCSF_ERR_NO_MEMORY. The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. The call allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine). All calls on a
+ * device share the one array and each call rewrites what it reads, so calls
+ * that overlap on the GPU (other streams, other threads) race: serialise them. */
+size_t scsf_sort_noalloc_capacity(void);
+scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                              int start, int32_t* perm_out);
+
 /* ---------------------------------------------------------------------------
  * Operators (App. D.2), Dirichlet boundary, n x n interior grid, h = 1/(n+1).
  *

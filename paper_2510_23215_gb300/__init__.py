@@ -40,6 +40,7 @@ EXPORTED_SYMBOLS = [
     "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
+    "scsf_sort_noalloc_capacity", "scsf_sort_noalloc",
 ]
 
 
@@ -112,6 +113,10 @@ def library() -> ctypes.CDLL:
     L.scsf_set_timing.restype = ctypes.c_int
     L.scsf_launch_count.argtypes = []
     L.scsf_launch_count.restype = ctypes.c_longlong
+    L.scsf_sort_noalloc_capacity.argtypes = []
+    L.scsf_sort_noalloc_capacity.restype = sz
+    L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    L.scsf_sort_noalloc.restype = ctypes.c_int
     for name in EXPORTED_SYMBOLS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int or name in (
@@ -272,6 +277,22 @@ def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] =
     perm = torch.empty(n_ops, dtype=torch.int32, device=fields.device)
     c.check(L.scsf_sort(c.handle, fields.data_ptr(), n_ops, p, p0, start, ws.data_ptr(),
                         ws.numel(), perm.data_ptr()))
+    return perm
+
+
+def sort_noalloc(fields: torch.Tensor, p0: int, start: int = 0,
+                 ctx: Optional[Context] = None) -> torch.Tensor:
+    """Alg. 2 through the allocation-free entry point: same result as sort(), with the
+    library's static device scratch instead of a workspace (only perm_out is allocated,
+    here by torch, because Python callers need a tensor to hold it)."""
+    _check(fields, "fields")
+    if fields.dim() != 3 or fields.shape[1] != fields.shape[2]:
+        raise ValueError("fields must be [n_ops, p, p]")
+    c = _ctx(ctx, fields.device)
+    n_ops, p = int(fields.shape[0]), int(fields.shape[1])
+    perm = torch.empty(n_ops, dtype=torch.int32, device=fields.device)
+    c.check(library().scsf_sort_noalloc(c.handle, fields.data_ptr(), n_ops, p, p0, start,
+                                        perm.data_ptr()))
     return perm
 
 

@@ -51,6 +51,17 @@ scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
                   std::string(#expr) + ": " + cudaGetErrorString(_e));                    \
   } while (0)
 
+}  // namespace
+
+namespace scsf {
+int ctx_device(const scsf_ctx* ctx) { return ctx->device; }
+scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg) {
+  return fail(ctx, status, msg);
+}
+}  // namespace scsf
+
+namespace {
+
 int block_width(const scsf_params* p) {
   const int nex = (p->nex >= 0) ? p->nex : (int)std::ceil(0.2 * p->k);
   return p->k + nex;

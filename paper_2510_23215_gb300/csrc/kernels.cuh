@@ -2,9 +2,17 @@
 // launch error). Layouts: row-major blocks, column index fastest.
 #pragma once
 
+#include <string>
+
+#include "../../include/scsf.h"
 #include "common.cuh"
 
 namespace scsf {
+
+// Context accessors for entry points defined outside api.cu.
+int ctx_device(const scsf_ctx* ctx);
+// Stores `msg` as the context's last error and returns `status`.
+scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg);
 
 // ---- operator assembly (stencil.cu) -------------------------------------
 // Builds d/we/wn for -div(a grad u) (ax, ay) or -Lap u + V u (v), and writes
