@@ -129,7 +129,8 @@ def run_ours(args):
     scsf.library()  # fails loudly when the extension is missing
     w = WORKLOAD
     n, k, n_ops = w["n"], w["k"], w["n_ops"]
-    params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank)
+    forms = {"mixed": scsf.MIXED, "fp64": scsf.FP64}
+    chosen = args.form
     ops = _workload_ops(rank)
     # host copies (pinned) for the end-to-end leg; device copies resident for the kernel leg
     h_fields = torch.from_numpy(np.stack([o.P for o in ops])).pin_memory()
@@ -140,8 +141,10 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h_evals = torch.empty((n_ops, k), dtype=torch.float64).pin_memory()
     h_resid = torch.empty((n_ops, k), dtype=torch.float64).pin_memory()
+    st = torch.cuda.current_stream(dev)
 
-    def step(fields, ax, ay):
+    def step(fields, ax, ay, precision):
+        params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank, precision=precision)
         perm = scsf.sort(fields, p0=w["p0"], start=0, ctx=ctx).cpu().tolist()
         dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i]) for i in perm]
         ev, rs, _, stats = scsf.solve(dops, params, ctx=ctx)
@@ -152,35 +155,51 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step(d_fields, d_ax, d_ay)
-    barrier()
-
-    ctx.set_timing(True)
-    st = torch.cuda.current_stream(dev)
-    times, all_stats, good = [], [], 0
-    launches0 = scsf.launch_count()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    def timed(precision, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(d_fields, d_ax, d_ay, precision)
+        barrier()
+        ctx.set_timing(True)
+        times, all_stats, good = [], [], 0
+        launches0 = scsf.launch_count()
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
+        for _ in range(steps):
             flush.zero_()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            ev, rs, stats = step(d_fields, d_ax, d_ay)
+            ev, rs, stats = step(d_fields, d_ax, d_ay, precision)
             e1.record(st)
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
             all_stats.extend(stats)
             good += int((rs <= w["tol"]).sum().item())
-    launches = scsf.launch_count() - launches0
-    ctx.set_timing(False)
-    clocks = clk.summary()
-    total_ms = sum(times)
+        if clk:
+            clk.__exit__(None, None, None)
+        ctx.set_timing(False)
+        return {"ms": sum(times), "stats": all_stats, "pairs": good,
+                "launches": scsf.launch_count() - launches0,
+                "clocks": clk.summary() if clk else None}
 
-    # end to end through the public API with host buffers
-    e2e_times = []
+    def reduce_max_sum(ms, pairs):
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        p = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        return float(t[0]), float(p[0])
+
+    main = timed(forms[chosen], args.steps, args.warmup, sample_clocks=True)
+    total_ms, pairs = reduce_max_sum(main["ms"], main["pairs"])
+    value = pairs / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers (chosen form)
+    e2e_ms = 0.0
     h2d = (h_fields.numel() + h_ax.numel() + h_ay.numel()) * 8
     d2h = 2 * n_ops * k * 8
+    e2e_pairs = 0
     for _ in range(args.steps):
         flush.zero_()
         barrier()
@@ -189,57 +208,73 @@ def run_ours(args):
         f = h_fields.to(dev, non_blocking=True)
         a = h_ax.to(dev, non_blocking=True)
         b = h_ay.to(dev, non_blocking=True)
-        ev, rs, _ = step(f, a, b)
+        ev, rs, _ = step(f, a, b, forms[chosen])
         h_evals.copy_(ev, non_blocking=True)
         h_resid.copy_(rs, non_blocking=True)
         e1.record(st)
         torch.cuda.synchronize(dev)
-        e2e_times.append(e0.elapsed_time(e1))
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_pairs += int((h_resid <= w["tol"]).sum().item())
+    e2e_ms, e2e_pairs = reduce_max_sum(e2e_ms, e2e_pairs)
+    e2e_value = e2e_pairs / (e2e_ms * 1e-3)
 
-    t_max = torch.tensor([total_ms, sum(e2e_times)], dtype=torch.float64, device=dev)
-    good_t = torch.tensor([float(good)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(good_t, op=dist.ReduceOp.SUM)
-    total_ms, e2e_ms = float(t_max[0]), float(t_max[1])
-    pairs = float(good_t[0])
-    value = pairs / (total_ms * 1e-3)
-    e2e_value = pairs / (e2e_ms * 1e-3)
+    other = None
+    if not args.no_plain and chosen != "fp64":
+        plain = timed(forms["fp64"], args.plain_steps, 1)
+        p_ms, p_pairs = reduce_max_sum(plain["ms"], plain["pairs"])
+        other = {"form": "plain FP64", "value": p_pairs / (p_ms * 1e-3),
+                 "ms_per_step": p_ms / args.plain_steps, "steps": args.plain_steps, "warmup": 1,
+                 "iters_per_op_mean": float(np.mean([s["iters"] for s in plain["stats"]]))}
 
+    all_stats = main["stats"]
     # live per-kernel rooflines from the CUDA-event phase timings of the timed steps
     filt_ms = sum(s["t_filter_ms"] for s in all_stats)
     filt_launch = sum(s["filter_steps"] for s in all_stats)
     filt_elems = sum(s["filter_elems"] for s in all_stats)
+    f32_ms = sum(s["t_filter32_ms"] for s in all_stats)
+    f32_launch = sum(s["filter32_steps"] for s in all_stats)
+    f32_elems = sum(s["filter32_elems"] for s in all_stats)
     rot_ms = sum(s["t_rot_ms"] for s in all_stats)
     rot_launch = sum(s["rot_launches"] for s in all_stats)
     rot_flops = sum(s["rot_flops"] for s in all_stats)
     phase_ms = {p: sum(s[f"t_{p}_ms"] for s in all_stats) for p in
-                ("filter", "orth", "rr", "eig", "rot", "resid")}
+                ("filter", "filter32", "orth", "rr", "eig", "rot", "resid")}
     peaks, peak_kind = _measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
     fp64_peak = FP64_PEAK_TFLOPS
-    # cheb step: 13 flop per (node, column) (4 neighbour FMA, centre FMA + mul, recurrence FMA)
-    filt_avg_s = filt_ms * 1e-3 / max(filt_launch, 1)
-    filt_flops_launch = 13.0 * filt_elems / max(filt_launch, 1)
-    filt_bytes_launch = 24.0 * filt_elems / max(filt_launch, 1)
-    rot_avg_s = rot_ms * 1e-3 / max(rot_launch, 1)
-    rot_flops_launch = rot_flops / max(rot_launch, 1)
-    kernels = {
-        "cheb_step_f64": {
-            "bound": "alu", "launches": filt_launch, "avg_us": filt_avg_s * 1e6,
-            "achieved": filt_flops_launch / filt_avg_s / 1e12 if filt_avg_s else None,
-            "peak": fp64_peak, "unit": "TFLOP/s",
-            "hbm_gbs_equiv": filt_bytes_launch / filt_avg_s / 1e9 if filt_avg_s else None},
-        "gemm_nn_f64 (rotation X = Q Z)": {
-            "bound": "alu", "launches": rot_launch, "avg_us": rot_avg_s * 1e6,
-            "achieved": rot_flops_launch / rot_avg_s / 1e12 if rot_avg_s else None,
-            "peak": fp64_peak, "unit": "TFLOP/s"},
-    }
-    dom = kernels["cheb_step_f64"]
-    roofline = {"bound": "alu", "kernel": "cheb_step_f64", "achieved": dom["achieved"],
-                "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (dom["achieved"] / fp64_peak) if dom["achieved"] else None,
-                "traffic": None,
-                "peak_source": "FP64 ALU rate derived from unit counts and clocks (not in MEASURED_PEAKS.json)"}
+    kernels = {}
+    if filt_launch:
+        avg = filt_ms * 1e-3 / filt_launch
+        kernels["cheb_step_f64"] = {
+            "bound": "alu", "launches": filt_launch, "avg_us": avg * 1e6,
+            "achieved": 13.0 * filt_elems / filt_launch / avg / 1e12, "peak": fp64_peak,
+            "unit": "TFLOP/s", "bytes_per_launch": 24.0 * filt_elems / filt_launch}
+    if f32_launch:
+        avg = f32_ms * 1e-3 / f32_launch
+        kernels["cheb_step_f32"] = {
+            "bound": "hbm", "launches": f32_launch, "avg_us": avg * 1e6,
+            "achieved": 12.0 * f32_elems / f32_launch / avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "bytes_per_launch": 12.0 * f32_elems / f32_launch,
+            "note": "3 x 7.9 MB blocks are L2-resident at this size: an effective rate, not DRAM"}
+    if rot_launch:
+        avg = rot_ms * 1e-3 / rot_launch
+        kernels["gemm_nn (rotation X = Q Z, FP32 or FP64 by phase)"] = {
+            "launches": rot_launch, "avg_us": avg * 1e6}
+    dom_name = max(("filter", "orth", "rr", "eig", "rot"), key=lambda p: phase_ms[p] +
+                   (phase_ms["filter32"] if p == "filter" else 0.0))
+    if "cheb_step_f32" in kernels and phase_ms["filter32"] >= phase_ms["filter"]:
+        kk = kernels["cheb_step_f32"]
+        roofline = {"bound": "hbm", "kernel": "cheb_step_f32", "achieved": kk["achieved"],
+                    "peak": hbm_peak, "unit": "GB/s", "frac": kk["achieved"] / hbm_peak,
+                    "traffic": None, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                    "note": kk["note"]}
+    else:
+        kk = kernels["cheb_step_f64"]
+        roofline = {"bound": "alu", "kernel": "cheb_step_f64", "achieved": kk["achieved"],
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": kk["achieved"] / fp64_peak,
+                    "traffic": None,
+                    "peak_source": "FP64 ALU rate from unit counts and clocks (152 SMs x 2 FMA/clk)"}
+    roofline["dominant_phase"] = dom_name
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -248,21 +283,27 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if chosen == "fp64" else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": w["name"], "grid": f"{n}x{n}", "N": n * n, "n_ops_per_gpu": n_ops,
-                   "k": k, "block_width": params.kb, "degree": w["degree"], "p0": w["p0"],
-                   "tol": w["tol"], "form": "plain FP64 (sort + chain solve)",
+                   "k": k, "block_width": scsf.block_width(k), "degree": w["degree"], "p0": w["p0"],
+                   "tol": w["tol"],
+                   "form": {"mixed": "mixed: FP32 phase + FP64 finish (sort + chain solve)",
+                            "fp64": "plain FP64 (sort + chain solve)"}[chosen],
                    "field_law": "a = exp(0.5 f/8), f = sum of 8x8 cosine modes, N(0,1) coefficients",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": f"replicas over chains x{ws}"},
         "eigenpairs_per_step": pairs / args.steps / ws,
         "iters_per_op_mean": float(np.mean([s["iters"] for s in all_stats])),
+        "iters_fp32_per_op_mean": float(np.mean([s["iters_fp32"] for s in all_stats])),
         "phase_ms_per_step": {p: v / args.steps for p, v in phase_ms.items()},
+        "plain_fp64": other,
+        "speedup_vs_plain_fp64": (value / other["value"]) if other else None,
         "roofline": roofline,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
+        "gpu_launches": int(main["launches"]),
+        "clocks": main["clocks"],
         "cpu_baseline": cpu,
         "peaks_source": peak_kind,
     }
@@ -330,6 +371,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample-ops", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed",
+                    help="headline form (default: the mixed form; plain FP64 is timed beside it)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--n-ops", type=int, default=None,
                     help="problems per batch (default 200; smaller only for profiler captures)")
     args = ap.parse_args()

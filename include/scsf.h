@@ -149,6 +149,11 @@ typedef struct {
   double t_eig_ms;       /* line 6: reduced eigensolve                       */
   double t_rot_ms;       /* line 6: rotation X = Q Z (one GEMM launch)       */
   double t_resid_ms;     /* line 7: residual norms                           */
+  /* SCSF_MIXED only: the FP32 phase (counted in iters; t_filter_ms is FP64 only). */
+  int iters_fp32;        /* outer iterations run in FP32                     */
+  int filter32_steps;    /* FP32 stencil steps                               */
+  double filter32_elems; /* sum over FP32 filter steps of N * columns        */
+  double t_filter32_ms;  /* FP32 filter time                                 */
 } scsf_stats;
 
 /* Enables (1) or disables (0) per-phase CUDA-event timing in scsf_stats. */
@@ -217,6 +222,12 @@ scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const doubl
                              double* Y, int ldy, void* scratch, size_t scratch_bytes);
 scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double* bounds_host,
                                  void* scratch, size_t scratch_bytes);
+/* scsf_cheb_filter on FP32 blocks (the mixed form's filter): X, Y [N][ncols]
+ * FP32 with ncols and ldx multiples of 4 and ldy == ncols; the operator is assembled in FP64
+ * and rounded to FP32; scratch >= 2 N ncols 4 + 6 N 8 + 64 KiB bytes. */
+scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const float* X, int ldx,
+                                 int ncols, int degree, double lambda, double c, double e,
+                                 float* Y, int ldy, void* scratch, size_t scratch_bytes);
 size_t scsf_small_eigh_scratch(int k);
 scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
                             void* scratch, size_t scratch_bytes);

@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
-    "scsf_sort_noalloc_capacity", "scsf_sort_noalloc",
+    "scsf_sort_noalloc_capacity", "scsf_sort_noalloc", "scsf_cheb_filter_f32",
 ]
 
 
@@ -69,7 +69,9 @@ class _CStats(ctypes.Structure):
                 ("rot_launches", ctypes.c_int), ("launches", ctypes.c_int),
                 ("t_filter_ms", ctypes.c_double), ("t_orth_ms", ctypes.c_double),
                 ("t_rr_ms", ctypes.c_double), ("t_eig_ms", ctypes.c_double),
-                ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double)]
+                ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
+                ("iters_fp32", ctypes.c_int), ("filter32_steps", ctypes.c_int),
+                ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -113,6 +115,9 @@ def library() -> ctypes.CDLL:
     L.scsf_set_timing.restype = ctypes.c_int
     L.scsf_launch_count.argtypes = []
     L.scsf_launch_count.restype = ctypes.c_longlong
+    L.scsf_cheb_filter_f32.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, i32, i32, dbl, dbl,
+                                       dbl, vp, i32, vp, sz]
+    L.scsf_cheb_filter_f32.restype = ctypes.c_int
     L.scsf_sort_noalloc_capacity.argtypes = []
     L.scsf_sort_noalloc_capacity.restype = sz
     L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
@@ -398,6 +403,23 @@ def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float
     cx.check(library().scsf_cheb_filter(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, ncols,
                                         degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
                                         ws.numel()))
+    return Y
+
+
+def cheb_filter_f32(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float, e: float,
+                    ctx: Optional[Context] = None) -> torch.Tensor:
+    """Alg. 1 on an FP32 block (the mixed form's filter); ncols must be a multiple of 4."""
+    _check(X, "X", dtype=torch.float32)
+    cx = _ctx(ctx, X.device)
+    N, ncols = int(X.shape[0]), int(X.shape[1])
+    if N != op.n * op.n:
+        raise ValueError("X must have n*n rows")
+    Y = torch.empty_like(X)
+    ws = _workspace(4 * 2 * N * ncols + 8 * 6 * N + (64 << 10), X.device)
+    cop = op._c()
+    cx.check(library().scsf_cheb_filter_f32(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols,
+                                            ncols, degree, lam, c, e, Y.data_ptr(), ncols,
+                                            ws.data_ptr(), ws.numel()))
     return Y
 
 

@@ -85,10 +85,12 @@ struct ChainBufs {
   void* eigh_scratch;
   int* status;
   int* cols;
+  // FP32 phase of the mixed form (null otherwise)
+  float *V32, *B32[3], *d32, *we32, *wn32, *partials32;
 };
 
 template <typename Cv>
-void carve_chain(Cv& c, int n, int kb, ChainBufs& b) {
+void carve_chain(Cv& c, int n, int kb, bool mixed, ChainBufs& b) {
   const size_t N = (size_t)n * n;
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
@@ -114,6 +116,17 @@ void carve_chain(Cv& c, int n, int kb, ChainBufs& b) {
   b.eigh_scratch = c.template take<char>(small_eigh_scratch_bytes(kb));
   b.status = c.template take<int>(4);
   b.cols = c.template take<int>(kb);
+  b.V32 = b.d32 = b.we32 = b.wn32 = b.partials32 = nullptr;
+  b.B32[0] = b.B32[1] = b.B32[2] = nullptr;
+  if (mixed) {
+    b.V32 = c.template take<float>(blk);
+    for (auto& p : b.B32) p = c.template take<float>(blk);
+    b.d32 = c.template take<float>(N);
+    b.we32 = c.template take<float>(N);
+    b.wn32 = c.template take<float>(N);
+    b.partials32 = c.template take<float>(std::max(gemm_tn_f32_partials((int)N, kb, kb, true),
+                                                   gemm_tn_f32_partials((int)N, kb, kb, false)));
+  }
 }
 
 struct SizeCarve {
@@ -151,6 +164,34 @@ cudaError_t run_filter(const Stencil& A, const double* Y0, int ld0, int ncols, i
     if (err != cudaSuccess) return err;
     prev = bufs[cur];
     ldp = lds[cur];
+    cur = nxt;
+    sigma = sigma_next;
+  }
+  *which = cur;
+  return cudaSuccess;
+}
+
+// The same recurrence on FP32 blocks (scalars computed in FP64, applied in FP32).
+cudaError_t run_filter_f32(const Stencil32& A, const float* Y0, int ld0, int ncols, int degree,
+                           double lam, double c, double e, float* const bufs[3], int ld,
+                           int* which, cudaStream_t st) {
+  const double sigma1 = e / (lam - c);
+  cudaError_t err = launch_cheb_step_f32(A, Y0, ld0, nullptr, 0, bufs[0], ld, ncols,
+                                         (float)(sigma1 / e), (float)(-sigma1 * c / e), 0.f, st);
+  if (err != cudaSuccess) return err;
+  double sigma = sigma1;
+  const float* prev = Y0;
+  int ldp = ld0;
+  int cur = 0;
+  for (int i = 1; i < degree; ++i) {
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    const int nxt = i % 3;
+    err = launch_cheb_step_f32(A, bufs[cur], ld, prev, ldp, bufs[nxt], ld, ncols,
+                               (float)(2.0 * sigma_next / e), (float)(-2.0 * sigma_next * c / e),
+                               (float)(-sigma_next * sigma), st);
+    if (err != cudaSuccess) return err;
+    prev = bufs[cur];
+    ldp = ld;
     cur = nxt;
     sigma = sigma_next;
   }
@@ -247,7 +288,7 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, n_max, kb, b);
+  carve_chain(c, n_max, kb, params->precision == SCSF_MIXED, b);
   return c.used;
 }
 
@@ -264,8 +305,11 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
     return fail(ctx, SCSF_ERR_INVALID_ARG, "grid too small for the block width");
   if (params->degree < 1 || !(params->tol > 0.0) || params->max_iter < 1)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need degree >= 1, tol > 0, max_iter >= 1");
-  if (params->precision != SCSF_FP64)
-    return fail(ctx, SCSF_ERR_INVALID_ARG, "only SCSF_FP64 is available in this build");
+  if (params->precision != SCSF_FP64 && params->precision != SCSF_MIXED)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "precision must be SCSF_FP64 or SCSF_MIXED");
+  if (params->precision == SCSF_MIXED && kb % 4 != 0)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "SCSF_MIXED needs k + nex divisible by 4 (float4 block rows)");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   scsf_chain* ch = new (std::nothrow) scsf_chain();
@@ -276,7 +320,7 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
   ch->N = n * n;
   ch->kb = kb;
   Carve c(workspace, workspace_bytes);
-  carve_chain(c, n, kb, ch->b);
+  carve_chain(c, n, kb, params->precision == SCSF_MIXED, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -342,7 +386,94 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     return timing ? cudaEventRecord(ctx->ev[i], st) : cudaSuccess;
   };
   bool converged = false;
-  for (it = 1; it <= ch->p.max_iter; ++it) {
+  bool fp32_first = true;  // first Cholesky QR factor in FP32
+  int it32 = 0, filter32_steps = 0;
+  double felems32 = 0.0, t_filter32 = 0.0;
+
+  // FP32 phase of the mixed form: the whole block iterates in FP32 (filter, Cholesky
+  // QR, Rayleigh-Ritz, rotation) without locking, until the wanted residuals stop
+  // improving, i.e. the subspace has converged to FP32 accuracy. FP32 storage floors
+  // the relative residual near eps32 ||A|| / lambda, so locking at the tolerance is
+  // left to the FP64 phase, which starts from this block.
+  if (ch->p.precision == SCSF_MIXED) {
+    const Stencil32 A32{b.d32, b.we32, b.wn32, n};
+    SCSF_CUDA(ctx, launch_to_f32(b.d, b.d32, N, st));
+    SCSF_CUDA(ctx, launch_to_f32(b.we, b.we32, N, st));
+    SCSF_CUDA(ctx, launch_to_f32(b.wn, b.wn32, N, st));
+    SCSF_CUDA(ctx, launch_block_f64_to_f32(N, kb, b.V, kb, b.V32, kb, st));
+    double prev_score = INFINITY;
+    const int max32 = std::max(0, ch->p.max_iter - 10);
+    while (it32 < max32) {
+      ++it32;
+      if (!(alpha < beta)) alpha = lam + 0.5 * (beta - lam);
+      if (!(lam < alpha)) lam = alpha - 1e-3 * (beta - alpha);
+      const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
+      int which = 0;
+      SCSF_CUDA(ctx, mark(0));
+      SCSF_CUDA(ctx, run_filter_f32(A32, b.V32, kb, kb, m, lam, c, e, b.B32, kb, &which, st));
+      SCSF_CUDA(ctx, mark(1));
+      filter32_steps += m;
+      felems32 += (double)m * N * kb;
+      float* Y = b.B32[which];
+      float* F1 = b.B32[(which + 1) % 3];
+      float* F2 = b.B32[(which + 2) % 3];
+      for (int pass = 0; pass < 2; ++pass) {
+        SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, Y, kb, b.G, kb, true, b.partials32, st));
+        SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + pass, st));
+        SCSF_CUDA(ctx, launch_gemm_nn_f32(N, kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true, st));
+        std::swap(Y, F1);
+      }
+      SCSF_CUDA(ctx, mark(2));
+      SCSF_CUDA(ctx, launch_cheb_step_f32(A32, Y, kb, nullptr, 0, F2, kb, kb, 1.f, 0.f, 0.f, st));
+      SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, F2, kb, b.H, kb, false, b.partials32, st));
+      SCSF_CUDA(ctx, mark(3));
+      SCSF_CUDA(ctx, launch_small_eigh_f32(kb, b.H, kb, b.theta, b.Z, kb, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, mark(4));
+      SCSF_CUDA(ctx, launch_gemm_nn_f32(N, kb, kb, 1.f, Y, kb, b.Z, kb, 0.f, b.V32, kb, false, st));
+      SCSF_CUDA(ctx, mark(5));
+      SCSF_CUDA(ctx, launch_residual_norms_f32(A32, b.V32, kb, kb, b.theta, b.res_partials, b.res2, st));
+      SCSF_CUDA(ctx, mark(6));
+      SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, kb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * kb * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+      SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+      if (timing) {
+        float ms = 0.f;
+        SCSF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        t_filter32 += ms;
+        for (int i = 1; i < 6; ++i) {
+          SCSF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+          tms[i] += ms;
+        }
+      }
+      // A vector stored in FP32 carries rounding noise of relative size ~eps32 in every
+      // eigendirection, which puts a floor of about c eps32 ||A|| / |theta_j| under its
+      // relative residual (||A|| <= beta). Once every wanted vector is at its floor the
+      // subspace has converged to FP32 accuracy and the FP64 phase takes over.
+      double score = 0.0;
+      int at_floor = 0;
+      for (int j = 0; j < kb; ++j) {
+        theta_h[j] = h[j];
+        const double rr = h[kMaxBlockWidth + j], aa = h[kMaxBlockWidth + kb + j];
+        r_h[j] = (aa > 0.0) ? std::sqrt(rr / aa) : 1.0;
+        if (j < k) {
+          const double floor_j = 16.0 * 5.96e-8 * beta / std::max(std::fabs(theta_h[j]), 1e-300);
+          at_floor += (r_h[j] <= std::max(floor_j, ch->p.tol)) ? 1 : 0;
+          score += std::log(std::max(r_h[j], 1e-300));
+        }
+      }
+      for (int j = 0; j < kb; ++j) ch->ritz[j] = theta_h[j];
+      lam = theta_h[0];
+      alpha = theta_h[kb - 1];
+      if (at_floor == k) break;
+      // safety: stop when the wanted residuals improve by less than 1.05x on average
+      if (score > prev_score - k * std::log(1.05)) break;
+      prev_score = score;
+    }
+    SCSF_CUDA(ctx, launch_block_f32_to_f64(N, kb, b.V32, kb, b.V, kb, st));
+  }
+
+  for (it = it32 + 1; it <= ch->p.max_iter; ++it) {
     const int ka = kb - nl;
     if (!(alpha < beta)) alpha = lam + 0.5 * (beta - lam);
     if (!(lam < alpha)) lam = alpha - 1e-3 * (beta - alpha);
@@ -371,7 +502,9 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     }
     for (int pass = 0; pass < 2; ++pass) {
       SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
-      SCSF_CUDA(ctx, launch_chol_inv(ka, b.G, ka, b.Rinv, b.status + pass, st));
+      // the first factor only has to precondition, so it is taken in FP32
+      SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, pass == 0 && fp32_first, b.C, b.Rinv,
+                                      b.status + pass, st));
       SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
       std::swap(Y, F1);
       flops += 2.0 * N * ka * ka;
@@ -407,6 +540,9 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     }
     int chol_status[2];
     std::memcpy(chol_status, h + 3 * kMaxBlockWidth, sizeof(chol_status));
+    // an FP32 first factor that needed a shift preconditions too weakly for one FP64 pass
+    // to reach FP64 orthogonality: take the first factor in FP64 for the rest of this problem
+    if (fp32_first && chol_status[0] > 0) fp32_first = false;
     if (chol_status[0] >= 1000 || chol_status[1] >= 1000)
       return fail(ctx, SCSF_ERR_BREAKDOWN, "Cholesky QR broke down even with a shift");
     for (int j = 0; j < ka; ++j) {
@@ -482,6 +618,10 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     stats->t_eig_ms = tms[3];
     stats->t_rot_ms = tms[4];
     stats->t_resid_ms = tms[5];
+    stats->iters_fp32 = it32;
+    stats->filter32_steps = filter32_steps;
+    stats->filter32_elems = felems32;
+    stats->t_filter32_ms = t_filter32;
   }
   if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
   return SCSF_OK;
@@ -565,6 +705,46 @@ scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const doubl
   SCSF_CUDA(ctx, run_filter(A, X, ldx, ncols, degree, lambda, c, e, bufs, lds, &which, st));
   if (bufs[which] != Y)
     SCSF_CUDA(ctx, launch_copy2d((int)N, ncols, bufs[which], lds[which], Y, ldy, st));
+  return SCSF_OK;
+}
+
+scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const float* X, int ldx,
+                                 int ncols, int degree, double lambda, double c, double e,
+                                 float* Y, int ldy, void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  if (ncols < 4 || ncols % 4 || ldx % 4 || ldx < ncols || ldy != ncols || degree < 1 ||
+      !(e > 0.0) || lambda == c)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "need ncols and ldx multiples of 4, ldy == ncols, valid filter parameters");
+  const int n = op->n;
+  const size_t N = (size_t)n * n;
+  Carve cv(scratch, scratch_bytes);
+  float* s0 = cv.take<float>(N * ncols);
+  float* s1 = cv.take<float>(N * ncols);
+  double* d = cv.take<double>(N);
+  double* we = cv.take<double>(N);
+  double* wn = cv.take<double>(N);
+  float* d32 = cv.take<float>(N);
+  float* we32 = cv.take<float>(N);
+  float* wn32 = cv.take<float>(N);
+  double* part = cv.take<double>(2 * (size_t)assemble_blocks(n));
+  double* bnd = cv.take<double>(2);
+  if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
+  SCSF_CUDA(ctx, launch_to_f32(d, d32, N, st));
+  SCSF_CUDA(ctx, launch_to_f32(we, we32, N, st));
+  SCSF_CUDA(ctx, launch_to_f32(wn, wn32, N, st));
+  const Stencil32 A{d32, we32, wn32, n};
+  // Y_i goes to rot[(i-1) % 3]; copy at the end if Y_m did not land in Y
+  float* rot[3] = {s0, s1, Y};
+  int which = 0;
+  SCSF_CUDA(ctx, run_filter_f32(A, X, ldx, ncols, degree, lambda, c, e, rot, ncols, &which, st));
+  if (rot[which] != Y)
+    SCSF_CUDA(ctx, cudaMemcpyAsync(Y, rot[which], N * ncols * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st));
   return SCSF_OK;
 }
 

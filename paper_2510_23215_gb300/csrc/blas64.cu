@@ -163,91 +163,6 @@ gemm_nn_kernel(int rows, int K, int n, double alpha, const double* __restrict__ 
     }
 }
 
-// ---- Cholesky G = L L^T (R = L^T) and R^{-1} = (L^{-1})^T -----------------
-// Shared layout: lower triangle + diagonal of S hold L; the strict upper
-// triangle holds L^{-1} transposed (S[j][i] = Linv[i][j], i > j); dinv[i] =
-// 1/L[i][i] = Linv[i][i]. On a non-positive pivot the factorisation restarts
-// on G + s I (shifted Cholesky QR) with s growing 100x per retry, starting
-// at 1e-14 k trace(G); status = number of shifted restarts, or 1000 if the
-// last attempt still failed.
-__global__ void __launch_bounds__(1024)
-chol_inv_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ Rinv,
-                int* __restrict__ status) {
-  extern __shared__ double S[];  // k*k
-  __shared__ double dinv[kMaxBlockWidth];
-  __shared__ int bad;
-  __shared__ double trace;
-  const int t = threadIdx.x, nt = blockDim.x;
-  if (t == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]);
-    trace = tr;
-  }
-  __syncthreads();
-  int attempt = 0;
-  for (; attempt < 4; ++attempt) {
-    const double shift = (attempt == 0) ? 0.0 : 1e-14 * k * trace * pow(100.0, attempt - 1);
-    for (int e = t; e < k * k; e += nt) {
-      const int i = e / k, j = e - (e / k) * k;
-      S[e] = (j <= i) ? G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0) : 0.0;
-    }
-    if (t == 0) bad = 0;
-    __syncthreads();
-    // right-looking Cholesky, one column at a time
-    for (int j = 0; j < k; ++j) {
-      if (t == 0) {
-        const double p = S[j * k + j];
-        if (!(p > 0.0)) {
-          if (bad == 0) bad = j + 1;
-          S[j * k + j] = 1.0;
-          dinv[j] = 1.0;
-        } else {
-          const double l = sqrt(p);
-          S[j * k + j] = l;
-          dinv[j] = 1.0 / l;
-        }
-      }
-      __syncthreads();
-      const double inv = dinv[j];
-      for (int i = j + 1 + t; i < k; i += nt) S[i * k + j] *= inv;
-      __syncthreads();
-      const int m = k - j - 1;  // trailing size
-      for (int e = t; e < m * m; e += nt) {
-        const int ii = e / m, cc = e - (e / m) * m;
-        if (cc <= ii) {
-          const int i = j + 1 + ii, c = j + 1 + cc;
-          S[i * k + c] = fma(-S[i * k + j], S[c * k + j], S[i * k + c]);
-        }
-      }
-      __syncthreads();
-    }
-    if (bad == 0) break;
-    __syncthreads();
-  }
-  // L^{-1} row by row: Linv[i][j] = -dinv[i] * sum_{c=j}^{i-1} L[i][c] Linv[c][j]
-  for (int i = 1; i < k; ++i) {
-    for (int j = t; j < i; j += nt) {
-      double s0 = S[i * k + j] * dinv[j], s1 = 0.0;
-      int c = j + 1;
-      for (; c + 1 < i; c += 2) {
-        s0 = fma(S[i * k + c], S[j * k + c], s0);
-        s1 = fma(S[i * k + c + 1], S[j * k + c + 1], s1);
-      }
-      if (c < i) s0 = fma(S[i * k + c], S[j * k + c], s0);
-      S[j * k + i] = -dinv[i] * (s0 + s1);
-    }
-    __syncthreads();
-  }
-  for (int e = t; e < k * k; e += nt) {
-    const int i = e / k, j = e - (e / k) * k;  // Rinv[i][j], upper: j >= i
-    double v = 0.0;
-    if (j > i) v = S[i * k + j];
-    else if (j == i) v = dinv[i];
-    Rinv[e] = v;
-  }
-  if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
-}
-
 __global__ void copy2d_kernel(int rows, int cols, const double* __restrict__ in, int ld_in,
                               double* __restrict__ out, int ld_out) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -305,18 +220,6 @@ cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A
                                                  upper);
   note_launch();
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_chol_inv(int k, const double* G, int ldg, double* Rinv, int* status,
-                            cudaStream_t st) {
-  if (k <= 0 || k > kMaxBlockWidth) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)k * k * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  chol_inv_kernel<<<1, 1024, smem, st>>>(k, G, ldg, Rinv, status);
-  note_launch();
   return cudaGetLastError();
 }
 

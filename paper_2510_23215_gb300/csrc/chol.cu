@@ -1,0 +1,145 @@
+// Cholesky factor and triangular inverse for Cholesky QR (Alg. 3 line 4).
+//
+// CholQR2 factors two Gram matrices per outer iteration. The first factor only
+// has to make X R^{-1} well conditioned, so it is computed in FP32 (60x the FP64
+// rate on GB300); the second, which fixes the final orthonormality, in FP64.
+// Both factorisations run in one CTA with the matrix in shared memory
+// (right-looking, one column per step, the trailing update on a 32 x 32 thread
+// grid without index division). The inverse R^{-1} = (L^{-1})^T is spread over
+// several CTAs, each holding L in shared memory: one warp forward-substitutes one
+// column of L^{-1}.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace scsf {
+namespace {
+
+__host__ __device__ __forceinline__ int odd_stride(int k) { return (k % 2 == 0) ? k + 1 : k; }
+
+// G = L L^T for k x k symmetric positive definite G (lower triangle read).
+// On a non-positive pivot the factorisation restarts on G + s I (shifted
+// Cholesky QR) with s growing 100x per retry, starting at c_eps k trace(G).
+// Writes L (lower, FP64, ld k, zeros above) and status = number of shifted
+// restarts, or 1000 if the last attempt still failed. blockDim = (32, 32).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L,
+            int* __restrict__ status, double shift_eps) {
+  extern __shared__ unsigned char smraw[];
+  T* S = reinterpret_cast<T*>(smraw);  // k x ks
+  const int ks = odd_stride(k);
+  __shared__ T dinv_s;
+  __shared__ int bad;
+  __shared__ double trace;
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  if (t == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]);
+    trace = tr;
+  }
+  __syncthreads();
+  int attempt = 0;
+  for (; attempt < 4; ++attempt) {
+    const double shift = (attempt == 0) ? 0.0 : shift_eps * k * trace * pow(100.0, attempt - 1);
+    for (int i = ty; i < k; i += 32)
+      for (int j = tx; j <= i; j += 32)
+        S[i * ks + j] = (T)(G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0));
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+      if (t == 0) {
+        const T p = S[j * ks + j];
+        if (!(p > T(0))) {
+          if (bad == 0) bad = j + 1;
+          S[j * ks + j] = T(1);
+          dinv_s = T(1);
+        } else {
+          const T l = sqrt(p);
+          S[j * ks + j] = l;
+          dinv_s = T(1) / l;
+        }
+      }
+      __syncthreads();
+      const T inv = dinv_s;
+      for (int i = j + 1 + t; i < k; i += 1024) S[i * ks + j] *= inv;
+      __syncthreads();
+      // trailing lower triangle: S[i][c] -= L[i][j] L[c][j], j < c <= i
+      for (int i = j + 1 + ty; i < k; i += 32) {
+        const T lij = S[i * ks + j];
+        for (int c = j + 1 + tx; c <= i; c += 32) S[i * ks + c] -= lij * S[c * ks + j];
+      }
+      __syncthreads();
+    }
+    if (bad == 0) break;
+    __syncthreads();
+  }
+  for (int i = ty; i < k; i += 32)
+    for (int j = tx; j < k; j += 32) L[(size_t)i * k + j] = (j <= i) ? (double)S[i * ks + j] : 0.0;
+  if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
+}
+
+// Rinv = (L^{-1})^T (upper, ld k). Each CTA stages L in shared memory; one warp
+// per column j of L^{-1}: x_j = 1/L_jj, x_i = -(sum_{c=j}^{i-1} L_ic x_c) / L_ii.
+constexpr int kTrinvWarps = 16;
+
+__global__ void __launch_bounds__(32 * kTrinvWarps)
+trinv_kernel(int k, const double* __restrict__ L, double* __restrict__ Rinv) {
+  extern __shared__ double Ls[];  // k x ks, then kTrinvWarps x k solution vectors
+  const int ks = odd_stride(k);
+  double* xs_all = Ls + (size_t)k * ks;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * kTrinvWarps;  // first column of this CTA
+  // rows >= j0 of L are the only ones this CTA's columns touch
+  for (int e = threadIdx.x; e < (k - j0) * k; e += blockDim.x) {
+    const int i = j0 + e / k, c = e - (e / k) * k;
+    if (c <= i) Ls[i * ks + c] = L[(size_t)i * k + c];
+  }
+  __syncthreads();
+  const int j = j0 + w;
+  if (j >= k) return;
+  double* x = xs_all + (size_t)w * k;
+  if (lane == 0) x[j] = 1.0 / Ls[j * ks + j];
+  __syncwarp();
+  for (int i = j + 1; i < k; ++i) {
+    const double* Li = Ls + (size_t)i * ks;
+    double s = 0.0;
+    for (int c = j + lane; c < i; c += 32) s = fma(Li[c], x[c], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] = -s / Li[i];
+    __syncwarp();
+  }
+  double* row = Rinv + (size_t)j * k;
+  for (int i = lane; i < k; i += 32) row[i] = (i >= j) ? x[i] : 0.0;
+}
+
+template <typename T>
+cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* status, double eps,
+                          cudaStream_t st) {
+  const size_t smem = (size_t)k * odd_stride(k) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  chol_kernel<T><<<1, dim3(32, 32), smem, st>>>(k, G, ldg, L, status, eps);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double* L, double* Rinv,
+                             int* status, cudaStream_t st) {
+  if (k <= 0 || k > kMaxBlockWidth) return cudaErrorInvalidValue;
+  cudaError_t e = fp32 ? launch_chol_t<float>(k, G, ldg, L, status, 1e-6, st)
+                       : launch_chol_t<double>(k, G, ldg, L, status, 1e-14, st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)k * odd_stride(k) + (size_t)kTrinvWarps * k) * sizeof(double);
+  if ((e = cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)) != cudaSuccess)
+    return e;
+  trinv_kernel<<<(k + kTrinvWarps - 1) / kTrinvWarps, 32 * kTrinvWarps, smem, st>>>(k, L, Rinv);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace scsf

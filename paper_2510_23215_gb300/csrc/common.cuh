@@ -25,6 +25,14 @@ struct Stencil {
   int n;
 };
 
+// FP32 copy of the stencil coefficients (mixed-precision path).
+struct Stencil32 {
+  const float* d;
+  const float* we;
+  const float* wn;
+  int n;
+};
+
 // Process-wide count of kernels this library has launched (for benchmarks).
 void note_launch();
 

@@ -48,10 +48,11 @@ cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, con
 cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A, int lda,
                            const double* M, int ldm, double beta, double* C, int ldc, bool upper,
                            cudaStream_t st);
-// Single-CTA FP64 Cholesky G = R^T R (G: k x k) and Rinv = R^{-1} (upper, k x k, ld k).
-// status[0] != 0 on a non-positive pivot (index + 1).
-cudaError_t launch_chol_inv(int k, const double* G, int ldg, double* Rinv, int* status,
-                            cudaStream_t st);
+// Cholesky QR factor (chol.cu): G = L L^T (FP32 or FP64, one CTA, shifted
+// restarts on breakdown) and Rinv = (L^T)^{-1} (upper, ld k, multi-CTA).
+// L: k x k scratch. status[0]: shifted restarts used, 1000 = failed.
+cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double* L, double* Rinv,
+                             int* status, cudaStream_t st);
 // out[i*ld_out + j] = in[i*ld_in + j], i < rows, j < cols.
 cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, double* out, int ld_out,
                           cudaStream_t st);
@@ -63,6 +64,32 @@ cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in,
 size_t small_eigh_scratch_bytes(int k);
 cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, double* Z, int ldz,
                               void* scratch, cudaStream_t st);
+
+// FP32 decomposition only (FP32 Jacobi + sort), for the FP32 phase: eigenvector
+// accuracy ~1e-6 relative, enough while residuals are far above the FP64 target.
+cudaError_t launch_small_eigh_f32(int k, const double* S, int lds, double* evals, double* Z,
+                                  int ldz, void* scratch, cudaStream_t st);
+
+// ---- FP32 kernels of the mixed-precision path (mixed.cu) ----------------
+// Stencil kernels need ncols % 4 == 0 and leading dimensions % 4 == 0.
+cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st);
+cudaError_t launch_block_f32_to_f64(int rows, int cols, const float* in, int ld_in, double* out,
+                                    int ld_out, cudaStream_t st);
+cudaError_t launch_block_f64_to_f32(int rows, int cols, const double* in, int ld_in, float* out,
+                                    int ld_out, cudaStream_t st);
+cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, const float* prev,
+                                 int ldp, float* out, int ldo, int ncols, float s1, float s2,
+                                 float s3, cudaStream_t st);
+cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ldx, int ncols,
+                                      const double* theta, double* partials, double* out2,
+                                      cudaStream_t st);
+size_t gemm_tn_f32_partials(int rows, int m, int n, bool symmetric);
+cudaError_t launch_gemm_tn_f32(int rows, int m, int n, const float* A, int lda, const float* B,
+                               int ldb, double* C, int ldc, bool symmetric, float* partials,
+                               cudaStream_t st);
+cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float* A, int lda,
+                               const double* M, int ldm, float beta, float* C, int ldc, bool upper,
+                               cudaStream_t st);
 
 // ---- random head block (rng.cu) -----------------------------------------
 cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64_t seed,

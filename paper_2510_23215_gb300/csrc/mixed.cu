@@ -1,0 +1,376 @@
+// FP32 kernels of the mixed-precision path: the FP32 phase of the solver runs
+// the Chebyshev filter (Alg. 1), Cholesky QR, Rayleigh-Ritz and rotation on an
+// FP32 copy of the block until its subspace stops improving at FP32 accuracy;
+// the FP64 phase then finishes to the residual tolerance.
+//
+// Layout: row-major N x ld blocks with ld % 4 == 0 and the column count a
+// multiple of 4 in the stencil kernels, so each thread moves one float4 of a
+// node row (16-byte aligned, coalesced across the row). Small k x k matrices
+// stay FP64 so the shared Cholesky and eigensolve kernels serve both phases.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace scsf {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (float)in[i];
+}
+
+__global__ void block_f32_to_f64_kernel(int rows, int cols, const float* __restrict__ in, int ld_in,
+                                        double* __restrict__ out, int ld_out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+  out[(size_t)r * ld_out + c] = (double)in[(size_t)r * ld_in + c];
+}
+
+__global__ void block_f64_to_f32_kernel(int rows, int cols, const double* __restrict__ in, int ld_in,
+                                        float* __restrict__ out, int ld_out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+  out[(size_t)r * ld_out + c] = (float)in[(size_t)r * ld_in + c];
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// out = s1 (A cur) + s2 cur + s3 prev, one float4 of one node row per thread.
+__global__ void __launch_bounds__(kThreads)
+cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
+                     const float* __restrict__ prev, int ldp, float* __restrict__ out, int ldo,
+                     int quads, float s1, float s2, float s3) {
+  const int n = A.n;
+  const long long N = (long long)n * n;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * quads) return;
+  const int I = (int)(t / quads);
+  const int c = 4 * (int)(t - (long long)I * quads);
+  const int i = I / n, j = I - i * n;
+  const float* row = cur + (size_t)I * ldc + c;
+  const float4 y = ld4(row);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < n - 1) acc = fma4(A.we[I], ld4(row + (size_t)n * ldc), acc);
+  if (i > 0) acc = fma4(A.we[I - n], ld4(row - (size_t)n * ldc), acc);
+  if (j < n - 1) acc = fma4(A.wn[I], ld4(row + ldc), acc);
+  if (j > 0) acc = fma4(A.wn[I - 1], ld4(row - ldc), acc);
+  const float diag = fmaf(s1, A.d[I], s2);
+  float4 r = make_float4(fmaf(-s1, acc.x, diag * y.x), fmaf(-s1, acc.y, diag * y.y),
+                         fmaf(-s1, acc.z, diag * y.z), fmaf(-s1, acc.w, diag * y.w));
+  if (prev) r = fma4(s3, ld4(prev + (size_t)I * ldp + c), r);
+  st4(out + (size_t)I * ldo + c, r);
+}
+
+// Per-column ||(A X)_j - theta_j X_j||^2 and ||(A X)_j||^2 (FP32 products, FP64 sums).
+constexpr int kRows32 = 8;
+__global__ void __launch_bounds__(32 * kRows32)
+residual_norms_f32_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int ncols,
+                          const double* __restrict__ theta, double* __restrict__ partials) {
+  constexpr int kChunks = kMaxBlockWidth / 32;
+  const int n = A.n, N = n * n;
+  double rr[kChunks], aa[kChunks];
+  float th[kChunks];
+#pragma unroll
+  for (int q = 0; q < kChunks; ++q) {
+    rr[q] = aa[q] = 0.0;
+    const int c = threadIdx.x + 32 * q;
+    th[q] = (c < ncols) ? (float)theta[c] : 0.f;
+  }
+  for (int I = blockIdx.x * kRows32 + threadIdx.y; I < N; I += gridDim.x * kRows32) {
+    const int i = I / n, j = I - i * n;
+    const float d = A.d[I], wE = A.we[I], wW = (i > 0) ? A.we[I - n] : 0.f, wN = A.wn[I],
+                wS = (j > 0) ? A.wn[I - 1] : 0.f;
+    const float* row = X + (size_t)I * ldx;
+#pragma unroll
+    for (int q = 0; q < kChunks; ++q) {
+      const int c = threadIdx.x + 32 * q;
+      if (c < ncols) {
+        const float x = row[c];
+        float off = 0.f;
+        if (i < n - 1) off = fmaf(wE, row[(size_t)n * ldx + c], off);
+        if (i > 0) off = fmaf(wW, row[-(ptrdiff_t)((size_t)n * ldx) + c], off);
+        if (j < n - 1) off = fmaf(wN, row[ldx + c], off);
+        if (j > 0) off = fmaf(wS, row[-(ptrdiff_t)ldx + c], off);
+        const float ax = fmaf(d, x, -off);
+        const float r = fmaf(-th[q], x, ax);
+        rr[q] += (double)r * r;
+        aa[q] += (double)ax * ax;
+      }
+    }
+  }
+  __shared__ double s_r[kRows32][kMaxBlockWidth];
+  __shared__ double s_a[kRows32][kMaxBlockWidth];
+#pragma unroll
+  for (int q = 0; q < kChunks; ++q) {
+    const int c = threadIdx.x + 32 * q;
+    if (c < ncols) {
+      s_r[threadIdx.y][c] = rr[q];
+      s_a[threadIdx.y][c] = aa[q];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int c = threadIdx.x; c < ncols; c += 32) {
+      double sr = 0.0, sa = 0.0;
+      for (int y = 0; y < kRows32; ++y) {
+        sr += s_r[y][c];
+        sa += s_a[y][c];
+      }
+      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c] = sr;
+      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c] = sa;
+    }
+  }
+}
+
+__global__ void colsum_reduce_kernel(const double* __restrict__ partials, int nb, int ncols,
+                                     double* __restrict__ out2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ncols) return;
+  const int which = t / ncols, c = t - which * ncols;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partials[((size_t)b * 2 + which) * ncols + c];
+  out2[t] = s;
+}
+
+// C = A^T B (FP32 products, FP32 per-chunk sums, FP64 final sum), 64 x 64 tiles,
+// split over rows; symmetric: only upper tiles, mirrored in the reduction.
+constexpr int TT = 64;
+__global__ void __launch_bounds__(256)
+gemm_tn_f32_partial_kernel(int rows, int m, int n, const float* __restrict__ A, int lda,
+                           const float* __restrict__ B, int ldb, bool symmetric, int chunk_rows,
+                           float* __restrict__ partials) {
+  __shared__ float As[16][TT + 4];
+  __shared__ float Bs[16][TT + 4];
+  int ti, tj;
+  if (symmetric) {
+    int t = blockIdx.x, T = (m + TT - 1) / TT;
+    ti = 0;
+    while (t >= T - ti) {
+      t -= T - ti;
+      ++ti;
+    }
+    tj = ti + t;
+  } else {
+    const int tn = (n + TT - 1) / TT;
+    ti = blockIdx.x / tn;
+    tj = blockIdx.x - ti * tn;
+  }
+  const int i0 = ti * TT, j0 = tj * TT;
+  const int r_begin = blockIdx.y * chunk_rows;
+  const int r_end = min(rows, r_begin + chunk_rows);
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;  // 4 x 4 outputs per thread
+  float acc[4][4] = {};
+  for (int r0 = r_begin; r0 < r_end; r0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + 256 * q;  // 0..1023 = 16 rows x 64 cols
+      const int rr = e >> 6, cc = e & 63;
+      const int r = r0 + rr;
+      const bool rin = r < r_end;
+      As[rr][cc] = (rin && i0 + cc < m) ? A[(size_t)r * lda + i0 + cc] : 0.f;
+      Bs[rr][cc] = (rin && j0 + cc < n) ? B[(size_t)r * ldb + j0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[rr][ty + 16 * u];
+        b[u] = Bs[rr][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  float* P = partials + (size_t)blockIdx.y * m * n;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < m && j < n) P[(size_t)i * n + j] = acc[u][v];
+    }
+}
+
+__global__ void gemm_tn_f32_reduce_kernel(int m, int n, int nchunk, bool symmetric,
+                                          const float* __restrict__ partials, double* __restrict__ C,
+                                          int ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  int i = e / n, j = e - i * n;
+  int si = i, sj = j;
+  if (symmetric && i > j) {
+    si = j;
+    sj = i;
+  }
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += (double)partials[(size_t)c * m * n + (size_t)si * n + sj];
+  C[(size_t)i * ldc + j] = s;
+}
+
+struct Plan32 {
+  int ntiles, nchunk, chunk_rows;
+};
+
+Plan32 plan32(int rows, int m, int n, bool symmetric) {
+  Plan32 p;
+  const int tm = (m + TT - 1) / TT, tn = (n + TT - 1) / TT;
+  p.ntiles = symmetric ? tm * (tm + 1) / 2 : tm * tn;
+  const int max_chunks = std::max(1, (rows + 15) / 16);
+  int want = (kSplitTarget + p.ntiles - 1) / p.ntiles;
+  want = std::max(1, std::min(want, max_chunks));
+  int cr = (rows + want - 1) / want;
+  cr = ((cr + 15) / 16) * 16;
+  p.chunk_rows = std::max(cr, 16);
+  p.nchunk = (rows + p.chunk_rows - 1) / p.chunk_rows;
+  return p;
+}
+
+// C[rows x n] = alpha A[rows x K] M[K x n] + beta C (M FP64 in memory, used as FP32).
+__global__ void __launch_bounds__(256)
+gemm_nn_f32_kernel(int rows, int K, int n, float alpha, const float* __restrict__ A, int lda,
+                   const double* __restrict__ M, int ldm, float beta, float* C, int ldc, bool upper) {
+  __shared__ float As[64][17];
+  __shared__ float Ms[16][TT + 4];
+  const int r0 = blockIdx.y * 64, j0 = blockIdx.x * TT;
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  float acc[4][4] = {};
+  const int k_end = upper ? min(K, j0 + TT) : K;
+  for (int k0 = 0; k0 < k_end; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + 256 * q;  // 64 rows x 16 k
+      const int rr = e >> 4, kk = e & 15;
+      const int r = r0 + rr, kc = k0 + kk;
+      As[rr][kk] = (r < rows && kc < K) ? A[(size_t)r * lda + kc] : 0.f;
+      const int kk2 = e >> 6, jj = e & 63;  // 16 k x 64 cols
+      const int kc2 = k0 + kk2, j = j0 + jj;
+      Ms[kk2][jj] = (kc2 < K && j < n) ? (float)M[(size_t)kc2 * ldm + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[ty + 16 * u][kk];
+        b[u] = Ms[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = r0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (r < rows && j < n) {
+        float* c = C + (size_t)r * ldc + j;
+        *c = (beta == 0.f) ? alpha * acc[u][v] : fmaf(alpha, acc[u][v], beta * (*c));
+      }
+    }
+}
+
+unsigned blocks_for(long long count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  to_f32_kernel<<<blocks_for(count, kThreads), kThreads, 0, st>>>(in, out, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_f32_to_f64(int rows, int cols, const float* in, int ld_in, double* out,
+                                    int ld_out, cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  block_f32_to_f64_kernel<<<blocks_for(tot, kThreads), kThreads, 0, st>>>(rows, cols, in, ld_in,
+                                                                           out, ld_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_f64_to_f32(int rows, int cols, const double* in, int ld_in, float* out,
+                                    int ld_out, cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  block_f64_to_f32_kernel<<<blocks_for(tot, kThreads), kThreads, 0, st>>>(rows, cols, in, ld_in,
+                                                                           out, ld_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, const float* prev,
+                                 int ldp, float* out, int ldo, int ncols, float s1, float s2,
+                                 float s3, cudaStream_t st) {
+  if (ncols % 4 || ldc % 4 || ldo % 4 || (prev && ldp % 4)) return cudaErrorInvalidValue;
+  const int quads = ncols / 4;
+  const long long tot = (long long)A.n * A.n * quads;
+  cheb_step_f32_kernel<<<blocks_for(tot, kThreads), kThreads, 0, st>>>(
+      A, cur, ldc, (s3 != 0.f) ? prev : nullptr, ldp, out, ldo, quads, s1, s2, s3);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ldx, int ncols,
+                                      const double* theta, double* partials, double* out2,
+                                      cudaStream_t st) {
+  if (ncols > kMaxBlockWidth) return cudaErrorInvalidValue;
+  const int nb = resid_blocks(A.n);
+  residual_norms_f32_kernel<<<nb, dim3(32, kRows32), 0, st>>>(A, X, ldx, ncols, theta, partials);
+  note_launch();
+  colsum_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+size_t gemm_tn_f32_partials(int rows, int m, int n, bool symmetric) {
+  const Plan32 p = plan32(rows, m, n, symmetric);
+  return (size_t)p.nchunk * m * n;
+}
+
+cudaError_t launch_gemm_tn_f32(int rows, int m, int n, const float* A, int lda, const float* B,
+                               int ldb, double* C, int ldc, bool symmetric, float* partials,
+                               cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (symmetric && m != n) return cudaErrorInvalidValue;
+  const Plan32 p = plan32(rows, m, n, symmetric);
+  gemm_tn_f32_partial_kernel<<<dim3(p.ntiles, p.nchunk), 256, 0, st>>>(rows, m, n, A, lda, B, ldb,
+                                                                       symmetric, p.chunk_rows,
+                                                                       partials);
+  note_launch();
+  gemm_tn_f32_reduce_kernel<<<(m * n + 255) / 256, 256, 0, st>>>(m, n, p.nchunk, symmetric, partials,
+                                                               C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float* A, int lda,
+                               const double* M, int ldm, float beta, float* C, int ldc, bool upper,
+                               cudaStream_t st) {
+  if (rows <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((n + TT - 1) / TT, (rows + 63) / 64);
+  gemm_nn_f32_kernel<<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc, upper);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace scsf

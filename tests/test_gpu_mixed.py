@@ -1,0 +1,88 @@
+"""Mixed-precision form (FP32 phase + FP64 finish) against the oracle and the FP64 form."""
+import numpy as np
+import pytest
+
+import scsf_inputs as si
+from oracle import chebyshev, compare, dense, operators
+from tests.gpu_util import host, need_gpu, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EIG_RTOL = 1e-10
+RES_TOL = 1e-8
+
+
+@pytest.mark.parametrize("n,ncols,degree", [(20, 36, 1), (33, 24, 7), (17, 120, 20), (40, 4, 16)])
+def test_filter_f32_matches_oracle(n, ncols, degree):
+    """FP32 recurrence vs the FP64 oracle: error at FP32 level, relative to the block size."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op = si.div_a_grad_chain(n, 1, seed=n + 1)[0]
+    A = operators.assemble(op)
+    lo, hi = operators.gershgorin_bounds(A)
+    lam, alpha = lo + 0.001 * (hi - lo), lo + 0.05 * (hi - lo)
+    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+    X = si.gaussian_block(n * n, ncols, seed=4)
+    ref = chebyshev.chebyshev_filter(A, X.astype(np.float32).astype(np.float64), degree, lam, c, e)
+    Y = scsf.cheb_filter_f32(to_dev([op], dev)[0], torch.as_tensor(X, dtype=torch.float32, device=dev),
+                             degree, lam, c, e)
+    got = host(Y).astype(np.float64)
+    scale = np.max(np.abs(ref))
+    # each step rounds to FP32 and the recurrence amplifies at most like the filter itself
+    assert np.max(np.abs(got - ref)) <= 2e-5 * degree * scale
+
+
+def _check(op, evals, resid, evecs, k, ref_vals, ref_vecs=None):
+    A = operators.assemble(op)
+    assert np.max(resid) <= RES_TOL
+    assert np.max(operators.relative_residuals(A, evecs, evals)) <= 1.05 * RES_TOL
+    assert compare.orthonormality_error(evecs) <= 1e-12
+    assert compare.max_rel_eig_error(ref_vals, evals) <= EIG_RTOL
+    if ref_vecs is not None:
+        assert compare.max_cluster_angle(ref_vals, ref_vecs, evecs) <= 1e-5
+
+
+def test_mixed_poisson32_chain_matches_dense_definition():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(32, 16, seed=0)
+    perm = host(scsf.sort(torch.as_tensor(np.stack([o.P for o in ops]), device=dev), p0=8))
+    ordered = [ops[i] for i in perm]
+    p = scsf.Params(k=20, degree=16, tol=1e-8, precision=scsf.MIXED)
+    ev, rs, vec, stats = scsf.solve(to_dev(ordered, dev), p, want_vectors=True)
+    ev, rs, vec = host(ev), host(rs), host(vec)
+    for j, op in enumerate(ordered):
+        w, V = dense.smallest_eigenpairs(operators.assemble(op), 20)
+        _check(op, ev[j], rs[j], vec[j], 20, w, V)
+    assert all(s["converged"] for s in stats)
+    assert all(s["iters_fp32"] >= 1 for s in stats)
+
+
+def test_mixed_matches_fp64_form_on_poisson128_prefix():
+    """The first 12 problems of the 128 x 128, k = 100 chain: both forms give the same pairs."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    n, k = 128, 100
+    ops = si.div_a_grad_chain(n, 200, seed=1)
+    perm = host(scsf.sort(torch.as_tensor(np.stack([o.P for o in ops]), device=dev), p0=8))
+    ordered = to_dev([ops[i] for i in perm[:12]], dev)
+    ev64, rs64, _, st64 = scsf.solve(ordered, scsf.Params(k=k, degree=20, tol=1e-8))
+    evm, rsm, vecm, stm = scsf.solve(ordered, scsf.Params(k=k, degree=20, tol=1e-8,
+                                                          precision=scsf.MIXED), want_vectors=True)
+    ev64, evm = host(ev64), host(evm)
+    for j in range(12):
+        assert compare.max_rel_eig_error(ev64[j], evm[j]) <= EIG_RTOL
+        assert float(rsm[j].max()) <= RES_TOL
+    op0 = ops[perm[0]]
+    A = operators.assemble(op0)
+    assert np.max(operators.relative_residuals(A, host(vecm)[0], evm[0])) <= 1.05 * RES_TOL
+    assert compare.orthonormality_error(host(vecm)[0]) <= 1e-12
+    assert all(s["iters_fp32"] >= 1 for s in stm)
+
+
+def test_mixed_rejects_block_width_not_multiple_of_four():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    with pytest.raises(scsf.ScsfError):
+        scsf.Chain(scsf.Params(k=10, nex=3, precision=scsf.MIXED), 16, device=dev)
