@@ -207,6 +207,33 @@ scsf_status scsf_solve(scsf_ctx* ctx, const scsf_operator* ops, int64_t n_ops,
                        double* evals, double* resid, double* evecs, scsf_stats* stats);
 
 /* ---------------------------------------------------------------------------
+ * Batched solve: many independent chains in flight on one GPU (App. D.6 splits
+ * the dataset into chunks, each solved by its own SCSF instance).
+ *
+ * Each chain is solved exactly as scsf_solve would (same kernels, same results);
+ * chains differ freely in grid side, k and parameters. Up to `concurrency`
+ * chains run at once, each on its own stream driven by its own host thread, so
+ * the latency-bound phases of one chain overlap with the others. The call
+ * returns when every chain is done; chains[i].status holds each chain's status.
+ * workspace: device, >= scsf_batch_workspace_size(chains, n_chains,
+ * concurrency) bytes, 256-byte aligned; it is split into one slot per worker.
+ * Inputs must be ready on the context's stream when the call is made. */
+typedef struct {
+  const scsf_operator* ops;  /* host array of n_ops descriptors in solve order (same n)  */
+  int64_t n_ops;
+  scsf_params params;
+  double* evals;             /* [n_ops][k]                                             */
+  double* resid;             /* [n_ops][k]                                             */
+  double* evecs;             /* [n_ops][N][k] or NULL                                  */
+  scsf_stats* stats;         /* host [n_ops] or NULL                                   */
+  int status;                /* out                                                    */
+} scsf_batch_chain;
+
+size_t scsf_batch_workspace_size(const scsf_batch_chain* chains, int n_chains, int concurrency);
+scsf_status scsf_solve_batched(scsf_ctx* ctx, scsf_batch_chain* chains, int n_chains,
+                               int concurrency, void* workspace, size_t workspace_bytes);
+
+/* ---------------------------------------------------------------------------
  * Building blocks exported for kernel-level parity tests. Same conventions.
  *
  * scsf_cheb_filter: Y = C_m(Abar) X / C_m(t_lambda) by the scaled recurrence of

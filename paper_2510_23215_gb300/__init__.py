@@ -41,6 +41,7 @@ EXPORTED_SYMBOLS = [
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
     "scsf_sort_noalloc_capacity", "scsf_sort_noalloc", "scsf_cheb_filter_f32",
+    "scsf_batch_workspace_size", "scsf_solve_batched",
 ]
 
 
@@ -72,6 +73,13 @@ class _CStats(ctypes.Structure):
                 ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
                 ("iters_fp32", ctypes.c_int), ("filter32_steps", ctypes.c_int),
                 ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double)]
+
+
+class _CBatchChain(ctypes.Structure):
+    _fields_ = [("ops", ctypes.POINTER(_COperator)), ("n_ops", ctypes.c_int64),
+                ("params", _CParams), ("evals", ctypes.c_void_p), ("resid", ctypes.c_void_p),
+                ("evecs", ctypes.c_void_p), ("stats", ctypes.POINTER(_CStats)),
+                ("status", ctypes.c_int)]
 
 
 _lib = None
@@ -115,6 +123,10 @@ def library() -> ctypes.CDLL:
     L.scsf_set_timing.restype = ctypes.c_int
     L.scsf_launch_count.argtypes = []
     L.scsf_launch_count.restype = ctypes.c_longlong
+    L.scsf_batch_workspace_size.argtypes = [ctypes.POINTER(_CBatchChain), i32, i32]
+    L.scsf_batch_workspace_size.restype = sz
+    L.scsf_solve_batched.argtypes = [vp, ctypes.POINTER(_CBatchChain), i32, i32, vp, sz]
+    L.scsf_solve_batched.restype = ctypes.c_int
     L.scsf_cheb_filter_f32.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, i32, i32, dbl, dbl,
                                        dbl, vp, i32, vp, sz]
     L.scsf_cheb_filter_f32.restype = ctypes.c_int
@@ -387,6 +399,43 @@ def solve(ops: List[Operator], params: Params, want_vectors: bool = False,
     c.check(L.scsf_solve(c.handle, cops, n_ops, ctypes.byref(cp), ws.data_ptr(), ws.numel(),
                          evals.data_ptr(), resid.data_ptr(), _ptr(evecs), stats))
     return evals, resid, evecs, [_stats_dict(s) for s in stats]
+
+
+def solve_batched(chains, concurrency: int = 8, want_vectors: bool = False,
+                  ctx: Optional[Context] = None, raise_on_error: bool = True):
+    """scsf_solve_batched over chains = [(ops, Params), ...] (each ops list in solve order).
+
+    Returns a list of (evals, resid, evecs|None, stats, status) per chain."""
+    if not chains:
+        raise ValueError("no chains")
+    dev = chains[0][0][0].device
+    c = _ctx(ctx, dev)
+    keep, cchains, outs = [], [], []
+    for ops, params in chains:
+        if not ops:
+            raise ValueError("empty chain")
+        n_ops, k, N = len(ops), params.k, ops[0].n * ops[0].n
+        evals = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
+        resid = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
+        evecs = torch.empty((n_ops, N, k), dtype=torch.float64, device=c.device) if want_vectors else None
+        cops = (_COperator * n_ops)(*[o._c() for o in ops])
+        stats = (_CStats * n_ops)()
+        keep.append((cops, stats))
+        cchains.append(_CBatchChain(ctypes.cast(cops, ctypes.POINTER(_COperator)), n_ops, params._c(),
+                                    evals.data_ptr(), resid.data_ptr(), _ptr(evecs),
+                                    ctypes.cast(stats, ctypes.POINTER(_CStats)), 0))
+        outs.append((evals, resid, evecs, stats))
+    arr = (_CBatchChain * len(cchains))(*cchains)
+    L = library()
+    nbytes = L.scsf_batch_workspace_size(arr, len(cchains), concurrency)
+    if nbytes == 0:
+        raise ValueError("unsupported chain parameters")
+    ws = _workspace(nbytes, c.device)
+    st = L.scsf_solve_batched(c.handle, arr, len(cchains), concurrency, ws.data_ptr(), ws.numel())
+    if st != OK and raise_on_error:
+        c.check(st)
+    return [(e, r, v, [_stats_dict(s) for s in stt], int(arr[i].status))
+            for i, (e, r, v, stt) in enumerate(outs)]
 
 
 def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float, e: float,

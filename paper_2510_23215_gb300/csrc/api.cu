@@ -55,6 +55,8 @@ scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
 
 namespace scsf {
 int ctx_device(const scsf_ctx* ctx) { return ctx->device; }
+cudaStream_t ctx_stream(const scsf_ctx* ctx) { return ctx->stream; }
+bool ctx_timing(const scsf_ctx* ctx) { return ctx->timing; }
 scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg) {
   return fail(ctx, status, msg);
 }

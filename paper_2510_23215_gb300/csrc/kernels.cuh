@@ -11,6 +11,8 @@ namespace scsf {
 
 // Context accessors for entry points defined outside api.cu.
 int ctx_device(const scsf_ctx* ctx);
+cudaStream_t ctx_stream(const scsf_ctx* ctx);
+bool ctx_timing(const scsf_ctx* ctx);
 // Stores `msg` as the context's last error and returns `status`.
 scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg);
 
