@@ -10,6 +10,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,6 +56,19 @@ scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
 }  // namespace
 
 namespace scsf {
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = granted[{fn, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 int ctx_device(const scsf_ctx* ctx) { return ctx->device; }
 cudaStream_t ctx_stream(const scsf_ctx* ctx) { return ctx->stream; }
 bool ctx_timing(const scsf_ctx* ctx) { return ctx->timing; }

@@ -117,8 +117,7 @@ template <typename T>
 cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* status, double eps,
                           cudaStream_t st) {
   const size_t smem = (size_t)k * odd_stride(k) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)chol_kernel<T>, smem);
   if (e != cudaSuccess) return e;
   chol_kernel<T><<<1, dim3(32, 32), smem, st>>>(k, G, ldg, L, status, eps);
   note_launch();
@@ -134,9 +133,7 @@ cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double*
                        : launch_chol_t<double>(k, G, ldg, L, status, 1e-14, st);
   if (e != cudaSuccess) return e;
   const size_t smem = ((size_t)k * odd_stride(k) + (size_t)kTrinvWarps * k) * sizeof(double);
-  if ((e = cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
-    return e;
+  if ((e = ensure_dynamic_smem((const void*)trinv_kernel, smem)) != cudaSuccess) return e;
   trinv_kernel<<<(k + kTrinvWarps - 1) / kTrinvWarps, 32 * kTrinvWarps, smem, st>>>(k, L, Rinv);
   note_launch();
   return cudaGetLastError();

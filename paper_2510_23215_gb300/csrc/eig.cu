@@ -329,7 +329,7 @@ struct SizeOnly {
 };
 
 cudaError_t set_smem(const void* fn, size_t bytes) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return ensure_dynamic_smem(fn, bytes);
 }
 
 }  // namespace

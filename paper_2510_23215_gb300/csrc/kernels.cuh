@@ -13,6 +13,11 @@ namespace scsf {
 int ctx_device(const scsf_ctx* ctx);
 cudaStream_t ctx_stream(const scsf_ctx* ctx);
 bool ctx_timing(const scsf_ctx* ctx);
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current
+// device. The attribute is per function, so concurrent chains with different
+// block widths must not shrink it under each other's launches.
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
+
 // Stores `msg` as the context's last error and returns `status`.
 scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg);
 

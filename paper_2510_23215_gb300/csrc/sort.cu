@@ -153,8 +153,7 @@ cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int 
   unsigned char* visited = reinterpret_cast<unsigned char*>(
       static_cast<char*>(workspace) + align256((size_t)n_ops * p0 * p0 * 2 * sizeof(double)));
   const size_t smem = (size_t)(2 * p + 2 * p * p0) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(dft_features_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)dft_features_kernel, smem);
   if (e != cudaSuccess) return e;
   dft_features_kernel<<<(unsigned)n_ops, kFeatThreads, smem, st>>>(fields, p, p0, feats);
   note_launch();
