@@ -144,7 +144,12 @@ def run_ours(args):
     st = torch.cuda.current_stream(dev)
 
     def step(fields, ax, ay, precision, chunks=1):
-        params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank, precision=precision)
+        if precision == scsf.MIXED:  # the chosen form tunes its filter degrees
+            params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32,
+                                 tol=w["tol"], seed=7 + rank, precision=precision)
+        else:                        # the plain form keeps the workload's degree
+            params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank,
+                                 precision=precision)
         perm = scsf.sort(fields, p0=w["p0"], start=0, ctx=ctx).cpu().tolist()
         dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i]) for i in perm]
         if chunks <= 1:
@@ -302,6 +307,8 @@ def run_ours(args):
                        f"; sorted sequence cut into {args.chunks} chains solved concurrently"
                        if args.chunks > 1 else "; one sequential chain"),
                    "chunks": args.chunks,
+                   "degrees": ({"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}
+                               if chosen == "mixed" else {"fp64": w["degree"]}),
                    "field_law": "a = exp(0.5 f/8), f = sum of 8x8 cosine modes, N(0,1) coefficients",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": f"replicas over chains x{ws}"},
@@ -387,6 +394,8 @@ def main():
                     help="headline form (default: the mixed form; plain FP64 is timed beside it)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--degree-fp32", type=int, default=60, help="mixed form: FP32-phase degree")
+    ap.add_argument("--degree-fp64", type=int, default=60, help="mixed form: FP64-phase degree")
     ap.add_argument("--chunks", type=int, default=8,
                     help="contiguous chunks of the sorted sequence solved as concurrent chains")
     ap.add_argument("--n-ops", type=int, default=None,

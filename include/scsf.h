@@ -128,6 +128,7 @@ typedef struct {
   int max_iter;      /* outer iterations per problem (Alg. 3 repeat loop), >= 1           */
   int precision;     /* scsf_precision                                                    */
   uint64_t seed;     /* Philox seed of the random head block (Sec. 3.2, first problem)    */
+  int degree_fp32;   /* SCSF_MIXED: Chebyshev degree of the FP32 phase (<= 0: degree)     */
 } scsf_params;
 
 typedef struct {
@@ -154,6 +155,10 @@ typedef struct {
   int filter32_steps;    /* FP32 stencil steps                               */
   double filter32_elems; /* sum over FP32 filter steps of N * columns        */
   double t_filter32_ms;  /* FP32 filter time                                 */
+  /* Optional convergence history (input): when history is a host array of at
+   * least 3 * max_iter doubles, iteration i writes {max, median residual of the
+   * wanted unlocked pairs, pairs locked so far} to history[3 i .. 3 i + 2]. */
+  double* history;
 } scsf_stats;
 
 /* Enables (1) or disables (0) per-phase CUDA-event timing in scsf_stats. */

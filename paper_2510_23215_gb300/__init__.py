@@ -59,7 +59,7 @@ class _COperator(ctypes.Structure):
 class _CParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nex", ctypes.c_int), ("degree", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int)]
 
 
 class _CStats(ctypes.Structure):
@@ -72,7 +72,8 @@ class _CStats(ctypes.Structure):
                 ("t_rr_ms", ctypes.c_double), ("t_eig_ms", ctypes.c_double),
                 ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
                 ("iters_fp32", ctypes.c_int), ("filter32_steps", ctypes.c_int),
-                ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double)]
+                ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double))]
 
 
 class _CBatchChain(ctypes.Structure):
@@ -214,10 +215,11 @@ class Params:
     nex: int = -1
     precision: int = FP64
     seed: int = 0
+    degree_fp32: int = 0   # MIXED: degree of the FP32 phase (0: same as degree)
 
     def _c(self) -> _CParams:
         return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
-                        self.seed & 0xFFFFFFFFFFFFFFFF)
+                        self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32)
 
     @property
     def kb(self) -> int:
@@ -314,7 +316,7 @@ def sort_noalloc(fields: torch.Tensor, p0: int, start: int = 0,
 
 
 def _stats_dict(s: _CStats) -> dict:
-    out = {name: getattr(s, name) for name, _ in _CStats._fields_}
+    out = {name: getattr(s, name) for name, _ in _CStats._fields_ if name != "history"}
     out["converged"] = bool(s.converged)
     return out
 
@@ -351,19 +353,29 @@ class Chain:
         arr = (ctypes.c_double * kb)(*[float(x) for x in ritz])
         self.ctx.check(library().scsf_chain_seed(self._h, block.data_ptr(), arr))
 
-    def step(self, op: Operator, want_vectors: bool = True, raise_on_nonconvergence: bool = True):
+    def step(self, op: Operator, want_vectors: bool = True, raise_on_nonconvergence: bool = True,
+             history: bool = False):
+        """Solves the next problem. With history=True, stats["history"] lists per outer
+        iteration (max residual, median residual of the wanted unlocked pairs, locked)."""
         k, N = self.params.k, self.n * self.n
         dev = self.ctx.device
         evals = torch.empty(k, dtype=torch.float64, device=dev)
         resid = torch.empty(k, dtype=torch.float64, device=dev)
         evecs = torch.empty((N, k), dtype=torch.float64, device=dev) if want_vectors else None
         stats = _CStats()
+        hist = None
+        if history:
+            hist = (ctypes.c_double * (3 * self.params.max_iter))()
+            stats.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         cop = op._c()
         st = library().scsf_chain_step(self._h, ctypes.byref(cop), evals.data_ptr(), resid.data_ptr(),
                                        _ptr(evecs), ctypes.byref(stats))
         if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
             self.ctx.check(st)
-        return evals, resid, evecs, _stats_dict(stats)
+        out = _stats_dict(stats)
+        if hist is not None:
+            out["history"] = [tuple(hist[3 * i: 3 * i + 3]) for i in range(stats.iters)]
+        return evals, resid, evecs, out
 
     def close(self):
         if getattr(self, "_h", None):

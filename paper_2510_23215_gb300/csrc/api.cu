@@ -398,6 +398,21 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   double flops = 0.0, fbytes = 0.0, felems = 0.0, rot_flops = 0.0;
   double tms[6] = {0, 0, 0, 0, 0, 0};
   const long long launches0 = scsf_launch_count();
+  // optional convergence history: {max, median residual of wanted unlocked pairs, locked}
+  double* hist = stats ? stats->history : nullptr;
+  auto record = [&](int iter, int count, int locked) {
+    if (!hist || iter < 1 || iter > ch->p.max_iter) return;
+    std::vector<double> v(r_h.begin(), r_h.begin() + std::max(0, std::min(count, (int)r_h.size())));
+    double mx = 0.0, med = 0.0;
+    if (!v.empty()) {
+      mx = *std::max_element(v.begin(), v.end());
+      std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+      med = v[v.size() / 2];
+    }
+    hist[3 * (iter - 1)] = mx;
+    hist[3 * (iter - 1) + 1] = med;
+    hist[3 * (iter - 1) + 2] = locked;
+  };
   const bool timing = ctx->timing;
   auto mark = [&](int i) -> cudaError_t {
     return timing ? cudaEventRecord(ctx->ev[i], st) : cudaSuccess;
@@ -420,6 +435,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, launch_block_f64_to_f32(N, kb, b.V, kb, b.V32, kb, st));
     double prev_score = INFINITY;
     const int max32 = std::max(0, ch->p.max_iter - 10);
+    const int m32 = (ch->p.degree_fp32 > 0) ? ch->p.degree_fp32 : m;
     while (it32 < max32) {
       ++it32;
       if (!(alpha < beta)) alpha = lam + 0.5 * (beta - lam);
@@ -427,10 +443,10 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
       int which = 0;
       SCSF_CUDA(ctx, mark(0));
-      SCSF_CUDA(ctx, run_filter_f32(A32, b.V32, kb, kb, m, lam, c, e, b.B32, kb, &which, st));
+      SCSF_CUDA(ctx, run_filter_f32(A32, b.V32, kb, kb, m32, lam, c, e, b.B32, kb, &which, st));
       SCSF_CUDA(ctx, mark(1));
-      filter32_steps += m;
-      felems32 += (double)m * N * kb;
+      filter32_steps += m32;
+      felems32 += (double)m32 * N * kb;
       float* Y = b.B32[which];
       float* F1 = b.B32[(which + 1) % 3];
       float* F2 = b.B32[(which + 2) % 3];
@@ -482,6 +498,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       for (int j = 0; j < kb; ++j) ch->ritz[j] = theta_h[j];
       lam = theta_h[0];
       alpha = theta_h[kb - 1];
+      record(it32, k, 0);
       if (at_floor == k) break;
       // safety: stop when the wanted residuals improve by less than 1.05x on average
       if (score > prev_score - k * std::log(1.05)) break;
@@ -567,6 +584,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       const double rr = h[kMaxBlockWidth + j], aa = h[kMaxBlockWidth + ka + j];
       r_h[j] = (aa > 0.0) ? std::sqrt(rr / aa) : (rr > 0.0 ? INFINITY : 0.0);
     }
+    record(it, std::max(0, k - nl), nl);
     int nconv = 0;
     while (nconv < ka && r_h[nconv] <= ch->p.tol) ++nconv;
     for (int j = 0; j < nconv; ++j) {

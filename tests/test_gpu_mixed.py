@@ -81,6 +81,19 @@ def test_mixed_matches_fp64_form_on_poisson128_prefix():
     assert all(s["iters_fp32"] >= 1 for s in stm)
 
 
+def test_mixed_high_degree_matches_dense_definition():
+    """The chosen form's tuning (degree 60 in both phases) gives the same pairs."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(48, 4, seed=21)
+    p = scsf.Params(k=40, degree=60, degree_fp32=60, tol=1e-8, precision=scsf.MIXED)
+    ev, rs, vec, stats = scsf.solve(to_dev(ops, dev), p, want_vectors=True)
+    for j, op in enumerate(ops):
+        w, V = dense.smallest_eigenpairs(operators.assemble(op), 40)
+        _check(op, host(ev)[j], host(rs)[j], host(vec)[j], 40, w, V)
+    assert all(s["converged"] for s in stats)
+
+
 def test_mixed_rejects_block_width_not_multiple_of_four():
     dev = need_gpu()
     import paper_2510_23215_gb300 as scsf
