@@ -239,6 +239,44 @@ scsf_status scsf_solve_batched(scsf_ctx* ctx, scsf_batch_chain* chains, int n_ch
                                int concurrency, void* workspace, size_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
+ * Learned proposal for chain heads (Sec. 3.2 starts a chain from a random
+ * block; this network proposes a better start). A Fourier neural operator maps
+ * the coefficient field P (the sort's parameter matrix, s x s nodes, s a
+ * multiple of 32, entries > 0) to log(lambda_1), log(lambda_kb) and a 32 x 32 x 64
+ * coarse block whose span should approximate the lowest eigenvectors. The
+ * filter and the FP64 residual test still decide every result.
+ *
+ * params: FP32 [scsf_proposal_param_count()] (master copy; matrices are used
+ * in BF16, accumulation is FP32). workspace: scsf_proposal_workspace_size(batch).
+ * fields: FP64 [batch][s][s]. bounds_out: FP32 [batch][2]; block_out: FP32
+ * [batch][1024][64] (row = coarse node I*32 + J). Either output may be NULL.
+ * train_step: forward + loss + backward (+ Adam when adam_m/adam_v non-NULL,
+ * step >= 1 and lr > 0); targets_bounds FP32 [batch][2] (log-bounds),
+ * targets_Q FP32 [batch][1024][64] orthonormal; loss_host (host, 3 doubles):
+ * subspace, orthonormality and bounds terms (batch means); grad_out FP32
+ * [param_count] or NULL.
+ * targets: pools fine eigenvectors (FP64 [batch][n*n][lde], first 64 columns)
+ * over 4x4 (n/32 x n/32) blocks and orthonormalises them (Cholesky QR2, FP64).
+ * prolong: bilinear interpolation of coarse blocks to the n x n grid (zero
+ * Dirichlet boundary) into fine (FP64 [batch][n*n][ld_fine], columns 0..63). */
+size_t scsf_proposal_param_count(void);
+size_t scsf_proposal_workspace_size(int batch);
+scsf_status scsf_proposal_init(scsf_ctx* ctx, float* params, uint64_t seed);
+scsf_status scsf_proposal_forward(scsf_ctx* ctx, const float* params, const double* fields,
+                                  int batch, int s, float* bounds_out, float* block_out,
+                                  void* workspace, size_t workspace_bytes);
+scsf_status scsf_proposal_train_step(scsf_ctx* ctx, float* params, float* adam_m, float* adam_v,
+                                     int step, float lr, const double* fields, int batch, int s,
+                                     const float* targets_bounds, const float* targets_Q,
+                                     double* loss_host, float* grad_out, void* workspace,
+                                     size_t workspace_bytes);
+size_t scsf_proposal_target_scratch(void);
+scsf_status scsf_proposal_targets(scsf_ctx* ctx, const double* evecs, int batch, int n, int lde,
+                                  float* Q_out, void* scratch, size_t scratch_bytes);
+scsf_status scsf_proposal_prolong(scsf_ctx* ctx, const float* block, int batch, int n,
+                                  double* fine, int ld_fine);
+
+/* ---------------------------------------------------------------------------
  * Building blocks exported for kernel-level parity tests. Same conventions.
  *
  * scsf_cheb_filter: Y = C_m(Abar) X / C_m(t_lambda) by the scaled recurrence of

@@ -42,6 +42,9 @@ EXPORTED_SYMBOLS = [
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
     "scsf_sort_noalloc_capacity", "scsf_sort_noalloc", "scsf_cheb_filter_f32",
     "scsf_batch_workspace_size", "scsf_solve_batched",
+    "scsf_proposal_param_count", "scsf_proposal_workspace_size", "scsf_proposal_init",
+    "scsf_proposal_forward", "scsf_proposal_train_step", "scsf_proposal_target_scratch",
+    "scsf_proposal_targets", "scsf_proposal_prolong",
 ]
 
 
@@ -131,6 +134,21 @@ def library() -> ctypes.CDLL:
     L.scsf_cheb_filter_f32.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, i32, i32, dbl, dbl,
                                        dbl, vp, i32, vp, sz]
     L.scsf_cheb_filter_f32.restype = ctypes.c_int
+    L.scsf_proposal_param_count.restype = sz
+    L.scsf_proposal_workspace_size.argtypes = [i32]
+    L.scsf_proposal_workspace_size.restype = sz
+    L.scsf_proposal_init.argtypes = [vp, vp, ctypes.c_uint64]
+    L.scsf_proposal_init.restype = ctypes.c_int
+    L.scsf_proposal_forward.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, sz]
+    L.scsf_proposal_forward.restype = ctypes.c_int
+    L.scsf_proposal_train_step.argtypes = [vp, vp, vp, vp, i32, ctypes.c_float, vp, i32, i32, vp, vp,
+                                           ctypes.POINTER(dbl), vp, vp, sz]
+    L.scsf_proposal_train_step.restype = ctypes.c_int
+    L.scsf_proposal_target_scratch.restype = sz
+    L.scsf_proposal_targets.argtypes = [vp, vp, i32, i32, i32, vp, vp, sz]
+    L.scsf_proposal_targets.restype = ctypes.c_int
+    L.scsf_proposal_prolong.argtypes = [vp, vp, i32, i32, vp, i32]
+    L.scsf_proposal_prolong.restype = ctypes.c_int
     L.scsf_sort_noalloc_capacity.argtypes = []
     L.scsf_sort_noalloc_capacity.restype = sz
     L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
@@ -508,3 +526,93 @@ def small_eigh(S: torch.Tensor, ctx: Optional[Context] = None):
     cx.check(L.scsf_small_eigh(cx.handle, S.data_ptr(), k, evals.data_ptr(), Z.data_ptr(),
                                ws.data_ptr(), ws.numel()))
     return evals, Z
+
+
+class Proposal:
+    """The learned head proposal (a Fourier neural operator; all compute in libscsf).
+
+    forward(fields) -> (bounds [B, 2] log(lambda_1), log(lambda_kb); block [B, 1024, 64])
+    train_step(fields, t_bounds, t_Q, lr) -> (subspace, orthonormality, bounds) losses
+    head_block(field, n, kb, seed) -> (FP64 [n*n, kb] start block, Ritz estimates) for Chain.seed
+    """
+
+    COARSE, KY = 32, 64
+
+    def __init__(self, seed: int = 0, device="cuda", ctx: Optional[Context] = None):
+        self.ctx = _ctx(ctx, device)
+        L = library()
+        self.count = int(L.scsf_proposal_param_count())
+        dev = self.ctx.device
+        self.params = torch.empty(self.count, dtype=torch.float32, device=dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.steps = 0
+        self._ws = {}
+        self.ctx.check(L.scsf_proposal_init(self.ctx.handle, self.params.data_ptr(), seed))
+
+    def _workspace(self, batch: int) -> torch.Tensor:
+        if batch not in self._ws:
+            self._ws[batch] = _workspace(library().scsf_proposal_workspace_size(batch), self.ctx.device)
+        return self._ws[batch]
+
+    def forward(self, fields: torch.Tensor):
+        _check(fields, "fields")
+        B, s = int(fields.shape[0]), int(fields.shape[1])
+        dev = self.ctx.device
+        bounds = torch.empty((B, 2), dtype=torch.float32, device=dev)
+        block = torch.empty((B, self.COARSE * self.COARSE, self.KY), dtype=torch.float32, device=dev)
+        ws = self._workspace(B)
+        self.ctx.check(library().scsf_proposal_forward(self.ctx.handle, self.params.data_ptr(),
+                                                       fields.data_ptr(), B, s, bounds.data_ptr(),
+                                                       block.data_ptr(), ws.data_ptr(), ws.numel()))
+        return bounds, block
+
+    def _train(self, fields, t_bounds, t_Q, lr, update: bool, want_grad: bool):
+        _check(fields, "fields")
+        _check(t_bounds, "t_bounds", dtype=torch.float32)
+        _check(t_Q, "t_Q", dtype=torch.float32)
+        B, s = int(fields.shape[0]), int(fields.shape[1])
+        ws = self._workspace(B)
+        loss = (ctypes.c_double * 3)()
+        grad = torch.empty_like(self.params) if want_grad else None
+        if update:
+            self.steps += 1
+        self.ctx.check(library().scsf_proposal_train_step(
+            self.ctx.handle, self.params.data_ptr(), self.m.data_ptr() if update else None,
+            self.v.data_ptr() if update else None, self.steps if update else 0, float(lr),
+            fields.data_ptr(), B, s, t_bounds.data_ptr(), t_Q.data_ptr(), loss, _ptr(grad),
+            ws.data_ptr(), ws.numel()))
+        return (loss[0], loss[1], loss[2]), grad
+
+    def train_step(self, fields, t_bounds, t_Q, lr: float = 1e-3):
+        return self._train(fields, t_bounds, t_Q, lr, True, False)[0]
+
+    def gradient(self, fields, t_bounds, t_Q):
+        """Loss terms and the gradient w.r.t. the parameters (no update)."""
+        return self._train(fields, t_bounds, t_Q, 0.0, False, True)
+
+    def targets(self, evecs: torch.Tensor, n: int) -> torch.Tensor:
+        """Coarse orthonormal targets from fine eigenvectors [B, n*n, >= 64] (FP64)."""
+        _check(evecs, "evecs")
+        B, lde = int(evecs.shape[0]), int(evecs.shape[2])
+        Q = torch.empty((B, self.COARSE * self.COARSE, self.KY), dtype=torch.float32, device=evecs.device)
+        L = library()
+        scratch = _workspace(L.scsf_proposal_target_scratch(), evecs.device)
+        self.ctx.check(L.scsf_proposal_targets(self.ctx.handle, evecs.data_ptr(), B, n, lde,
+                                               Q.data_ptr(), scratch.data_ptr(), scratch.numel()))
+        return Q
+
+    def head_block(self, field: torch.Tensor, n: int, kb: int, seed: int = 0):
+        """Start block for a chain head: 64 prolonged proposal columns, the rest Gaussian
+        (seeded), and Ritz estimates spanning the predicted [lambda_1, lambda_kb]."""
+        bounds, block = self.forward(field.reshape(1, *field.shape).contiguous())
+        fine = torch.empty((n * n, kb), dtype=torch.float64, device=self.ctx.device)
+        if kb > self.KY:
+            g = torch.Generator(device="cpu").manual_seed(seed)
+            fine[:, self.KY:] = torch.randn((n * n, kb - self.KY), generator=g,
+                                            dtype=torch.float64).to(self.ctx.device)
+        self.ctx.check(library().scsf_proposal_prolong(self.ctx.handle, block.data_ptr(), 1, n,
+                                                       fine.data_ptr(), kb))
+        lo, hi = [math.exp(float(x)) for x in bounds[0].cpu()]
+        ritz = [lo + (hi - lo) * i / (kb - 1) for i in range(kb)]
+        return fine, ritz
