@@ -144,12 +144,12 @@ typedef struct {
   int launches;          /* kernels launched by this call                    */
   /* Per-phase device time in ms (CUDA events on the context stream), filled
    * only after scsf_set_timing(ctx, 1); zero otherwise. */
-  double t_filter_ms;    /* Alg. 3 line 3: Chebyshev filter                  */
-  double t_orth_ms;      /* line 4: deflation + Cholesky QR                  */
-  double t_rr_ms;        /* line 5: A Q and Q^T A Q                          */
-  double t_eig_ms;       /* line 6: reduced eigensolve                       */
-  double t_rot_ms;       /* line 6: rotation X = Q Z (one GEMM launch)       */
-  double t_resid_ms;     /* line 7: residual norms                           */
+  double t_filter_ms;    /* Chebyshev filter                          */
+  double t_orth_ms;      /* deflation + Cholesky QR                  */
+  double t_rr_ms;        /* A Q and Q^T A Q                          */
+  double t_eig_ms;       /* reduced eigensolve                       */
+  double t_rot_ms;       /* rotation X = Q Z (one GEMM launch)       */
+  double t_resid_ms;     /* residual norms                           */
   /* SCSF_MIXED only: the FP32 phase (counted in iters; t_filter_ms is FP64 only). */
   int iters_fp32;        /* outer iterations run in FP32                     */
   int filter32_steps;    /* FP32 stencil steps                               */
@@ -253,8 +253,10 @@ scsf_status scsf_solve_batched(scsf_ctx* ctx, scsf_batch_chain* chains, int n_ch
  * train_step: forward + loss + backward (+ Adam when adam_m/adam_v non-NULL,
  * step >= 1 and lr > 0); targets_bounds FP32 [batch][2] (log-bounds),
  * targets_Q FP32 [batch][1024][64] orthonormal; loss_host (host, 3 doubles):
- * subspace, orthonormality and bounds terms (batch means); grad_out FP32
- * [param_count] or NULL.
+ * batch means of sub = 64 - tr((G + 1e-3 I)^-1 C^T C) (G = Y^T Y, C = Q^T Y: the
+ * squared sines of the principal angles between the block and the targets),
+ * orth = |G - I|_F^2 and bounds = |s - t|^2; the objective whose gradient is taken
+ * is sub + 0.01 orth + bounds. grad_out FP32 [param_count] or NULL.
  * targets: pools fine eigenvectors (FP64 [batch][n*n][lde], first 64 columns)
  * over 4x4 (n/32 x n/32) blocks and orthonormalises them (Cholesky QR2, FP64).
  * prolong: bilinear interpolation of coarse blocks to the n x n grid (zero

@@ -14,9 +14,9 @@ Readings taken where the paper is silent or garbled:
   c = (alpha+beta)/2, e = (beta-alpha)/2; updated after every Rayleigh-Ritz.
 * Head of a chain (random start, Sec. 3.2): lambda = Gershgorin lower bound,
   alpha = lo + 2 (k_b/N)(hi - lo).
-* Alg. 3 line 5's garbled G = Q_0^T A Q is read as G = Q_a^T A Q_a over the
+* Alg. 3's Rayleigh-quotient step with its garbled G = Q_0^T A Q is read as G = Q_a^T A Q_a over the
   active (unlocked) columns of Q = qr([locked | filtered active]).
-* Locking (line 7): the leading contiguous run of active Ritz pairs (ascending
+* Locking (Alg. 3, lock step): the leading contiguous run of active Ritz pairs (ascending
   Ritz value) whose relative residual (App. D.5) is <= tol is locked; the loop
   ends once at least k pairs are locked; the k smallest locked pairs are
   returned.
@@ -70,16 +70,16 @@ def chfsi_solve(A, k: int, degree: int, tol: float, V0: np.ndarray, lam: float, 
         it += 1
         c = 0.5 * (alpha + beta)
         e = 0.5 * (beta - alpha)
-        Y = chebyshev_filter(A, X, degree, lam, c, e)                 # line 3
+        Y = chebyshev_filter(A, X, degree, lam, c, e)
         nl = locked_V.shape[1]
-        Q, _ = np.linalg.qr(np.hstack([locked_V, Y]))                 # line 4
+        Q, _ = np.linalg.qr(np.hstack([locked_V, Y]))
         Qa = Q[:, nl:]
-        G = Qa.T @ (A @ Qa)                                           # line 5
+        G = Qa.T @ (A @ Qa)
         G = 0.5 * (G + G.T)
-        w, Z = np.linalg.eigh(G)                                      # line 6
+        w, Z = np.linalg.eigh(G)
         X = Qa @ Z
         r = relative_residuals(A, X, w)
-        nconv = 0                                                     # line 7
+        nconv = 0
         while nconv < X.shape[1] and r[nconv] <= tol:
             nconv += 1
         locked_V = np.hstack([locked_V, X[:, :nconv]])

@@ -12,11 +12,16 @@ documented in the library header:
   (e^{-i theta}, theta = 2 pi (k1 x + k2 y)/32), R multiplies each mode by its
   own complex 32 x 32 matrix, and G maps back with e^{+i theta}, weight 1 for
   k2 = 0 and 2 for k2 > 0, divided by 1024;
-* heads: Y = v Wy (1024 x 64 coarse block), s = mean_nodes(v) Wb + bb;
-* loss: mean over the batch of |s - t|^2 + |(I - Q Q^T) Y|_F^2 + |Y^T Y - I|_F^2.
+* heads: Y = gelu(v Wh + bh) Wy (1024 x 64 coarse block through a 128-wide hidden
+  layer, so the block can have full rank), s = mean_nodes(v) Wb + bb;
+* loss terms, batch means: sub = 64 - tr((G + delta I)^-1 C^T C) with G = Y^T Y,
+  C = Q^T Y (the sum of squared sines of the principal angles between span Y and
+  span Q as delta -> 0), orth = |G - I|_F^2, bounds = |s - t|^2; the training
+  objective is sub + mu orth + bounds, delta = 1e-3, mu = 0.01.
 
 Parameters are one flat vector: Wl [3][32], bl [32], then per layer Rr [288][32][32],
-Ri [288][32][32], Wp [32][32], bp [32], then Wy [32][64], Wb [32][2], bb [2]; every
+Ri [288][32][32], Wp [32][32], bp [32], then Wh [32][128], bh [128], Wy [128][64],
+Wb [32][2], bb [2]; every
 block starts at a multiple of 64 entries. gelu is the tanh form
 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).
 """
@@ -24,7 +29,8 @@ from __future__ import annotations
 
 import numpy as np
 
-S, W, MODES, L, KY, CIN = 32, 32, 12, 4, 64, 3
+S, W, MODES, L, KY, H, CIN = 32, 32, 12, 4, 64, 128, 3
+DELTA, MU = 1e-3, 0.01
 K1 = np.concatenate([np.arange(MODES), np.arange(S - MODES, S)])
 K2 = np.arange(MODES)
 M = len(K1) * len(K2)
@@ -46,7 +52,9 @@ def layout():
         take(f"Ri{l}", M * W * W)
         take(f"Wp{l}", W * W)
         take(f"bp{l}", W)
-    take("Wy", W * KY)
+    take("Wh", W * H)
+    take("bh", H)
+    take("Wy", H * KY)
     take("Wb", W * 2)
     take("bb", 2)
     return off, o
@@ -59,7 +67,8 @@ def unpack(params):
     def g(name, shape):
         a, n = OFFSETS[name]
         return np.asarray(params[a:a + n], dtype=np.float64).reshape(shape)
-    p = {"Wl": g("Wl", (CIN, W)), "bl": g("bl", (W,)), "Wy": g("Wy", (W, KY)),
+    p = {"Wl": g("Wl", (CIN, W)), "bl": g("bl", (W,)), "Wh": g("Wh", (W, H)),
+         "bh": g("bh", (H,)), "Wy": g("Wy", (H, KY)),
          "Wb": g("Wb", (W, 2)), "bb": g("bb", (2,))}
     for l in range(L):
         p[f"R{l}"] = g(f"Rr{l}", (M, W, W)) + 1j * g(f"Ri{l}", (M, W, W))
@@ -86,6 +95,25 @@ def inverse_matrix():
 G_INV = inverse_matrix()
 
 
+def spectral_conv(v, R):
+    """Re(G (R (F v))) for v [B, 1024, w] (node-major) and R [M, w, w'] complex."""
+    B, w = v.shape[0], v.shape[2]
+    spec = np.fft.fft2(v.reshape(B, S, S, w), axes=(1, 2))            # e^{-i theta}
+    Vhat = spec[:, K1][:, :, K2].reshape(B, M, w)
+    Uhat = np.einsum("bmw,mwo->bmo", Vhat, R)
+    return np.real(np.einsum("pm,bmo->bpo", G_INV, Uhat))
+
+
+def block_terms(Y, Q):
+    """(sub, orth) for one block Y [P, 64] and orthonormal targets Q [P, 64]."""
+    G = Y.T @ Y
+    C = Q.T @ Y
+    Minv = np.linalg.inv(G + DELTA * np.eye(Y.shape[1]))
+    sub = Y.shape[1] - np.trace(Minv @ C.T @ C)
+    orth = np.sum((G - np.eye(Y.shape[1])) ** 2)
+    return float(sub), float(orth)
+
+
 def forward(params, fields):
     """(s [B, 2], Y [B, 1024, 64]) for fields [B, s, s] of positive coefficients."""
     p = unpack(params)
@@ -98,28 +126,22 @@ def forward(params, fields):
                    axis=-1).reshape(B, S * S, CIN)
     v = inp @ p["Wl"] + p["bl"]
     for l in range(L):
-        spec = np.fft.fft2(v.reshape(B, S, S, W), axes=(1, 2))            # e^{-i theta}
-        Vhat = spec[:, K1][:, :, K2].reshape(B, M, W)
-        Uhat = np.einsum("bmw,mwo->bmo", Vhat, p[f"R{l}"])
-        u = np.real(np.einsum("pm,bmo->bpo", G_INV, Uhat))
-        a = u + v @ p[f"Wp{l}"] + p[f"bp{l}"]
+        a = spectral_conv(v, p[f"R{l}"]) + v @ p[f"Wp{l}"] + p[f"bp{l}"]
         v = gelu(a) if l + 1 < L else a
-    Yb = v @ p["Wy"]
+    Yb = gelu(v @ p["Wh"] + p["bh"]) @ p["Wy"]
     sb = v.mean(axis=1) @ p["Wb"] + p["bb"]
     return sb, Yb
 
 
 def loss(params, fields, t_bounds, t_Q):
-    """Mean over the batch of the three loss terms; returns (subspace, orth, bounds)."""
+    """Batch means of the three loss terms: (sub, orth, bounds)."""
     sb, Yb = forward(params, fields)
     B = fields.shape[0]
     l1 = l2 = 0.0
     for b in range(B):
-        Q = t_Q[b]
-        E1 = Yb[b] - Q @ (Q.T @ Yb[b])
-        E2 = Yb[b].T @ Yb[b] - np.eye(KY)
-        l1 += np.sum(E1 * E1)
-        l2 += np.sum(E2 * E2)
+        e1, e2 = block_terms(Yb[b], t_Q[b])
+        l1 += e1
+        l2 += e2
     l3 = np.sum((sb - t_bounds) ** 2)
     return l1 / B, l2 / B, l3 / B
 
@@ -140,3 +162,9 @@ def matrix_mask():
         if not name.startswith("b"):
             mask[a:a + n] = True
     return mask
+
+
+def objective(params, fields, t_bounds, t_Q):
+    """The trained scalar: sub + mu orth + bounds."""
+    l1, l2, l3 = loss(params, fields, t_bounds, t_Q)
+    return l1 + MU * l2 + l3

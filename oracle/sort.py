@@ -18,7 +18,7 @@ import numpy as np
 
 
 def truncated_dft(P: np.ndarray, p0: int) -> np.ndarray:
-    """Alg. 2 lines 3-5: F[k1, k2] = (1/p) sum_{x,y} P[x,y] exp(-2 pi i (k1 x + k2 y)/p)."""
+    """Alg. 2, feature step: F[k1, k2] = (1/p) sum_{x,y} P[x,y] exp(-2 pi i (k1 x + k2 y)/p)."""
     p = P.shape[0]
     assert P.shape == (p, p) and 0 < p0 <= p
     k = np.arange(p0)
@@ -39,7 +39,7 @@ def squared_distance(Fa: np.ndarray, Fb: np.ndarray) -> float:
 
 
 def greedy_chain(F: np.ndarray, start: int = 0):
-    """Alg. 2 lines 6-14: nearest-neighbour chain from ``start``.
+    """Alg. 2, greedy step: nearest-neighbour chain from ``start``.
 
     Returns (perm, rel_gaps) where perm is the visiting order (int32) and
     rel_gaps[s] = (second best - best) / scale at step s, with scale the

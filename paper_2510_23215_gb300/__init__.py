@@ -531,8 +531,8 @@ def small_eigh(S: torch.Tensor, ctx: Optional[Context] = None):
 class Proposal:
     """The learned head proposal (a Fourier neural operator; all compute in libscsf).
 
-    forward(fields) -> (bounds [B, 2] log(lambda_1), log(lambda_kb); block [B, 1024, 64])
-    train_step(fields, t_bounds, t_Q, lr) -> (subspace, orthonormality, bounds) losses
+    forward(fields) -> (bounds [B, 2] log(lambda_1), log(lambda_64); block [B, 1024, 64])
+    train_step(fields, t_bounds, t_Q, lr) -> (subspace, orthonormality, bounds) loss terms
     head_block(field, n, kb, seed) -> (FP64 [n*n, kb] start block, Ritz estimates) for Chain.seed
     """
 
@@ -604,7 +604,10 @@ class Proposal:
 
     def head_block(self, field: torch.Tensor, n: int, kb: int, seed: int = 0):
         """Start block for a chain head: 64 prolonged proposal columns, the rest Gaussian
-        (seeded), and Ritz estimates spanning the predicted [lambda_1, lambda_kb]."""
+        (seeded), and Ritz estimates spanning [lambda_1, lambda_kb]. The network predicts
+        lambda_1 and lambda_64; lambda_kb is extrapolated by the 2-D Weyl law (the
+        eigenvalue count grows linearly in lambda), lambda_kb ~ lambda_64 kb / 64, so the
+        filter's damped interval starts above the whole block."""
         bounds, block = self.forward(field.reshape(1, *field.shape).contiguous())
         fine = torch.empty((n * n, kb), dtype=torch.float64, device=self.ctx.device)
         if kb > self.KY:
@@ -614,5 +617,6 @@ class Proposal:
         self.ctx.check(library().scsf_proposal_prolong(self.ctx.handle, block.data_ptr(), 1, n,
                                                        fine.data_ptr(), kb))
         lo, hi = [math.exp(float(x)) for x in bounds[0].cpu()]
+        hi = max(hi * kb / self.KY, hi)
         ritz = [lo + (hi - lo) * i / (kb - 1) for i in range(kb)]
         return fine, ritz

@@ -387,7 +387,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, launch_philox_normal(b.V, N, kb, kb, ch->p.seed, st));
     lam = lo;
     alpha = lo + 2.0 * ((double)kb / N) * (hi - lo);
-  } else {               // warm start: previous block and Ritz values (Alg. 3 line 1)
+  } else {               // warm start: previous block and Ritz values (Alg. 3, warm start)
     lam = *std::min_element(ch->ritz.begin(), ch->ritz.end());
     alpha = *std::max_element(ch->ritz.begin(), ch->ritz.end());
   }
@@ -512,7 +512,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     if (!(alpha < beta)) alpha = lam + 0.5 * (beta - lam);
     if (!(lam < alpha)) lam = alpha - 1e-3 * (beta - alpha);
     const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
-    // line 3: Chebyshev filter on the active columns
+    // filter step: Chebyshev filter on the active columns
     double* bufs[3] = {b.B0, b.B1, b.B2};
     const int lds[3] = {kb, kb, kb};
     int which = 0;
@@ -526,7 +526,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     double* Y = bufs[which];
     double* F1 = bufs[(which + 1) % 3];
     double* F2 = bufs[(which + 2) % 3];
-    // line 4: orthonormalise [locked | active]: CGS2 against the locked block, then CholQR2
+    // orthonormalise [locked | active]: CGS2 against the locked block, then CholQR2
     if (nl > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         SCSF_CUDA(ctx, launch_gemm_tn(N, nl, ka, b.V, kb, Y, kb, b.C, ka, false, b.gemm_partials, st));
@@ -544,18 +544,18 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       flops += 2.0 * N * ka * ka;
     }
     SCSF_CUDA(ctx, mark(2));
-    // line 5: Rayleigh quotient G = Q^T A Q on the active columns
+    // Rayleigh quotient G = Q^T A Q on the active columns
     SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
     SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
     SCSF_CUDA(ctx, mark(3));
-    // line 6: reduced eigenproblem and rotation back
+    // reduced eigenproblem and rotation back
     SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
     SCSF_CUDA(ctx, mark(4));
     SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
     SCSF_CUDA(ctx, mark(5));
     rot_launches += 1;
     rot_flops += 2.0 * N * ka * ka;
-    // line 7: residuals of the new Ritz pairs (App. D.5), then lock a converged prefix
+    // residuals of the new Ritz pairs (App. D.5), then lock a converged prefix
     SCSF_CUDA(ctx, launch_residual_norms(A, b.V + nl, kb, ka, b.theta, b.res_partials, b.res2, st));
     SCSF_CUDA(ctx, mark(6));
     flops += (double)N * ka * (2.0 * ka * 2 + 12.0) + 2.0 * N * ka * ka;

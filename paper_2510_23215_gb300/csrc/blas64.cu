@@ -1,5 +1,5 @@
 // FP64 block kernels for the plain path: tall-skinny Gram / projection
-// products (Alg. 3 lines 4-6), block rotation, Cholesky + triangular inverse.
+// products (Alg. 3, orthonormalisation to eigensolve), block rotation, Cholesky + triangular inverse.
 //
 // GB300 executes FP64 at about 2 FMA/clk/SM, so these kernels are bound by
 // the FP64 pipe, not by memory: they spread the work over all SMs (split-K

@@ -1,4 +1,4 @@
-// Cholesky factor and triangular inverse for Cholesky QR (Alg. 3 line 4).
+// Cholesky factor and triangular inverse for Cholesky QR (Alg. 3, orthonormalisation).
 //
 // CholQR2 factors two Gram matrices per outer iteration. The first factor only
 // has to make X R^{-1} well conditioned, so it is computed in FP32 (60x the FP64

@@ -12,10 +12,14 @@
 //            v_l = gelu(a_l) (l < L), v_L = a_L
 //            F: truncated DFT to M = 2*12 x 12 modes (+-k1, k2 >= 0), R_l: one
 //            complex W x W matrix per mode, G: Hermitian-completed inverse DFT
-//   heads  : Y = v_L Wy (S*S x 64 block); s = mean_p(v_L) Wb + bb (2 log-bounds)
-// Loss per sample: |s - t|^2 + |(I - Q Q^T) Y|_F^2 + |Y^T Y - I|_F^2, with Q an
-// orthonormal basis of the pooled true eigenvectors: invariant to rotations of
-// the target subspace, and the second term keeps the 64 columns independent.
+//   heads  : Y = gelu(v_L Wh + bh) Wy (S*S x 64 block, a pointwise 32 -> 128 -> 64 MLP so
+//            the block can have full rank); s = mean_p(v_L) Wb + bb (2 log-bounds)
+// Objective per sample: sub + mu orth + |s - t|^2 with Q an orthonormal basis of the
+// pooled true eigenvectors, G = Y^T Y, C = Q^T Y and
+//   sub  = 64 - tr((G + delta I)^-1 C^T C)   (sum of squared sines of the principal
+//          angles between span(Y) and span(Q) as delta -> 0; invariant to Y -> Y S),
+//   orth = |G - I|_F^2 (keeps the columns well conditioned), delta = 1e-3, mu = 0.01.
+// Gradient: d sub / dY = 2 (Y T - Q C M), M = (G + delta I)^-1, T = M C^T C M.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,11 +41,14 @@ constexpr int M1 = 2 * MODES;    // k1 in {0..11} U {S-12..S-1}
 constexpr int M = M1 * MODES;    // kept complex modes
 constexpr int L = 4;             // Fourier layers
 constexpr int KY = 64;           // coarse block columns
+constexpr int H = 128;           // hidden width of the block head (full-rank 64-column output)
 constexpr int CIN = 3;           // pooled log a, x, y
+constexpr double kRidge = 1e-3;  // delta in the subspace loss (G + delta I)^-1
+constexpr float kOrthWeight = 0.01f;  // mu: weight of |Y^T Y - I|^2 in the objective
 
 // flat FP32 parameter layout
 struct Layout {
-  size_t Wl, bl, Rr[L], Ri[L], Wp[L], bp[L], Wy, Wb, bb, total;
+  size_t Wl, bl, Rr[L], Ri[L], Wp[L], bp[L], Wh, bh, Wy, Wb, bb, total;
   Layout() {
     size_t o = 0;
     auto take = [&](size_t n) { size_t r = o; o += (n + 63) & ~size_t(63); return r; };
@@ -53,7 +60,9 @@ struct Layout {
       Wp[l] = take(W * W);
       bp[l] = take(W);
     }
-    Wy = take(W * KY);
+    Wh = take(W * H);
+    bh = take(H);
+    Wy = take(H * KY);
     Wb = take(W * 2);
     bb = take(2);
     total = o;
@@ -219,39 +228,99 @@ __global__ void to_bf16_kernel(long long count, const float* __restrict__ in,
   if (e < count) out[e] = __float2bfloat16_rn(in[e]);
 }
 
-__global__ void colsum_kernel(long long rows, int w, const float* __restrict__ x,
-                              float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= w) return;
-  float s = 0.f;
-  for (long long r = 0; r < rows; ++r) s += x[r * w + c];
-  out[c] = s;
-}
+// column sums of x [rows][w] in two deterministic stages: kColsumChunks row chunks of
+// partial sums (32 columns x 8 row lanes per block), then one sum per column
+constexpr int kColsumChunks = 64;
 
-// per-sample loss pieces; dY = (2 E1 + 4 Y (Y^T Y - I)) / B, ds = 2 (s - t) / B
-__global__ void block_loss_grad_kernel(int batch, const float* __restrict__ Y,
-                                       const float* __restrict__ E1, const float* __restrict__ YtY,
-                                       float* __restrict__ dY_scaled_E1, float* __restrict__ SmI) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n1 = (long long)batch * P * KY, n2 = (long long)batch * KY * KY;
-  if (e < n1) dY_scaled_E1[e] = 2.f * E1[e] / batch;
-  if (e < n2) {
-    const int ij = (int)(e % (KY * KY)), i = ij / KY, j = ij - i * KY;
-    SmI[e] = (YtY[e] - (i == j ? 1.f : 0.f)) * (4.f / batch);
+__global__ void colsum_partial_kernel(long long rows, int w, const float* __restrict__ x,
+                                      float* __restrict__ part) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const long long chunk = (rows + kColsumChunks - 1) / kColsumChunks;
+  const long long r0 = blockIdx.y * chunk;
+  const long long r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  float s = 0.f;
+  if (c < w)
+    for (long long r = r0 + threadIdx.y; r < r1; r += 8) s += x[r * w + c];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < w) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    part[(size_t)blockIdx.y * w + c] = t;
   }
 }
 
-__global__ void loss_reduce_kernel(int batch, const float* __restrict__ E1,
-                                   const float* __restrict__ YtY, const float* __restrict__ s,
-                                   const float* __restrict__ t, float* __restrict__ ds,
-                                   double* __restrict__ loss3) {
+__global__ void colsum_final_kernel(int w, const float* __restrict__ part, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= w) return;
+  float s = 0.f;
+  for (int i = 0; i < kColsumChunks; ++i) s += part[(size_t)i * w + c];
+  out[c] = s;
+}
+
+void colsum(long long rows, int w, const float* x, float* out, float* part, cudaStream_t st) {
+  colsum_partial_kernel<<<dim3((w + 31) / 32, kColsumChunks), dim3(32, 8), 0, st>>>(rows, w, x, part);
+  note_launch();
+  colsum_final_kernel<<<(w + 127) / 128, 128, 0, st>>>(w, part, out);
+  note_launch();
+}
+
+// M = (G + delta I)^-1 per sample (G = Y^T Y, K x K SPD): in-place Gauss-Jordan in FP64
+// shared memory, no pivoting (the ridge keeps every pivot positive), one CTA per sample.
+__global__ void __launch_bounds__(256) ridge_inverse_kernel(const float* __restrict__ G,
+                                                            float* __restrict__ Minv) {
+  __shared__ double a[KY][KY + 1];
+  __shared__ double colp[KY], rowp[KY];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const float* g = G + (size_t)b * KY * KY;
+  for (int e = tid; e < KY * KY; e += blockDim.x) {
+    const int i = e / KY, j = e - i * KY;
+    a[i][j] = 0.5 * ((double)g[i * KY + j] + (double)g[j * KY + i]) + (i == j ? kRidge : 0.0);
+  }
+  for (int p = 0; p < KY; ++p) {
+    __syncthreads();
+    if (tid < KY) colp[tid] = a[tid][p];
+    __syncthreads();
+    const double piv = 1.0 / colp[p];
+    if (tid < KY) rowp[tid] = (tid == p ? 1.0 : a[p][tid]) * piv;
+    __syncthreads();
+    for (int e = tid; e < KY * KY; e += blockDim.x) {
+      const int i = e / KY, j = e - i * KY;
+      if (i == p) a[i][j] = rowp[j];
+      else a[i][j] = (j == p ? 0.0 : a[i][j]) - colp[i] * rowp[j];
+    }
+  }
+  __syncthreads();
+  float* m = Minv + (size_t)b * KY * KY;
+  for (int e = tid; e < KY * KY; e += blockDim.x) {
+    const int i = e / KY, j = e - i * KY;
+    m[e] = (float)(0.5 * (a[i][j] + a[j][i]));
+  }
+}
+
+// S = (2 T + 4 mu (G - I)) / B, the right factor of the Y-part of dY
+__global__ void block_grad_factor_kernel(int batch, const float* __restrict__ T,
+                                         const float* __restrict__ G, float* __restrict__ S) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)batch * KY * KY) return;
+  const int ij = (int)(e % (KY * KY)), i = ij / KY, j = ij - i * KY;
+  S[e] = (2.f * T[e] + 4.f * kOrthWeight * (G[e] - (i == j ? 1.f : 0.f))) / batch;
+}
+
+// batch means of: K - sum(M o C^T C) (subspace), |G - I|^2 (orthonormality), |s - t|^2
+// (bounds); ds = 2 (s - t) / B
+__global__ void loss_reduce_kernel(int batch, const float* __restrict__ Minv,
+                                   const float* __restrict__ CtC, const float* __restrict__ G,
+                                   const float* __restrict__ s, const float* __restrict__ t,
+                                   float* __restrict__ ds, double* __restrict__ loss3) {
   __shared__ double red[3][256];
   double l1 = 0, l2 = 0, l3 = 0;
-  const long long n1 = (long long)batch * P * KY, n2 = (long long)batch * KY * KY;
-  for (long long e = threadIdx.x; e < n1; e += blockDim.x) l1 += (double)E1[e] * E1[e];
+  const long long n2 = (long long)batch * KY * KY;
   for (long long e = threadIdx.x; e < n2; e += blockDim.x) {
     const int ij = (int)(e % (KY * KY)), i = ij / KY, j = ij - i * KY;
-    const double d = YtY[e] - (i == j ? 1.0 : 0.0);
+    l1 -= (double)Minv[e] * CtC[e];
+    const double d = G[e] - (i == j ? 1.0 : 0.0);
     l2 += d * d;
   }
   for (int e = threadIdx.x; e < batch * 2; e += blockDim.x) {
@@ -268,8 +337,11 @@ __global__ void loss_reduce_kernel(int batch, const float* __restrict__ E1,
       for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) loss3[q] = red[q][0] / batch;
+  if (threadIdx.x == 0) {
+    loss3[0] = (double)KY + red[0][0] / batch;
+    loss3[1] = red[1][0] / batch;
+    loss3[2] = red[2][0] / batch;
+  }
 }
 
 // dWb[w][j] = sum_b g[b][w] ds[b][j]; dbb[j] = sum_b ds[b][j]; dv4 += (ds Wb^T)/P broadcast
@@ -358,10 +430,10 @@ unsigned nb(long long count, int t = 256) { return (unsigned)((count + t - 1) / 
 
 // ---- workspace -------------------------------------------------------------
 struct Acts {
-  float *in, *v[L + 1], *a[L + 1], *Vr[L], *Vi[L], *Ur, *Ui, *Y, *g, *s;
+  float *in, *v[L + 1], *a[L + 1], *Vr[L], *Vi[L], *Ur, *Ui, *hpre, *hid, *dhid, *Y, *g, *s;
   float *Fr, *Fi, *Gr, *Gs;
   // backward
-  float *dv, *dvp, *da, *dUr, *dUi, *dVr, *dVi, *E1, *C1, *YtY, *SmI, *dY, *ds;
+  float *dv, *dvp, *da, *dUr, *dUi, *dVr, *dVi, *C1, *YtY, *CtC, *Mi, *Tt, *CM, *SmI, *dY, *ds, *part;
   float* grad;
   __nv_bfloat16* wb;  // bf16 copy of the parameters
   double* loss3;
@@ -382,6 +454,9 @@ Acts carve_acts(Cv& c, int B) {
   }
   a.Ur = c.template take<float>(bmw);
   a.Ui = c.template take<float>(bmw);
+  a.hpre = c.template take<float>((size_t)B * P * H);
+  a.hid = c.template take<float>((size_t)B * P * H);
+  a.dhid = c.template take<float>((size_t)B * P * H);
   a.Y = c.template take<float>((size_t)B * P * KY);
   a.g = c.template take<float>((size_t)B * W);
   a.s = c.template take<float>((size_t)B * 2);
@@ -396,12 +471,16 @@ Acts carve_acts(Cv& c, int B) {
   a.dUi = c.template take<float>(bmw);
   a.dVr = c.template take<float>(bmw);
   a.dVi = c.template take<float>(bmw);
-  a.E1 = c.template take<float>((size_t)B * P * KY);
   a.C1 = c.template take<float>((size_t)B * KY * KY);
   a.YtY = c.template take<float>((size_t)B * KY * KY);
   a.SmI = c.template take<float>((size_t)B * KY * KY);
+  a.CtC = c.template take<float>((size_t)B * KY * KY);
+  a.Mi = c.template take<float>((size_t)B * KY * KY);
+  a.Tt = c.template take<float>((size_t)B * KY * KY);
+  a.CM = c.template take<float>((size_t)B * KY * KY);
   a.dY = c.template take<float>((size_t)B * P * KY);
   a.ds = c.template take<float>((size_t)B * 2);
+  a.part = c.template take<float>((size_t)kColsumChunks * H);
   a.grad = c.template take<float>(kLay.total);
   a.wb = c.template take<__nv_bfloat16>(kLay.total);
   a.loss3 = c.template take<double>(4);
@@ -462,8 +541,11 @@ cudaError_t forward(const Acts& A, const float* prm, int B, int s, const double*
     bias_act_kernel<<<nb(BP * W), 256, 0, st>>>(BP, W, prm + kLay.bp[l], al, A.v[l + 1], l + 1 < L);
     note_launch();
   }
-  // heads
-  LTRY(bgemm(1, (int)BP, KY, W, 1.f, A.v[L], W, 0, false, w + kLay.Wy, KY, 0, false, 0.f, A.Y, KY, 0, st));
+  // heads: Y = gelu(v_L Wh + bh) Wy
+  LTRY(bgemm(1, (int)BP, H, W, 1.f, A.v[L], W, 0, false, w + kLay.Wh, H, 0, false, 0.f, A.hpre, H, 0, st));
+  bias_act_kernel<<<nb(BP * H), 256, 0, st>>>(BP, H, prm + kLay.bh, A.hpre, A.hid, true);
+  note_launch();
+  LTRY(bgemm(1, (int)BP, KY, H, 1.f, A.hid, H, 0, false, w + kLay.Wy, KY, 0, false, 0.f, A.Y, KY, 0, st));
   mean_rows_kernel<<<nb((long long)B * W), 256, 0, st>>>(B, P, W, A.v[L], A.g);
   note_launch();
   bounds_head_kernel<<<nb(B * 2), 256, 0, st>>>(B, A.g, w + kLay.Wb, prm + kLay.bb, A.s);
@@ -477,23 +559,34 @@ cudaError_t loss_backward(const Acts& A, int B, const float* Q, const float* t, 
   const __nv_bfloat16* w = A.wb;
   const long long BP = (long long)B * P;
   const long long sPY = (long long)P * KY, sYY = (long long)KY * KY;
-  // C1 = Q^T Y, E1 = Y - Q C1, YtY = Y^T Y
+  // C = Q^T Y, G = Y^T Y, C^T C, M = (G + delta I)^-1
   LTRY(bgemm(B, KY, KY, P, 1.f, Q, KY, sPY, true, A.Y, KY, sPY, false, 0.f, A.C1, KY, sYY, st));
-  LTRY(cudaMemcpyAsync(A.E1, A.Y, sizeof(float) * BP * KY, cudaMemcpyDeviceToDevice, st));
-  LTRY(bgemm(B, P, KY, KY, -1.f, Q, KY, sPY, false, A.C1, KY, sYY, false, 1.f, A.E1, KY, sPY, st));
   LTRY(bgemm(B, KY, KY, P, 1.f, A.Y, KY, sPY, true, A.Y, KY, sPY, false, 0.f, A.YtY, KY, sYY, st));
-  loss_reduce_kernel<<<1, 256, 0, st>>>(B, A.E1, A.YtY, A.s, t, A.ds, A.loss3);
+  LTRY(bgemm(B, KY, KY, KY, 1.f, A.C1, KY, sYY, true, A.C1, KY, sYY, false, 0.f, A.CtC, KY, sYY, st));
+  ridge_inverse_kernel<<<B, 256, 0, st>>>(A.YtY, A.Mi);
   note_launch();
-  block_loss_grad_kernel<<<nb(std::max(BP * KY, (long long)B * sYY)), 256, 0, st>>>(B, A.Y, A.E1, A.YtY,
-                                                                                  A.dY, A.SmI);
+  loss_reduce_kernel<<<1, 256, 0, st>>>(B, A.Mi, A.CtC, A.YtY, A.s, t, A.ds, A.loss3);
   note_launch();
-  // dY = 2 E1 / B + Y (4 (Y^T Y - I) / B)
-  LTRY(bgemm(B, P, KY, KY, 1.f, A.Y, KY, sPY, false, A.SmI, KY, sYY, false, 1.f, A.dY, KY, sPY, st));
+  // dY = Y (2 T + 4 mu (G - I)) / B - (2 / B) Q (C M), T = M C^T C M
+  // (CM holds T = M (C^T C M) until it is overwritten with C M)
+  LTRY(bgemm(B, KY, KY, KY, 1.f, A.CtC, KY, sYY, false, A.Mi, KY, sYY, false, 0.f, A.Tt, KY, sYY, st));
+  LTRY(bgemm(B, KY, KY, KY, 1.f, A.Mi, KY, sYY, false, A.Tt, KY, sYY, false, 0.f, A.CM, KY, sYY, st));
+  block_grad_factor_kernel<<<nb((long long)B * sYY), 256, 0, st>>>(B, A.CM, A.YtY, A.SmI);
+  note_launch();
+  LTRY(bgemm(B, KY, KY, KY, 1.f, A.C1, KY, sYY, false, A.Mi, KY, sYY, false, 0.f, A.CM, KY, sYY, st));
+  LTRY(bgemm(B, P, KY, KY, 1.f, A.Y, KY, sPY, false, A.SmI, KY, sYY, false, 0.f, A.dY, KY, sPY, st));
+  LTRY(bgemm(B, P, KY, KY, -2.f / B, Q, KY, sPY, false, A.CM, KY, sYY, false, 1.f, A.dY, KY, sPY, st));
   float* g = A.grad;
   LTRY(cudaMemsetAsync(g, 0, sizeof(float) * kLay.total, st));
-  // block head: dWy = v4^T dY, dv4 = dY Wy^T
-  LTRY(bgemm(1, W, KY, (int)BP, 1.f, A.v[L], W, 0, true, A.dY, KY, 0, false, 0.f, g + kLay.Wy, KY, 0, st));
-  LTRY(bgemm(1, (int)BP, W, KY, 1.f, A.dY, KY, 0, false, w + kLay.Wy, KY, 0, true, 0.f, A.dv, W, 0, st));
+  // block head: dWy = hid^T dY, dhid = dY Wy^T, dhpre = dhid gelu'(hpre),
+  // dWh = v4^T dhpre, dbh = colsum(dhpre), dv4 = dhpre Wh^T
+  LTRY(bgemm(1, H, KY, (int)BP, 1.f, A.hid, H, 0, true, A.dY, KY, 0, false, 0.f, g + kLay.Wy, KY, 0, st));
+  LTRY(bgemm(1, (int)BP, H, KY, 1.f, A.dY, KY, 0, false, w + kLay.Wy, KY, 0, true, 0.f, A.dhid, H, 0, st));
+  gelu_back_kernel<<<nb(BP * H), 256, 0, st>>>(BP * H, A.hpre, A.dhid, A.dhid);
+  note_launch();
+  LTRY(bgemm(1, W, H, (int)BP, 1.f, A.v[L], W, 0, true, A.dhid, H, 0, false, 0.f, g + kLay.Wh, H, 0, st));
+  colsum(BP, H, A.dhid, g + kLay.bh, A.part, st);
+  LTRY(bgemm(1, (int)BP, W, H, 1.f, A.dhid, H, 0, false, w + kLay.Wh, H, 0, true, 0.f, A.dv, W, 0, st));
   // bounds head
   bounds_back_kernel<<<nb(BP * W), 256, 0, st>>>(B, A.g, A.ds, w + kLay.Wb, g + kLay.Wb, g + kLay.bb, A.dv);
   note_launch();
@@ -510,8 +603,7 @@ cudaError_t loss_backward(const Acts& A, int B, const float* Q, const float* t, 
     const float* vin = A.v[l];
     // pointwise: dWp = vin^T da, dbp = colsum(da), dvp = da Wp^T
     LTRY(bgemm(1, W, W, (int)BP, 1.f, vin, W, 0, true, da, W, 0, false, 0.f, g + kLay.Wp[l], W, 0, st));
-    colsum_kernel<<<1, 64, 0, st>>>(BP, W, da, g + kLay.bp[l]);
-    note_launch();
+    colsum(BP, W, da, g + kLay.bp[l], A.part, st);
     LTRY(bgemm(1, (int)BP, W, W, 1.f, da, W, 0, false, w + kLay.Wp[l], W, 0, true, 0.f, A.dvp, W, 0, st));
     // spectral: dUr = Gr^T da, dUi = -Gs^T da (per sample)
     LTRY(bgemm(B, M, W, P, 1.f, A.Gr, M, 0, true, da, W, (long long)P * W, false, 0.f, A.dUr, W,
@@ -542,8 +634,7 @@ cudaError_t loss_backward(const Acts& A, int B, const float* Q, const float* t, 
   }
   // lift: dWl = in^T dv0, dbl = colsum(dv0)
   LTRY(bgemm(1, CIN, W, (int)BP, 1.f, A.in, CIN, 0, true, A.dv, W, 0, false, 0.f, g + kLay.Wl, W, 0, st));
-  colsum_kernel<<<1, 64, 0, st>>>(BP, W, A.dv, g + kLay.bl);
-  note_launch();
+  colsum(BP, W, A.dv, g + kLay.bl, A.part, st);
   return cudaGetLastError();
 }
 
@@ -564,7 +655,8 @@ __global__ void init_params_kernel(float* __restrict__ p, long long count, unsig
     if (in(lay.Rr[l], (size_t)M * W * W) || in(lay.Ri[l], (size_t)M * W * W)) scale = 1.f / W;
     if (in(lay.Wp[l], W * W)) scale = 1.f / sqrtf((float)W);
   }
-  if (in(lay.Wy, W * KY)) scale = 1.f / sqrtf((float)W);
+  if (in(lay.Wh, W * H)) scale = 1.f / sqrtf((float)W);
+  if (in(lay.Wy, H * KY)) scale = 1.f / sqrtf((float)H * P);  // unit-norm block columns
   if (in(lay.Wb, W * 2)) scale = 1.f / sqrtf((float)W);
   p[e] = scale * u;
 }

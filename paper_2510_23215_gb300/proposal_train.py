@@ -1,0 +1,119 @@
+"""Training and evaluation driver for the learned head proposal.
+
+Labels come from the plain method itself: a batch of chains of -div(a grad u)
+operators is solved to the residual tolerance, and the lowest 64 eigenvectors of
+every operator are pooled to the 32 x 32 coarse grid and orthonormalised (the
+targets); log(lambda_1) and log(lambda_64) are the bound targets. The network is
+trained with Adam on a cosine learning-rate schedule, and evaluated by solving
+held-out operators as chain heads twice: from the seeded Gaussian block (Sec. 3.2)
+and from the proposal block. Both runs must reach the same residual tolerance; the
+difference in filter iterations is the gain.
+
+    python -m paper_2510_23215_gb300.proposal_train --n 128 --train 5000 --test 500
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import Chain, Operator, Params, Proposal, solve_batched
+
+
+def label(ops, n: int, params: Params, device, chunk: int = 256, chain_len: int = 16,
+          concurrency: int = 8, proposal: Proposal | None = None):
+    """(Q [B, 1024, 64] FP32 targets, bounds [B, 2] FP32 log-bounds) for ``ops``."""
+    prop = proposal or Proposal(device=device)
+    Qs, tbs = [], []
+    for c0 in range(0, len(ops), chunk):
+        dops = [Operator.from_workload(o, device) for o in ops[c0:c0 + chunk]]
+        chains = [(dops[i:i + chain_len], params) for i in range(0, len(dops), chain_len)]
+        for evals, _, evecs, _, status in solve_batched(chains, concurrency=concurrency, want_vectors=True):
+            if status != 0:
+                raise RuntimeError(f"labelling solve failed with status {status}")
+            Qs.append(prop.targets(evecs.contiguous(), n))
+            tbs.append(torch.stack([torch.log(evals[:, 0]), torch.log(evals[:, prop.KY - 1])], 1).float())
+    return torch.cat(Qs).contiguous(), torch.cat(tbs).contiguous()
+
+
+def train(prop: Proposal, fields, Q, tb, steps: int, batch: int = 32, lr: float = 1e-3,
+          seed: int = 0, log_every: int = 0):
+    """Adam steps on random minibatches with a cosine schedule; returns the logged losses."""
+    g = torch.Generator().manual_seed(seed)
+    hist = []
+    n_train = fields.shape[0]
+    for s in range(steps):
+        idx = torch.randint(0, n_train, (batch,), generator=g).to(fields.device)
+        rate = lr * 0.5 * (1.0 + np.cos(np.pi * s / steps))
+        loss = prop.train_step(fields[idx].contiguous(), tb[idx].contiguous(), Q[idx].contiguous(), lr=rate)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            hist.append((s, [round(x, 5) for x in loss]))
+    return hist
+
+
+def head_iterations(prop: Proposal, ops, fields, n: int, params: Params, device):
+    """Filter iterations of each operator solved as a chain head from the Gaussian
+    block and from the proposal, with the largest final residual of each."""
+    out = {"random": [], "proposal": [], "resid_random": 0.0, "resid_proposal": 0.0}
+    for j, o in enumerate(ops):
+        op = Operator.from_workload(o, device)
+        ch = Chain(params, n, device=device)
+        _, r1, _, st1 = ch.step(op, want_vectors=False)
+        block, ritz = prop.head_block(fields[j], n, params.kb, seed=j)
+        ch2 = Chain(params, n, device=device)
+        ch2.seed(block, ritz)
+        _, r2, _, st2 = ch2.step(op, want_vectors=False)
+        out["random"].append(int(st1["iters"]))
+        out["proposal"].append(int(st2["iters"]))
+        out["resid_random"] = max(out["resid_random"], float(r1.max()))
+        out["resid_proposal"] = max(out["resid_proposal"], float(r2.max()))
+    return out
+
+
+def run(n: int, n_train: int, n_test: int, steps: int, degree: int, lr: float, seed: int,
+        device="cuda", log_every: int = 0):
+    import scsf_inputs as si  # seeded operator generators (no method arithmetic)
+    device = torch.device(device)
+    params = Params(k=Proposal.KY, degree=degree, tol=1e-8, max_iter=400)
+    ops = si.div_a_grad_chain(n, n_train + n_test, seed=seed)
+    fields = torch.as_tensor(np.stack([o.P for o in ops]), device=device)
+    prop = Proposal(seed=seed + 1, device=device)
+    t0 = time.time()
+    Q, tb = label(ops, n, params, device, proposal=prop)
+    t_label = time.time() - t0
+    t0 = time.time()
+    hist = train(prop, fields[:n_train], Q[:n_train], tb[:n_train], steps, lr=lr, log_every=log_every)
+    t_train = time.time() - t0
+    te = slice(n_train, n_train + min(n_test, 256))
+    held, _ = prop.gradient(fields[te].contiguous(), tb[te].contiguous(), Q[te].contiguous())
+    its = head_iterations(prop, ops[n_train:], fields[n_train:], n, params, device)
+    return {
+        "n": n, "k": Proposal.KY, "kb": params.kb, "degree": degree, "train": n_train,
+        "test": n_test, "steps": steps, "label_s": round(t_label, 1), "train_s": round(t_train, 1),
+        "heldout_loss": [round(x, 5) for x in held], "train_log": hist,
+        "mean_iters_random": float(np.mean(its["random"])),
+        "mean_iters_proposal": float(np.mean(its["proposal"])),
+        "resid_random": its["resid_random"], "resid_proposal": its["resid_proposal"],
+        "iters_random": its["random"], "iters_proposal": its["proposal"],
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--train", type=int, default=5000)
+    ap.add_argument("--test", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--degree", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=77)
+    a = ap.parse_args()
+    r = run(a.n, a.train, a.test, a.steps, a.degree, a.lr, a.seed, log_every=max(1, a.steps // 8))
+    print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

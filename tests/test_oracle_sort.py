@@ -10,7 +10,7 @@ from oracle import sort
 
 @pytest.mark.parametrize("p,p0", [(8, 3), (16, 8), (7, 7)])
 def test_truncated_dft_matches_library_fft(p, p0):
-    """Alg. 2 line 4 reading: unshifted [0, p0)^2 block of the DFT, unitary 1/p scaling."""
+    """Alg. 2, truncation reading: unshifted [0, p0)^2 block of the DFT, unitary 1/p scaling."""
     P = np.random.default_rng(p).standard_normal((p, p))
     ref = np.fft.fft2(P)[:p0, :p0] / p
     np.testing.assert_allclose(sort.truncated_dft(P, p0), ref, rtol=1e-12, atol=1e-12)
