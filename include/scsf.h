@@ -155,6 +155,12 @@ typedef struct {
   int filter32_steps;    /* FP32 stencil steps                               */
   double filter32_elems; /* sum over FP32 filter steps of N * columns        */
   double t_filter32_ms;  /* FP32 filter time                                 */
+  /* SCSF_MIXED only: FP64-phase iterations filter through the defect-corrected form
+   * (FP32 recurrence on Z = Y - X diag(y(theta)) driven by the FP64 residual block;
+   * these steps are not in filter_steps / filter_elems / t_filter_ms). */
+  int filter_dc_steps;   /* defect-corrected filter steps                    */
+  double filter_dc_elems;/* sum over those steps of N * active columns       */
+  double t_filter_dc_ms; /* defect-corrected filter time                     */
   /* Optional convergence history (input): when history is a host array of at
    * least 3 * max_iter doubles, iteration i writes {max, median residual of the
    * wanted unlocked pairs, pairs locked so far} to history[3 i .. 3 i + 2]. */
@@ -300,6 +306,19 @@ scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double*
 scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const float* X, int ldx,
                                  int ncols, int degree, double lambda, double c, double e,
                                  float* Y, int ldy, void* scratch, size_t scratch_bytes);
+/* Defect-corrected filter (the mixed form's FP64-phase filter): the same Y as
+ * scsf_cheb_filter, computed as Y = X diag(y_m(theta)) + Z_m, where y_i(theta_j) runs
+ * the filter's scalar recurrence at theta_j and Z_i the block recurrence driven by
+ * s1 R diag(y_i), R = A X - X diag(theta) formed in FP64 and stored in FP32, Z in FP32.
+ * Any theta gives the same Y up to rounding; Ritz values (small R) make the FP32
+ * rounding negligible. The paper has no counterpart (its filter runs in one precision).
+ * X, Y: FP64 [N][ncols] (ldx, ldy >= ncols), theta: device FP64 [ncols],
+ * 1 <= ncols <= scsf_max_block_width(); scratch >= scsf_cheb_filter_dc_scratch(). */
+size_t scsf_cheb_filter_dc_scratch(int n, int ncols, int degree);
+scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                                const double* theta, int ncols, int degree, double lambda,
+                                double c, double e, double* Y, int ldy, void* scratch,
+                                size_t scratch_bytes);
 size_t scsf_small_eigh_scratch(int k);
 scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
                             void* scratch, size_t scratch_bytes);

@@ -45,6 +45,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_param_count", "scsf_proposal_workspace_size", "scsf_proposal_init",
     "scsf_proposal_forward", "scsf_proposal_train_step", "scsf_proposal_target_scratch",
     "scsf_proposal_targets", "scsf_proposal_prolong",
+    "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc",
 ]
 
 
@@ -76,6 +77,8 @@ class _CStats(ctypes.Structure):
                 ("t_rot_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
                 ("iters_fp32", ctypes.c_int), ("filter32_steps", ctypes.c_int),
                 ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double),
+                ("filter_dc_steps", ctypes.c_int), ("filter_dc_elems", ctypes.c_double),
+                ("t_filter_dc_ms", ctypes.c_double),
                 ("history", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -149,6 +152,11 @@ def library() -> ctypes.CDLL:
     L.scsf_proposal_targets.restype = ctypes.c_int
     L.scsf_proposal_prolong.argtypes = [vp, vp, i32, i32, vp, i32]
     L.scsf_proposal_prolong.restype = ctypes.c_int
+    L.scsf_cheb_filter_dc_scratch.argtypes = [i32, i32, i32]
+    L.scsf_cheb_filter_dc_scratch.restype = sz
+    L.scsf_cheb_filter_dc.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, vp, i32, i32, dbl,
+                                      dbl, dbl, vp, i32, vp, sz]
+    L.scsf_cheb_filter_dc.restype = ctypes.c_int
     L.scsf_sort_noalloc_capacity.argtypes = []
     L.scsf_sort_noalloc_capacity.restype = sz
     L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
@@ -499,6 +507,29 @@ def cheb_filter_f32(op: Operator, X: torch.Tensor, degree: int, lam: float, c: f
     cx.check(library().scsf_cheb_filter_f32(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols,
                                             ncols, degree, lam, c, e, Y.data_ptr(), ncols,
                                             ws.data_ptr(), ws.numel()))
+    return Y
+
+
+def cheb_filter_dc(op: Operator, X: torch.Tensor, theta: torch.Tensor, degree: int, lam: float,
+                   c: float, e: float, ctx: Optional[Context] = None) -> torch.Tensor:
+    """Alg. 1 on an FP64 block through the defect-corrected form (FP32 remainder
+    recurrence driven by the residual block of (X, theta))."""
+    _check(X, "X")
+    _check(theta, "theta")
+    cx = _ctx(ctx, X.device)
+    N, ncols = int(X.shape[0]), int(X.shape[1])
+    if N != op.n * op.n or int(theta.numel()) != ncols:
+        raise ValueError("X must have n*n rows and theta one entry per column")
+    Y = torch.empty_like(X)
+    L = library()
+    nbytes = L.scsf_cheb_filter_dc_scratch(op.n, ncols, degree)
+    if nbytes == 0:
+        raise ValueError("unsupported filter shape")
+    ws = _workspace(nbytes, X.device)
+    cop = op._c()
+    cx.check(L.scsf_cheb_filter_dc(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, theta.data_ptr(),
+                                   ncols, degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
+                                   ws.numel()))
     return Y
 
 

@@ -102,12 +102,15 @@ struct ChainBufs {
   void* eigh_scratch;
   int* status;
   int* cols;
-  // FP32 phase of the mixed form (null otherwise)
+  // FP32 phase of the mixed form (null otherwise); in the FP64 phase V32 holds the
+  // FP32 residual block of the defect-corrected filter, B32 its remainder blocks
   float *V32, *B32[3], *d32, *we32, *wn32, *partials32;
+  float* ytab;  // [degree][kb] scalar filter values at the Ritz values
+  double* ym;   // [kb]
 };
 
 template <typename Cv>
-void carve_chain(Cv& c, int n, int kb, bool mixed, ChainBufs& b) {
+void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   const size_t N = (size_t)n * n;
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
@@ -135,7 +138,11 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, ChainBufs& b) {
   b.cols = c.template take<int>(kb);
   b.V32 = b.d32 = b.we32 = b.wn32 = b.partials32 = nullptr;
   b.B32[0] = b.B32[1] = b.B32[2] = nullptr;
+  b.ytab = nullptr;
+  b.ym = nullptr;
   if (mixed) {
+    b.ytab = c.template take<float>((size_t)std::max(degree, 1) * kb);
+    b.ym = c.template take<double>(kb);
     b.V32 = c.template take<float>(blk);
     for (auto& p : b.B32) p = c.template take<float>(blk);
     b.d32 = c.template take<float>(N);
@@ -214,6 +221,59 @@ cudaError_t run_filter_f32(const Stencil32& A, const float* Y0, int ld0, int nco
   }
   *which = cur;
   return cudaSuccess;
+}
+
+template <typename Cv>
+void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3], double** d,
+                     double** we, double** wn, float** d32, float** we32, float** wn32,
+                     double** part, double** bnd, double** rpart, double** res2, float** ytab,
+                     double** ym) {
+  const size_t N = (size_t)n * n;
+  *R = cv.template take<float>(N * ncols);
+  for (int i = 0; i < 3; ++i) z[i] = cv.template take<float>(N * ncols);
+  *d = cv.template take<double>(N);
+  *we = cv.template take<double>(N);
+  *wn = cv.template take<double>(N);
+  *d32 = cv.template take<float>(N);
+  *we32 = cv.template take<float>(N);
+  *wn32 = cv.template take<float>(N);
+  *part = cv.template take<double>(2 * (size_t)assemble_blocks(n));
+  *bnd = cv.template take<double>(2);
+  *rpart = cv.template take<double>((size_t)resid_blocks(n) * 2 * ncols);
+  *res2 = cv.template take<double>(2 * (size_t)ncols);
+  *ytab = cv.template take<float>((size_t)std::max(degree, 1) * ncols);
+  *ym = cv.template take<double>(ncols);
+}
+
+// Defect-corrected filter of the FP64 phase (mixed form): X (FP64, ncols active
+// columns) with its residual block R = A X - X diag(theta) (FP32) and Ritz values theta
+// (device). The remainder Z runs through zb; Y = X diag(y_m) + Z_m lands in Y (FP64).
+cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const float* R, int ldr,
+                          const double* theta, int ncols, int degree, double lam, double c,
+                          double e, float* const zb[3], int ldz, float* ytab, double* ym,
+                          double* Y, int ldy, cudaStream_t st) {
+  cudaError_t err = launch_dc_ytab(theta, ncols, degree, lam, c, e, ytab, ym, st);
+  if (err != cudaSuccess) return err;
+  const double sigma1 = e / (lam - c);
+  // Z_1 = s1 R diag(y_0), y_0 = 1
+  err = launch_cheb_step_dc(A, nullptr, nullptr, ldz, R, ldr, ytab, zb[0], ncols,
+                            (float)(sigma1 / e), 0.f, 0.f, st);
+  if (err != cudaSuccess) return err;
+  double sigma = sigma1;
+  const float* prev = nullptr;  // Z_0 = 0
+  int cur = 0;
+  for (int i = 1; i < degree; ++i) {
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    const int nxt = i % 3;
+    err = launch_cheb_step_dc(A, zb[cur], prev, ldz, R, ldr, ytab + (size_t)i * ncols, zb[nxt],
+                              ncols, (float)(2.0 * sigma_next / e), (float)(-2.0 * sigma_next * c / e),
+                              (float)(-sigma_next * sigma), st);
+    if (err != cudaSuccess) return err;
+    prev = zb[cur];
+    cur = nxt;
+    sigma = sigma_next;
+  }
+  return launch_dc_combine(A.n * A.n, ncols, X, ldx, ym, zb[cur], ldz, Y, ldy, st);
 }
 
 }  // namespace
@@ -305,7 +365,7 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, n_max, kb, params->precision == SCSF_MIXED, b);
+  carve_chain(c, n_max, kb, params->precision == SCSF_MIXED, params->degree, b);
   return c.used;
 }
 
@@ -337,7 +397,7 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
   ch->N = n * n;
   ch->kb = kb;
   Carve c(workspace, workspace_bytes);
-  carve_chain(c, n, kb, params->precision == SCSF_MIXED, ch->b);
+  carve_chain(c, n, kb, params->precision == SCSF_MIXED, params->degree, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -421,14 +481,21 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   bool fp32_first = true;  // first Cholesky QR factor in FP32
   int it32 = 0, filter32_steps = 0;
   double felems32 = 0.0, t_filter32 = 0.0;
+  // defect-corrected filter of the mixed form's FP64 phase: residual block in b.V32
+  // (columns aligned with b.V), Ritz values of the active columns at dc_theta
+  const bool mixed = ch->p.precision == SCSF_MIXED;
+  const Stencil32 A32{b.d32, b.we32, b.wn32, n};
+  bool have_R = false;
+  const double* dc_theta = nullptr;
+  int dc_steps = 0;
+  double dc_elems = 0.0, t_filter_dc = 0.0;
 
   // FP32 phase of the mixed form: the whole block iterates in FP32 (filter, Cholesky
   // QR, Rayleigh-Ritz, rotation) without locking, until the wanted residuals stop
   // improving, i.e. the subspace has converged to FP32 accuracy. FP32 storage floors
   // the relative residual near eps32 ||A|| / lambda, so locking at the tolerance is
   // left to the FP64 phase, which starts from this block.
-  if (ch->p.precision == SCSF_MIXED) {
-    const Stencil32 A32{b.d32, b.we32, b.wn32, n};
+  if (mixed) {
     SCSF_CUDA(ctx, launch_to_f32(b.d, b.d32, N, st));
     SCSF_CUDA(ctx, launch_to_f32(b.we, b.we32, N, st));
     SCSF_CUDA(ctx, launch_to_f32(b.wn, b.wn32, N, st));
@@ -505,6 +572,12 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       prev_score = score;
     }
     SCSF_CUDA(ctx, launch_block_f32_to_f64(N, kb, b.V32, kb, b.V, kb, st));
+    if (it32 > 0) {  // FP64 residual block of the FP32 phase's Ritz pairs
+      SCSF_CUDA(ctx, launch_residual_norms(A, b.V, kb, kb, b.theta, b.res_partials, b.res2, st,
+                                           b.V32, kb));
+      have_R = true;
+      dc_theta = b.theta;
+    }
   }
 
   for (it = it32 + 1; it <= ch->p.max_iter; ++it) {
@@ -516,13 +589,21 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     double* bufs[3] = {b.B0, b.B1, b.B2};
     const int lds[3] = {kb, kb, kb};
     int which = 0;
+    const bool dc = mixed && have_R;
     SCSF_CUDA(ctx, mark(0));
-    SCSF_CUDA(ctx, run_filter(A, b.V + nl, kb, ka, m, lam, c, e, bufs, lds, &which, st));
+    if (dc) {
+      SCSF_CUDA(ctx, run_filter_dc(A32, b.V + nl, kb, b.V32 + nl, kb, dc_theta, ka, m, lam, c, e,
+                                   b.B32, kb, b.ytab, b.ym, bufs[0], kb, st));
+      dc_steps += m;
+      dc_elems += (double)m * N * ka;
+    } else {
+      SCSF_CUDA(ctx, run_filter(A, b.V + nl, kb, ka, m, lam, c, e, bufs, lds, &which, st));
+      filter_steps += m;
+      felems += (double)m * N * ka;
+      fbytes += (double)m * N * ka * 24.0;
+      flops += (double)m * N * ka * 14.0;
+    }
     SCSF_CUDA(ctx, mark(1));
-    filter_steps += m;
-    felems += (double)m * N * ka;
-    fbytes += (double)m * N * ka * 24.0;
-    flops += (double)m * N * ka * 14.0;
     double* Y = bufs[which];
     double* F1 = bufs[(which + 1) % 3];
     double* F2 = bufs[(which + 2) % 3];
@@ -556,7 +637,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     rot_launches += 1;
     rot_flops += 2.0 * N * ka * ka;
     // residuals of the new Ritz pairs (App. D.5), then lock a converged prefix
-    SCSF_CUDA(ctx, launch_residual_norms(A, b.V + nl, kb, ka, b.theta, b.res_partials, b.res2, st));
+    SCSF_CUDA(ctx, launch_residual_norms(A, b.V + nl, kb, ka, b.theta, b.res_partials, b.res2, st,
+                                         mixed ? b.V32 + nl : nullptr, kb));
     SCSF_CUDA(ctx, mark(6));
     flops += (double)N * ka * (2.0 * ka * 2 + 12.0) + 2.0 * N * ka * ka;
     SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, ka * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -569,7 +651,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       for (int i = 0; i < 6; ++i) {
         float ms = 0.f;
         SCSF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
-        tms[i] += ms;
+        if (i == 0 && dc) t_filter_dc += ms;
+        else tms[i] += ms;
       }
     }
     int chol_status[2];
@@ -593,6 +676,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     }
     for (int j = 0; j < ka; ++j) ch->ritz[nl + j] = theta_h[j];
     nl += nconv;
+    have_R = mixed;
+    dc_theta = b.theta + nconv;
     if (nl >= k) {
       converged = true;
       break;
@@ -657,6 +742,9 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     stats->filter32_steps = filter32_steps;
     stats->filter32_elems = felems32;
     stats->t_filter32_ms = t_filter32;
+    stats->filter_dc_steps = dc_steps;
+    stats->filter_dc_elems = dc_elems;
+    stats->t_filter_dc_ms = t_filter_dc;
   }
   if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
   return SCSF_OK;
@@ -780,6 +868,48 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
   if (rot[which] != Y)
     SCSF_CUDA(ctx, cudaMemcpyAsync(Y, rot[which], N * ncols * sizeof(float),
                                    cudaMemcpyDeviceToDevice, st));
+  return SCSF_OK;
+}
+
+size_t scsf_cheb_filter_dc_scratch(int n, int ncols, int degree) {
+  if (n < 1 || ncols < 1 || ncols > kMaxBlockWidth || degree < 1) return 0;
+  SizeCarve sc;
+  float *R, *z[3], *d32, *we32, *wn32, *ytab;
+  double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
+  carve_filter_dc(sc, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
+                  &rpart, &res2, &ytab, &ym);
+  return sc.used + 256;
+}
+
+scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                                const double* theta, int ncols, int degree, double lambda,
+                                double c, double e, double* Y, int ldy, void* scratch,
+                                size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!op_ok(op) || !X || !Y || !theta || !scratch)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  if (ncols < 1 || ncols > kMaxBlockWidth || ldx < ncols || ldy < ncols || degree < 1 ||
+      !(e > 0.0) || lambda == c)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 160, ld >= ncols, valid filter parameters");
+  const int n = op->n;
+  Carve cv(scratch, scratch_bytes);
+  float *R, *z[3], *d32, *we32, *wn32, *ytab;
+  double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
+  carve_filter_dc(cv, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
+                  &rpart, &res2, &ytab, &ym);
+  if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const size_t N = (size_t)n * n;
+  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
+  SCSF_CUDA(ctx, launch_to_f32(d, d32, N, st));
+  SCSF_CUDA(ctx, launch_to_f32(we, we32, N, st));
+  SCSF_CUDA(ctx, launch_to_f32(wn, wn32, N, st));
+  const Stencil A{d, we, wn, n};
+  const Stencil32 A32{d32, we32, wn32, n};
+  SCSF_CUDA(ctx, launch_residual_norms(A, X, ldx, ncols, theta, rpart, res2, st, R, ncols));
+  SCSF_CUDA(ctx, run_filter_dc(A32, X, ldx, R, ncols, theta, ncols, degree, lambda, c, e, z, ncols,
+                               ytab, ym, Y, ldy, st));
   return SCSF_OK;
 }
 

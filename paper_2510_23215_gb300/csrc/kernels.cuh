@@ -37,11 +37,12 @@ cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, c
                                  double s3, cudaStream_t st);
 
 // Column sums of r_j = ||(A X)_j - theta_j X_j||^2 and ||(A X)_j||^2 without
-// storing A X. partials: [resid_blocks(n)][2][ncols]; out2: [2][ncols].
+// storing A X. partials: [resid_blocks(n)][2][ncols]; out2: [2][ncols]. With R32
+// non-null the residual block A X - X diag(theta) is also stored there in FP32 (ld ldr).
 int resid_blocks(int n);
 cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
                                   const double* theta, double* partials, double* out2,
-                                  cudaStream_t st);
+                                  cudaStream_t st, float* R32 = nullptr, int ldr = 0);
 
 // ---- FP64 block BLAS (blas64.cu) ----------------------------------------
 // C[m x n] = A^T B over `rows` rows, A: rows x m (lda), B: rows x n (ldb).
@@ -90,6 +91,20 @@ cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, 
 cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ldx, int ncols,
                                       const double* theta, double* partials, double* out2,
                                       cudaStream_t st);
+// Defect-corrected filter (any ncols and leading dimensions): with R = A X - X diag(theta),
+// the filtered block is Y_m = X diag(y_m(theta)) + Z_m, where y_i are the scalar
+// recurrences of the filter at the Ritz values and Z_i obeys the same recurrence with
+// the extra term s1 R diag(y_i) (Z_0 = 0). Z is small when R is, so FP32 suffices.
+//   ytab: per column y_0 .. y_{degree-1} (FP32, [degree][ncols]) and y_degree (FP64, ym)
+cudaError_t launch_dc_ytab(const double* theta, int ncols, int degree, double lam, double c,
+                           double e, float* ytab, double* ym, cudaStream_t st);
+// out = s1 (A cur) + s2 cur + s3 prev + s1 R diag(ycol); cur == nullptr means Z_0 = 0.
+cudaError_t launch_cheb_step_dc(const Stencil32& A, const float* cur, const float* prev, int ld,
+                                const float* R, int ldr, const float* ycol, float* out,
+                                int ncols, float s1, float s2, float s3, cudaStream_t st);
+// Y = X diag(ym) + Z in FP64.
+cudaError_t launch_dc_combine(int rows, int ncols, const double* X, int ldx, const double* ym,
+                              const float* Z, int ldz, double* Y, int ldy, cudaStream_t st);
 size_t gemm_tn_f32_partials(int rows, int m, int n, bool symmetric);
 cudaError_t launch_gemm_tn_f32(int rows, int m, int n, const float* A, int lda, const float* B,
                                int ldb, double* C, int ldc, bool symmetric, float* partials,

@@ -69,6 +69,76 @@ cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
   st4(out + (size_t)I * ldo + c, r);
 }
 
+// ---- defect-corrected filter ------------------------------------------------
+// The filter's three-term recurrence Y_{i+1} = s1 A Y_i + s2 Y_i + s3 Y_{i-1} started
+// from Y_0 = X splits exactly as Y_i = X diag(y_i) + Z_i: y_i(theta_j) is the same
+// recurrence on the scalar theta_j, and with A X = X diag(theta) + R the remainder obeys
+// Z_{i+1} = s1 A Z_i + s2 Z_i + s3 Z_{i-1} + s1 R diag(y_i), Z_0 = 0. Near convergence
+// Z is of the size of R, so it is computed in FP32 while X diag(y_m) stays in FP64:
+// the result has FP64 accuracy at the cost of an FP32 stencil sweep.
+
+// One thread per column: y_0 .. y_{m-1} (FP32) and y_m (FP64), with the scaled
+// coefficients of the filter (sigma_1 = e / (lam - c), sigma_{i+1} = 1 / (2 / sigma_1 - sigma_i)).
+__global__ void dc_ytab_kernel(const double* __restrict__ theta, int ncols, int degree, double lam,
+                               double c, double e, float* __restrict__ ytab, double* __restrict__ ym) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  const double t = theta[j];
+  const double sigma1 = e / (lam - c);
+  double y_prev = 1.0, y = sigma1 * (t - c) / e, sigma = sigma1;
+  ytab[j] = 1.f;
+  for (int i = 1; i < degree; ++i) {
+    ytab[(size_t)i * ncols + j] = (float)y;
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    const double y_next = 2.0 * sigma_next * (t - c) / e * y - sigma_next * sigma * y_prev;
+    y_prev = y;
+    y = y_next;
+    sigma = sigma_next;
+  }
+  ym[j] = y;
+}
+
+constexpr int kDcRows = 8;
+__global__ void __launch_bounds__(32 * kDcRows)
+cheb_step_dc_kernel(Stencil32 A, const float* __restrict__ cur, const float* __restrict__ prev,
+                    int ld, const float* __restrict__ R, int ldr, const float* __restrict__ ycol,
+                    float* __restrict__ out, int ncols, float s1, float s2, float s3) {
+  const int n = A.n, N = n * n;
+  for (int I = blockIdx.x * kDcRows + threadIdx.y; I < N; I += gridDim.x * kDcRows) {
+    const int i = I / n, j = I - i * n;
+    const float d = A.d[I];
+    const float wS = (i < n - 1) ? A.we[I] : 0.f, wN = (i > 0) ? A.we[I - n] : 0.f;
+    const float wE = (j < n - 1) ? A.wn[I] : 0.f, wW = (j > 0) ? A.wn[I - 1] : 0.f;
+    const size_t o = (size_t)I * ld;
+    for (int c = threadIdx.x; c < ncols; c += 32) {
+      float r = s1 * R[(size_t)I * ldr + c] * ycol[c];
+      if (cur) {
+        const float* row = cur + o + c;
+        float acc = 0.f;
+        if (i < n - 1) acc = fmaf(wS, row[(size_t)n * ld], acc);
+        if (i > 0) acc = fmaf(wN, row[-(long long)n * ld], acc);
+        if (j < n - 1) acc = fmaf(wE, row[ld], acc);
+        if (j > 0) acc = fmaf(wW, row[-(long long)ld], acc);
+        const float y = row[0];
+        r = fmaf(s1, fmaf(d, y, -acc), fmaf(s2, y, r));
+      }
+      if (prev) r = fmaf(s3, prev[o + c], r);
+      out[o + c] = r;
+    }
+  }
+}
+
+__global__ void dc_combine_kernel(int rows, int ncols, const double* __restrict__ X, int ldx,
+                                  const double* __restrict__ ym, const float* __restrict__ Z, int ldz,
+                                  double* __restrict__ Y, int ldy) {
+  const long long tot = (long long)rows * ncols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(e / ncols), c = (int)(e - (long long)I * ncols);
+    Y[(size_t)I * ldy + c] = fma(X[(size_t)I * ldx + c], ym[c], (double)Z[(size_t)I * ldz + c]);
+  }
+}
+
 // Per-column ||(A X)_j - theta_j X_j||^2 and ||(A X)_j||^2 (FP32 products, FP64 sums).
 constexpr int kRows32 = 8;
 __global__ void __launch_bounds__(32 * kRows32)
@@ -369,6 +439,35 @@ cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float*
   if (rows <= 0 || n <= 0) return cudaSuccess;
   dim3 grid((n + TT - 1) / TT, (rows + 63) / 64);
   gemm_nn_f32_kernel<<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc, upper);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dc_ytab(const double* theta, int ncols, int degree, double lam, double c,
+                           double e, float* ytab, double* ym, cudaStream_t st) {
+  if (ncols < 1 || degree < 1) return cudaErrorInvalidValue;
+  dc_ytab_kernel<<<(ncols + 127) / 128, 128, 0, st>>>(theta, ncols, degree, lam, c, e, ytab, ym);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step_dc(const Stencil32& A, const float* cur, const float* prev, int ld,
+                                const float* R, int ldr, const float* ycol, float* out,
+                                int ncols, float s1, float s2, float s3, cudaStream_t st) {
+  if (ncols < 1 || ld < ncols || ldr < ncols) return cudaErrorInvalidValue;
+  const long long N = (long long)A.n * A.n;
+  const int nb = (int)std::min<long long>((N + kDcRows - 1) / kDcRows, 152LL * 16);
+  cheb_step_dc_kernel<<<nb, dim3(32, kDcRows), 0, st>>>(A, cur, (s3 != 0.f) ? prev : nullptr, ld,
+                                                        R, ldr, ycol, out, ncols, s1, s2, s3);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dc_combine(int rows, int ncols, const double* X, int ldx, const double* ym,
+                              const float* Z, int ldz, double* Y, int ldy, cudaStream_t st) {
+  const long long tot = (long long)rows * ncols;
+  const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
+  dc_combine_kernel<<<nb, 256, 0, st>>>(rows, ncols, X, ldx, ym, Z, ldz, Y, ldy);
   note_launch();
   return cudaGetLastError();
 }

@@ -139,7 +139,8 @@ cheb_step_f64_kernel(Stencil A, const double* __restrict__ cur, int ldc,
 
 __global__ void __launch_bounds__(32 * kRowsPerBlock)
 residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncols,
-                      const double* __restrict__ theta, double* __restrict__ partials) {
+                      const double* __restrict__ theta, double* __restrict__ partials,
+                      float* __restrict__ R32, int ldr) {
   const int N = A.n * A.n;
   double rr[kMaxColChunks], aa[kMaxColChunks];
 #pragma unroll
@@ -154,6 +155,7 @@ residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncol
         const double x = row[c];
         const double ax = fma(k.d, x, -offdiag_sum(k, A.n, row, (size_t)ldx, c));
         const double r = fma(-theta[c], x, ax);
+        if (R32) R32[(size_t)I * ldr + c] = (float)r;
         rr[q] = fma(r, r, rr[q]);
         aa[q] = fma(ax, ax, aa[q]);
       }
@@ -232,10 +234,11 @@ int resid_blocks(int n) {
 
 cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
                                   const double* theta, double* partials, double* out2,
-                                  cudaStream_t st) {
-  if (ncols > kMaxBlockWidth) return cudaErrorInvalidValue;
+                                  cudaStream_t st, float* R32, int ldr) {
+  if (ncols > kMaxBlockWidth || (R32 && ldr < ncols)) return cudaErrorInvalidValue;
   const int nb = resid_blocks(A.n);
-  residual_norms_kernel<<<nb, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta, partials);
+  residual_norms_kernel<<<nb, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta, partials,
+                                                                R32, ldr);
   note_launch();
   column_partials_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
   note_launch();
