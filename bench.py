@@ -2,8 +2,11 @@
 Chebyshev filtered subspace iteration) on GB300, at relative residual <= 1e-8.
 
 One step = the whole path over one batch: sort 200 synthetic -div(a grad u)
-operators on a 128 x 128 grid (p0 = 8), then solve them in sorted order as one
-warm-started chain for the k = 100 smallest eigenpairs (degree 20, tol 1e-8).
+operators on a 128 x 128 grid (p0 = 8), then solve them in sorted order, each problem
+warm-started from its predecessor, for the k = 100 smallest eigenpairs (tol 1e-8). The timed form is the
+mixed one (FP32 phase, then FP64 phase with the defect-corrected filter; filter degrees
+100 and 100), with the sorted sequence cut into 8 chains solved concurrently; the plain
+FP64 form at the workload degree 20, one sequential chain, is timed beside it.
 Each rank runs its own batch (weak scaling, no data-path collective).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -31,8 +34,66 @@ import scsf_inputs as si  # noqa: E402
 METRIC = "eigenpairs/s at rel. residual <=1e-8 (SCSF sort + warm-started ChFSI chain)"
 UNIT = "eigenpairs/s"
 WORKLOAD = dict(name="poisson128_k100", n=128, n_ops=200, k=100, degree=20, p0=8, tol=1e-8, seed=1)
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA core) rate: 152 SMs x 2 FMA/clk x 2 flop x ~2.06 GHz
 L2_FLUSH_BYTES = 512 << 20
+# algorithmic bytes per (node, column) per filter step: read Y_i and Y_{i-1}, write Y_{i+1}
+# (FP64: 24 B, FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
+BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 16.0}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of the current
+# kernels (None until captured)
+TRAFFIC_PER_LAUNCH = {}
+
+
+def isolated_filter_rates(scsf, ctx, dev, st, degree: int):
+    """Per-step device time of the filter kernels, each launched alone on the context's
+    stream: CUDA events around filters of degree m and m + 100, the difference over 100
+    (operator assembly and the end passes cancel). Shapes: one chain of the workload
+    (N = 16384, kb = 120), and for the FP32 step also N = 65536, kb = 480 (a 256 x 256
+    grid with k = 400), whose blocks do not fit in L2."""
+    import torch
+    w = WORKLOAD
+    out = {}
+    m = max(degree, 20)
+
+    def per_step(run):
+        times = []
+        for deg in (m, m + 100):
+            run(deg)  # warm
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(3):
+                run(deg)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1) / 3)
+        return (times[1] - times[0]) / 100 * 1e3  # us
+
+    n, kb = w["n"], scsf.block_width(w["k"])
+    op = scsf.Operator.from_workload(si.div_a_grad_chain(n, 1, seed=5)[0], dev)
+    lo, hi = scsf.assemble_bounds(op, ctx)
+    lam, alpha = lo + 1e-3 * (hi - lo), lo + 2.0 * kb / (n * n) * (hi - lo)
+    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(dev)
+    X32 = X.float()
+    theta = torch.linspace(lam, alpha, kb, dtype=torch.float64, device=dev)
+    us = per_step(lambda d: scsf.cheb_filter_f32(op, X32, d, lam, c, e, ctx=ctx))
+    out["cheb_step_f32"] = {"avg_us_alone": us, "shape_alone": f"N = {n * n}, kb = {kb}"}
+    us = per_step(lambda d: scsf.cheb_filter_dc(op, X, theta, d, lam, c, e, ctx=ctx))
+    out["cheb_step_dc"] = {"avg_us_alone": us, "shape_alone": f"N = {n * n}, kb = {kb}"}
+    del X, X32
+    nb, kbb = 256, 480
+    opb = scsf.Operator.from_workload(si.lap_plus_v_chain(nb, 1, seed=2)[0], dev)
+    lo, hi = scsf.assemble_bounds(opb, ctx)
+    lam, alpha = lo + 1e-3 * (hi - lo), lo + 2.0 * kbb / (nb * nb) * (hi - lo)
+    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+    Xb = torch.randn((nb * nb, kbb), generator=g, dtype=torch.float32).to(dev)
+    us = per_step(lambda d: scsf.cheb_filter_f32(opb, Xb, d, lam, c, e, ctx=ctx))
+    out["cheb_step_f32_256x256_kb480"] = {"avg_us_alone": us,
+                                           "bytes_per_launch": 12.0 * nb * nb * kbb}
+    del Xb
+    torch.cuda.synchronize(dev)
+    return out
 
 
 def _dist():
@@ -241,54 +302,57 @@ def run_ours(args):
                  "iters_per_op_mean": float(np.mean([s["iters"] for s in plain["stats"]]))}
 
     all_stats = main["stats"]
-    # live per-kernel rooflines from the CUDA-event phase timings of the timed steps
-    filt_ms = sum(s["t_filter_ms"] for s in all_stats)
-    filt_launch = sum(s["filter_steps"] for s in all_stats)
-    filt_elems = sum(s["filter_elems"] for s in all_stats)
-    f32_ms = sum(s["t_filter32_ms"] for s in all_stats)
-    f32_launch = sum(s["filter32_steps"] for s in all_stats)
-    f32_elems = sum(s["filter32_elems"] for s in all_stats)
-    rot_ms = sum(s["t_rot_ms"] for s in all_stats)
-    rot_launch = sum(s["rot_launches"] for s in all_stats)
-    rot_flops = sum(s["rot_flops"] for s in all_stats)
+    # per-phase device time of the timed steps: CUDA events on each chain's own stream,
+    # summed over chains (chains run concurrently, so these add up to more than the wall)
     phase_ms = {p: sum(s[f"t_{p}_ms"] for s in all_stats) for p in
-                ("filter", "filter32", "orth", "rr", "eig", "rot", "resid")}
+                ("filter", "filter32", "filter_dc", "orth", "rr", "eig", "rot", "resid")}
+    launches = {"cheb_step_f64": sum(s["filter_steps"] for s in all_stats),
+                "cheb_step_f32": sum(s["filter32_steps"] for s in all_stats),
+                "cheb_step_dc": sum(s["filter_dc_steps"] for s in all_stats)}
+    elems = {"cheb_step_f64": sum(s["filter_elems"] for s in all_stats),
+             "cheb_step_f32": sum(s["filter32_elems"] for s in all_stats),
+             "cheb_step_dc": sum(s["filter_dc_elems"] for s in all_stats)}
+    phase_of = {"cheb_step_f64": "filter", "cheb_step_f32": "filter32", "cheb_step_dc": "filter_dc"}
     peaks, peak_kind = _measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
-    fp64_peak = FP64_PEAK_TFLOPS
     kernels = {}
-    if filt_launch:
-        avg = filt_ms * 1e-3 / filt_launch
-        kernels["cheb_step_f64"] = {
-            "bound": "alu", "launches": filt_launch, "avg_us": avg * 1e6,
-            "achieved": 13.0 * filt_elems / filt_launch / avg / 1e12, "peak": fp64_peak,
-            "unit": "TFLOP/s", "bytes_per_launch": 24.0 * filt_elems / filt_launch}
-    if f32_launch:
-        avg = f32_ms * 1e-3 / f32_launch
-        kernels["cheb_step_f32"] = {
-            "bound": "hbm", "launches": f32_launch, "avg_us": avg * 1e6,
-            "achieved": 12.0 * f32_elems / f32_launch / avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
-            "bytes_per_launch": 12.0 * f32_elems / f32_launch,
-            "note": "3 x 7.9 MB blocks are L2-resident at this size: an effective rate, not DRAM"}
-    if rot_launch:
-        avg = rot_ms * 1e-3 / rot_launch
-        kernels["gemm_nn (rotation X = Q Z, FP32 or FP64 by phase)"] = {
-            "launches": rot_launch, "avg_us": avg * 1e6}
-    dom_name = max(("filter", "orth", "rr", "eig", "rot"), key=lambda p: phase_ms[p] +
-                   (phase_ms["filter32"] if p == "filter" else 0.0))
-    if "cheb_step_f32" in kernels and phase_ms["filter32"] >= phase_ms["filter"]:
-        kk = kernels["cheb_step_f32"]
-        roofline = {"bound": "hbm", "kernel": "cheb_step_f32", "achieved": kk["achieved"],
-                    "peak": hbm_peak, "unit": "GB/s", "frac": kk["achieved"] / hbm_peak,
-                    "traffic": None, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                    "note": kk["note"]}
-    else:
-        kk = kernels["cheb_step_f64"]
-        roofline = {"bound": "alu", "kernel": "cheb_step_f64", "achieved": kk["achieved"],
-                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": kk["achieved"] / fp64_peak,
-                    "traffic": None,
-                    "peak_source": "FP64 ALU rate from unit counts and clocks (152 SMs x 2 FMA/clk)"}
-    roofline["dominant_phase"] = dom_name
+    for name, nl in launches.items():
+        if not nl:
+            continue
+        avg = phase_ms[phase_of[name]] * 1e-3 / nl
+        kernels[name] = {"launches": nl, "avg_us_in_step": avg * 1e6,
+                         "bytes_per_launch": BYTES_PER_ELEM[name] * elems[name] / nl,
+                         "elems_per_launch": elems[name] / nl}
+    iso = isolated_filter_rates(scsf, ctx, dev, st, args.degree_fp32)
+    for name, r in iso.items():
+        if name in kernels:
+            kernels[name].update(r)
+    # the roofline line reports the filter kernel with the most in-step time; the kernel's
+    # own duration is taken alone on the launching stream (in the step, 8 chains share the
+    # GPU, so a launch's event-to-event time there includes the other chains' work)
+    filt = [k for k in kernels if k != "cheb_step_f64"] or list(kernels)
+    dom = max(filt, key=lambda k: phase_ms[phase_of[k]])
+    kk = kernels[dom]
+    ach = kk["bytes_per_launch"] / (kk["avg_us_alone"] * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}), burst copy",
+                "achieved_in_step": kk["bytes_per_launch"] / (kk["avg_us_in_step"] * 1e-6) / 1e9,
+                "bytes_per_launch": kk["bytes_per_launch"],
+                "note": (f"{BYTES_PER_ELEM[dom]:.0f} B per (node, column) per step, "
+                         f"{kk['elems_per_launch']:.0f} (node, column) pairs per launch; the "
+                         "blocks of one chain fit in L2, so alone the rate is an effective one")}
+    big = iso.get("cheb_step_f32_256x256_kb480")
+    roofline_dram = None
+    if big:
+        ach_b = big["bytes_per_launch"] / (big["avg_us_alone"] * 1e-6) / 1e9
+        roofline_dram = {"bound": "hbm", "kernel": "cheb_step_f32", "shape": "N = 65536, kb = 480",
+                         "achieved": ach_b, "peak": hbm_peak, "unit": "GB/s", "frac": ach_b / hbm_peak,
+                         "traffic": TRAFFIC_PER_LAUNCH.get("cheb_step_f32_256x256_kb480"),
+                         "note": "3 x 126 MB FP32 blocks: every step streams through DRAM"}
+    dom_phase = max(("filter", "filter32", "filter_dc", "orth", "rr", "eig", "rot", "resid"),
+                    key=lambda p: phase_ms[p])
+    roofline["dominant_phase"] = dom_phase
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -316,9 +380,11 @@ def run_ours(args):
         "iters_per_op_mean": float(np.mean([s["iters"] for s in all_stats])),
         "iters_fp32_per_op_mean": float(np.mean([s["iters_fp32"] for s in all_stats])),
         "phase_ms_per_step": {p: v / args.steps for p, v in phase_ms.items()},
+        "phase_note": "per-phase CUDA-event time summed over the concurrent chains' streams",
         "plain_fp64": other,
         "speedup_vs_plain_fp64": (value / other["value"]) if other else None,
         "roofline": roofline,
+        "roofline_filter_dram": roofline_dram,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(main["launches"]),
@@ -394,8 +460,8 @@ def main():
                     help="headline form (default: the mixed form; plain FP64 is timed beside it)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--degree-fp32", type=int, default=60, help="mixed form: FP32-phase degree")
-    ap.add_argument("--degree-fp64", type=int, default=60, help="mixed form: FP64-phase degree")
+    ap.add_argument("--degree-fp32", type=int, default=100, help="mixed form: FP32-phase degree")
+    ap.add_argument("--degree-fp64", type=int, default=100, help="mixed form: FP64-phase degree")
     ap.add_argument("--chunks", type=int, default=8,
                     help="contiguous chunks of the sorted sequence solved as concurrent chains")
     ap.add_argument("--n-ops", type=int, default=None,

@@ -106,7 +106,7 @@ struct ChainBufs {
   // FP32 residual block of the defect-corrected filter, B32 its remainder blocks
   float *V32, *B32[3], *d32, *we32, *wn32, *partials32;
   float* ytab;  // [degree][kb] scalar filter values at the Ritz values
-  double* ym;   // [kb]
+  double* ym;   // [2][kb] recurrence state; y_m in the second row
 };
 
 template <typename Cv>
@@ -142,7 +142,7 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   b.ym = nullptr;
   if (mixed) {
     b.ytab = c.template take<float>((size_t)std::max(degree, 1) * kb);
-    b.ym = c.template take<double>(kb);
+    b.ym = c.template take<double>(2 * (size_t)kb);
     b.V32 = c.template take<float>(blk);
     for (auto& p : b.B32) p = c.template take<float>(blk);
     b.d32 = c.template take<float>(N);
@@ -242,7 +242,7 @@ void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3
   *rpart = cv.template take<double>((size_t)resid_blocks(n) * 2 * ncols);
   *res2 = cv.template take<double>(2 * (size_t)ncols);
   *ytab = cv.template take<float>((size_t)std::max(degree, 1) * ncols);
-  *ym = cv.template take<double>(ncols);
+  *ym = cv.template take<double>(2 * (size_t)ncols);
 }
 
 // Defect-corrected filter of the FP64 phase (mixed form): X (FP64, ncols active
@@ -250,30 +250,49 @@ void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3
 // (device). The remainder Z runs through zb; Y = X diag(y_m) + Z_m lands in Y (FP64).
 cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const float* R, int ldr,
                           const double* theta, int ncols, int degree, double lam, double c,
-                          double e, float* const zb[3], int ldz, float* ytab, double* ym,
+                          double e, float* const zb[3], int ldz, float* ytab, double* ystate,
                           double* Y, int ldy, cudaStream_t st) {
-  cudaError_t err = launch_dc_ytab(theta, ncols, degree, lam, c, e, ytab, ym, st);
-  if (err != cudaSuccess) return err;
+  // coefficients of step i (Y_i -> Y_{i+1}): s1 A Y_i + s2 Y_i + s3 Y_{i-1}
+  std::vector<double> s1(degree), s2(degree), s3(degree);
   const double sigma1 = e / (lam - c);
-  // Z_1 = s1 R diag(y_0), y_0 = 1
-  err = launch_cheb_step_dc(A, nullptr, nullptr, ldz, R, ldr, ytab, zb[0], ncols,
-                            (float)(sigma1 / e), 0.f, 0.f, st);
-  if (err != cudaSuccess) return err;
   double sigma = sigma1;
-  const float* prev = nullptr;  // Z_0 = 0
-  int cur = 0;
+  s1[0] = sigma1 / e;
+  s2[0] = -sigma1 * c / e;
+  s3[0] = 0.0;
   for (int i = 1; i < degree; ++i) {
     const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    s1[i] = 2.0 * sigma_next / e;
+    s2[i] = -2.0 * sigma_next * c / e;
+    s3[i] = -sigma_next * sigma;
+    sigma = sigma_next;
+  }
+  cudaError_t err = cudaSuccess;
+  DcSteps P;
+  for (int i0 = 0; i0 < degree; i0 += kDcChunk) {
+    P.i0 = i0;
+    P.count = std::min(kDcChunk, degree - i0);
+    for (int q = 0; q < P.count; ++q) {
+      P.s1[q] = s1[i0 + q];
+      P.s2[q] = s2[i0 + q];
+      P.s3[q] = s3[i0 + q];
+    }
+    if ((err = launch_dc_ytab(theta, ncols, P, ytab, ystate, st)) != cudaSuccess) return err;
+  }
+  // Z_1 = s1 R diag(y_0), y_0 = 1; Z_0 = 0
+  err = launch_cheb_step_dc(A, nullptr, nullptr, ldz, R, ldr, ytab, zb[0], ncols, (float)s1[0],
+                            0.f, 0.f, st);
+  if (err != cudaSuccess) return err;
+  const float* prev = nullptr;
+  int cur = 0;
+  for (int i = 1; i < degree; ++i) {
     const int nxt = i % 3;
     err = launch_cheb_step_dc(A, zb[cur], prev, ldz, R, ldr, ytab + (size_t)i * ncols, zb[nxt],
-                              ncols, (float)(2.0 * sigma_next / e), (float)(-2.0 * sigma_next * c / e),
-                              (float)(-sigma_next * sigma), st);
+                              ncols, (float)s1[i], (float)s2[i], (float)s3[i], st);
     if (err != cudaSuccess) return err;
     prev = zb[cur];
     cur = nxt;
-    sigma = sigma_next;
   }
-  return launch_dc_combine(A.n * A.n, ncols, X, ldx, ym, zb[cur], ldz, Y, ldy, st);
+  return launch_dc_combine(A.n * A.n, ncols, X, ldx, ystate + ncols, zb[cur], ldz, Y, ldy, st);
 }
 
 }  // namespace

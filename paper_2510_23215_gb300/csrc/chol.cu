@@ -6,8 +6,8 @@
 // Both factorisations run in one CTA with the matrix in shared memory
 // (right-looking, one column per step, the trailing update on a 32 x 32 thread
 // grid without index division). The inverse R^{-1} = (L^{-1})^T is spread over
-// several CTAs, each holding L in shared memory: one warp forward-substitutes one
-// column of L^{-1}.
+// k single-warp CTAs: one warp forward-substitutes one column of L^{-1}, in FP32 for
+// the first pass and FP64 for the second.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -79,38 +79,61 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
   if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
 }
 
-// Rinv = (L^{-1})^T (upper, ld k). Each CTA stages L in shared memory; one warp
-// per column j of L^{-1}: x_j = 1/L_jj, x_i = -(sum_{c=j}^{i-1} L_ic x_c) / L_ii.
-constexpr int kTrinvWarps = 16;
+// Rinv = (L^{-1})^T (upper, ld k): one warp per column j of L^{-1}, one warp per CTA so
+// that the columns spread over the SMs (the FP64 pipe of one SM is narrow). Column-
+// oriented forward substitution: lane l keeps the running sums s_r of the rows
+// r = l + 32 q in registers; at step i the owner lane of row i forms
+// x_i = -s_i / L_ii (x_j = 1 / L_jj), broadcasts it, and every lane adds L_ri x_i to
+// its rows r > i. L is staged 32 columns at a time ([k][33] tile, conflict-free).
+// T = float serves the first (preconditioning) Cholesky QR pass, T = double the second.
+constexpr int kTrinvRowsPerLane = (kMaxBlockWidth + 31) / 32;
 
-__global__ void __launch_bounds__(32 * kTrinvWarps)
+template <typename T>
+__global__ void __launch_bounds__(32)
 trinv_kernel(int k, const double* __restrict__ L, double* __restrict__ Rinv) {
-  extern __shared__ double Ls[];  // k x ks, then kTrinvWarps x k solution vectors
-  const int ks = odd_stride(k);
-  double* xs_all = Ls + (size_t)k * ks;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j0 = blockIdx.x * kTrinvWarps;  // first column of this CTA
-  // rows >= j0 of L are the only ones this CTA's columns touch
-  for (int e = threadIdx.x; e < (k - j0) * k; e += blockDim.x) {
-    const int i = j0 + e / k, c = e - (e / k) * k;
-    if (c <= i) Ls[i * ks + c] = L[(size_t)i * k + c];
+  extern __shared__ unsigned char tile_raw[];
+  T* tile = reinterpret_cast<T*>(tile_raw);  // [k][33]
+  const int lane = threadIdx.x, j = blockIdx.x;
+  T s[kTrinvRowsPerLane], dinv[kTrinvRowsPerLane], x[kTrinvRowsPerLane];
+#pragma unroll
+  for (int q = 0; q < kTrinvRowsPerLane; ++q) {
+    const int r = lane + 32 * q;
+    s[q] = T(0);
+    x[q] = T(0);
+    dinv[q] = (r >= j && r < k) ? T(1) / (T)L[(size_t)r * k + r] : T(0);
   }
-  __syncthreads();
-  const int j = j0 + w;
-  if (j >= k) return;
-  double* x = xs_all + (size_t)w * k;
-  if (lane == 0) x[j] = 1.0 / Ls[j * ks + j];
-  __syncwarp();
-  for (int i = j + 1; i < k; ++i) {
-    const double* Li = Ls + (size_t)i * ks;
-    double s = 0.0;
-    for (int c = j + lane; c < i; c += 32) s = fma(Li[c], x[c], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[i] = -s / Li[i];
-    __syncwarp();
+#pragma unroll
+  for (int cq = 0; cq < kTrinvRowsPerLane; ++cq) {
+    const int c0 = 32 * cq;
+    if (c0 < k && c0 + 31 >= j) {
+      // stage L[r][c0 + t] for rows r >= max(j, c0), t < 32
+      __syncwarp();
+      const int rfirst = max(j, c0);
+      const int c = c0 + lane;
+      for (int r = rfirst; r < k; ++r)
+        tile[r * 33 + lane] = (c < k && c <= r) ? (T)L[(size_t)r * k + c] : T(0);
+      __syncwarp();
+      for (int t = 0; t < 32; ++t) {
+        const int i = c0 + t;
+        if (i >= k) break;
+        if (i < j) continue;
+        T xi = (i == j) ? dinv[cq] : -s[cq] * dinv[cq];
+        xi = __shfl_sync(0xffffffffu, xi, t);
+        if (lane == t) x[cq] = xi;
+#pragma unroll
+        for (int q = cq; q < kTrinvRowsPerLane; ++q) {
+          const int r = lane + 32 * q;
+          if (r > i && r < k) s[q] = fma(tile[r * 33 + t], xi, s[q]);
+        }
+      }
+    }
   }
   double* row = Rinv + (size_t)j * k;
-  for (int i = lane; i < k; i += 32) row[i] = (i >= j) ? x[i] : 0.0;
+#pragma unroll
+  for (int q = 0; q < kTrinvRowsPerLane; ++q) {
+    const int r = lane + 32 * q;
+    if (r < k) row[r] = (r >= j) ? (double)x[q] : 0.0;
+  }
 }
 
 template <typename T>
@@ -132,9 +155,15 @@ cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double*
   cudaError_t e = fp32 ? launch_chol_t<float>(k, G, ldg, L, status, 1e-6, st)
                        : launch_chol_t<double>(k, G, ldg, L, status, 1e-14, st);
   if (e != cudaSuccess) return e;
-  const size_t smem = ((size_t)k * odd_stride(k) + (size_t)kTrinvWarps * k) * sizeof(double);
-  if ((e = ensure_dynamic_smem((const void*)trinv_kernel, smem)) != cudaSuccess) return e;
-  trinv_kernel<<<(k + kTrinvWarps - 1) / kTrinvWarps, 32 * kTrinvWarps, smem, st>>>(k, L, Rinv);
+  if (fp32) {
+    const size_t smem = (size_t)k * 33 * sizeof(float);
+    if ((e = ensure_dynamic_smem((const void*)trinv_kernel<float>, smem)) != cudaSuccess) return e;
+    trinv_kernel<float><<<k, 32, smem, st>>>(k, L, Rinv);
+  } else {
+    const size_t smem = (size_t)k * 33 * sizeof(double);
+    if ((e = ensure_dynamic_smem((const void*)trinv_kernel<double>, smem)) != cudaSuccess) return e;
+    trinv_kernel<double><<<k, 32, smem, st>>>(k, L, Rinv);
+  }
   note_launch();
   return cudaGetLastError();
 }

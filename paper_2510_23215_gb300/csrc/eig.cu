@@ -4,8 +4,9 @@
 // in FP32 and then refined to FP64 accuracy:
 //   1. parallel cyclic Jacobi in FP32, one CTA, both k x k matrices in shared
 //      memory with an odd row stride (column accesses are bank-conflict free),
-//      round-robin (circle method) pair ordering, one warp per rotation pair:
-//      k/2 disjoint rotations per round, two barriers per round;
+//      round-robin (circle method) pair ordering: the k/2 disjoint rotations of a
+//      round are applied as one similarity transform, thread by thread over 2 x 2
+//      blocks, two barriers per round;
 //   2. two Ogita-Aishima refinement steps in FP64 (X' = X (I + E) with
 //      R = I - X^T X, S = X^T G X, lambda_i = s_ii/(1 - r_ii), E_ij =
 //      (s_ij + lambda_j r_ij)/(lambda_j - lambda_i), or r_ij/2 for pairs closer
@@ -101,6 +102,100 @@ __device__ __forceinline__ void jacobi_round(T* A, int ks, T* V, int ldv, int k,
   __syncthreads();
 }
 
+// The same round applied as one similarity step A' = J^T A J, V' = V J, with all k/2
+// rotations of the round forming J: for i, j with partners i', j' and coefficients
+// (alpha, beta) -- row_i' = alpha_i row_i + beta_i row_i'(partner), so alpha = c and
+// beta = -s for the first index of a pair, +s for the second, (1, 0) when the pair does
+// not rotate -- A'_ij = alpha_i alpha_j A_ij + alpha_i beta_j A_ij' + beta_i alpha_j A_i'j
+// + beta_i beta_j A_i'j'. Every thread updates whole 2 x 2 blocks (pair a x pair b, a <= b,
+// mirrored), so the round needs only the angle pass, one barrier, the block pass and a
+// second barrier, with all 1024 threads busy in the block pass.
+template <typename T, typename Keep>
+__device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv, int k, int kp,
+                                                    int round, Keep keep, T* al, T* be, int* plist) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
+  const int npairs = kp / 2;
+  for (int pr = t; pr < npairs; pr += nt) {
+    int p, q;
+    circle_pair(pr, round, kp, p, q);
+    plist[2 * pr] = p;
+    plist[2 * pr + 1] = q;
+    T c = T(1), sn = T(0);
+    bool act = false;
+    if (q < k) {
+      const T apq = A[p * ks + q], app = A[p * ks + p], aqq = A[q * ks + q];
+      if (keep(apq, app, aqq)) {
+        jacobi_angle(app, aqq, apq, c, sn);
+        act = true;
+      }
+    }
+    al[p] = act ? c : T(1);
+    be[p] = act ? -sn : T(0);
+    if (q < k) {
+      al[q] = act ? c : T(1);
+      be[q] = act ? sn : T(0);
+    }
+  }
+  __syncthreads();
+  for (int a = warp; a < npairs; a += nwarps) {
+    const int pa = plist[2 * a], qa = plist[2 * a + 1];
+    const bool ha = qa < k;
+    const T a_p = al[pa], b_p = be[pa];
+    const T a_q = ha ? al[qa] : T(1), b_q = ha ? be[qa] : T(0);
+    for (int b = a + lane; b < npairs; b += 32) {
+      const int pb = plist[2 * b], qb = plist[2 * b + 1];
+      const bool hb = qb < k;
+      const T c_p = al[pb], d_p = be[pb];
+      const T c_q = hb ? al[qb] : T(1), d_q = hb ? be[qb] : T(0);
+      const T s_pp = A[pa * ks + pb];
+      const T s_pq = hb ? A[pa * ks + qb] : T(0);
+      const T s_qp = ha ? A[qa * ks + pb] : T(0);
+      const T s_qq = (ha && hb) ? A[qa * ks + qb] : T(0);
+      const T n_pp = a_p * (c_p * s_pp + d_p * s_pq) + b_p * (c_p * s_qp + d_p * s_qq);
+      const T n_pq = a_p * (c_q * s_pq + d_q * s_pp) + b_p * (c_q * s_qq + d_q * s_qp);
+      const T n_qp = a_q * (c_p * s_qp + d_p * s_qq) + b_q * (c_p * s_pp + d_p * s_pq);
+      const T n_qq = a_q * (c_q * s_qq + d_q * s_qp) + b_q * (c_q * s_pq + d_q * s_pp);
+      if (a == b) {  // the pair's own block: the rotation annihilates its off-diagonal entry
+        const bool act = ha && b_q != T(0);
+        A[pa * ks + pa] = n_pp;
+        if (ha) {
+          A[qa * ks + qa] = n_qq;
+          A[pa * ks + qa] = act ? T(0) : n_pq;
+          A[qa * ks + pa] = act ? T(0) : n_qp;
+        }
+      } else {
+        A[pa * ks + pb] = n_pp;
+        A[pb * ks + pa] = n_pp;
+        if (hb) {
+          A[pa * ks + qb] = n_pq;
+          A[qb * ks + pa] = n_pq;
+        }
+        if (ha) {
+          A[qa * ks + pb] = n_qp;
+          A[pb * ks + qa] = n_qp;
+        }
+        if (ha && hb) {
+          A[qa * ks + qb] = n_qq;
+          A[qb * ks + qa] = n_qq;
+        }
+      }
+    }
+  }
+  // V' = V J: column pairs, rows across the lanes (odd stride: conflict-free)
+  for (int b = warp; b < npairs; b += nwarps) {
+    const int pb = plist[2 * b], qb = plist[2 * b + 1];
+    if (qb >= k || be[qb] == T(0)) continue;
+    const T c_p = al[pb], d_p = be[pb], c_q = al[qb], d_q = be[qb];
+    for (int r = lane; r < k; r += 32) {
+      const T vp = V[r * ldv + pb], vq = V[r * ldv + qb];
+      V[r * ldv + pb] = c_p * vp + d_p * vq;
+      V[r * ldv + qb] = c_q * vq + d_q * vp;
+    }
+  }
+  __syncthreads();
+}
+
 // Block-wide sums of two values (every thread gets the results).
 template <typename T>
 __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
@@ -131,6 +226,8 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
   float* A = smf;           // k x ks
   float* V = smf + k * ks;  // k x ks
   __shared__ float red[64];
+  __shared__ float s_al[kMaxBlockWidth + 1], s_be[kMaxBlockWidth + 1];
+  __shared__ int s_pl[kMaxBlockWidth + 2];
   const int t = threadIdx.x, nt = blockDim.x;
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
@@ -157,9 +254,9 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
     for (int round = 0; round < kp - 1; ++round)
       // threshold Jacobi: entries already at FP32 rounding level relative to their
       // diagonal pair are left alone, so late sweeps rotate (and move) little
-      jacobi_round<float>(A, ks, V, ks, k, kp, round, [](float apq, float app, float aqq) {
+      jacobi_round_blocks<float>(A, ks, V, ks, k, kp, round, [](float apq, float app, float aqq) {
         return fabsf(apq) > 3e-8f * (fabsf(app) + fabsf(aqq)) && apq != 0.f;
-      });
+      }, s_al, s_be, s_pl);
   }
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;

@@ -95,9 +95,16 @@ cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ld
 // the filtered block is Y_m = X diag(y_m(theta)) + Z_m, where y_i are the scalar
 // recurrences of the filter at the Ritz values and Z_i obeys the same recurrence with
 // the extra term s1 R diag(y_i) (Z_0 = 0). Z is small when R is, so FP32 suffices.
-//   ytab: per column y_0 .. y_{degree-1} (FP32, [degree][ncols]) and y_degree (FP64, ym)
-cudaError_t launch_dc_ytab(const double* theta, int ncols, int degree, double lam, double c,
-                           double e, float* ytab, double* ym, cudaStream_t st);
+//   ytab: per column y_0 .. y_{degree-1} (FP32, [degree][ncols]), computed in chunks of
+//   kDcChunk steps whose coefficients travel by value; state [2][ncols] (FP64) carries
+//   (y_{i-1}, y_i) between chunks and ends with y_degree in state[1].
+constexpr int kDcChunk = 128;
+struct DcSteps {
+  int i0, count;
+  double s1[kDcChunk], s2[kDcChunk], s3[kDcChunk];
+};
+cudaError_t launch_dc_ytab(const double* theta, int ncols, const DcSteps& P, float* ytab,
+                           double* state, cudaStream_t st);
 // out = s1 (A cur) + s2 cur + s3 prev + s1 R diag(ycol); cur == nullptr means Z_0 = 0.
 cudaError_t launch_cheb_step_dc(const Stencil32& A, const float* cur, const float* prev, int ld,
                                 const float* R, int ldr, const float* ycol, float* out,

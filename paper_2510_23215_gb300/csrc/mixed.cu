@@ -77,25 +77,25 @@ cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
 // Z is of the size of R, so it is computed in FP32 while X diag(y_m) stays in FP64:
 // the result has FP64 accuracy at the cost of an FP32 stencil sweep.
 
-// One thread per column: y_0 .. y_{m-1} (FP32) and y_m (FP64), with the scaled
-// coefficients of the filter (sigma_1 = e / (lam - c), sigma_{i+1} = 1 / (2 / sigma_1 - sigma_i)).
-__global__ void dc_ytab_kernel(const double* __restrict__ theta, int ncols, int degree, double lam,
-                               double c, double e, float* __restrict__ ytab, double* __restrict__ ym) {
+// One thread per column: y_i(theta_j) for the steps [i0, i0 + count) of the filter,
+// y_{i+1} = (s1_i theta + s2_i) y_i + s3_i y_{i-1} with the filter's own (host-computed)
+// coefficients. y_i goes to ytab row i (FP32); state [2][ncols] carries (y_{i-1}, y_i)
+// in FP64 from chunk to chunk, and after the last chunk state[1] holds y_m.
+__global__ void dc_ytab_kernel(const double* __restrict__ theta, int ncols, DcSteps P,
+                               float* __restrict__ ytab, double* __restrict__ state) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncols) return;
   const double t = theta[j];
-  const double sigma1 = e / (lam - c);
-  double y_prev = 1.0, y = sigma1 * (t - c) / e, sigma = sigma1;
-  ytab[j] = 1.f;
-  for (int i = 1; i < degree; ++i) {
-    ytab[(size_t)i * ncols + j] = (float)y;
-    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
-    const double y_next = 2.0 * sigma_next * (t - c) / e * y - sigma_next * sigma * y_prev;
-    y_prev = y;
-    y = y_next;
-    sigma = sigma_next;
+  double yp = (P.i0 == 0) ? 0.0 : state[j];
+  double y = (P.i0 == 0) ? 1.0 : state[ncols + j];
+  for (int q = 0; q < P.count; ++q) {
+    ytab[(size_t)(P.i0 + q) * ncols + j] = (float)y;
+    const double yn = fma(fma(P.s1[q], t, P.s2[q]), y, P.s3[q] * yp);
+    yp = y;
+    y = yn;
   }
-  ym[j] = y;
+  state[j] = yp;
+  state[ncols + j] = y;
 }
 
 constexpr int kDcRows = 8;
@@ -443,10 +443,10 @@ cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_dc_ytab(const double* theta, int ncols, int degree, double lam, double c,
-                           double e, float* ytab, double* ym, cudaStream_t st) {
-  if (ncols < 1 || degree < 1) return cudaErrorInvalidValue;
-  dc_ytab_kernel<<<(ncols + 127) / 128, 128, 0, st>>>(theta, ncols, degree, lam, c, e, ytab, ym);
+cudaError_t launch_dc_ytab(const double* theta, int ncols, const DcSteps& P, float* ytab,
+                           double* state, cudaStream_t st) {
+  if (ncols < 1 || P.count < 1 || P.count > kDcChunk) return cudaErrorInvalidValue;
+  dc_ytab_kernel<<<(ncols + 127) / 128, 128, 0, st>>>(theta, ncols, P, ytab, state);
   note_launch();
   return cudaGetLastError();
 }
