@@ -207,7 +207,8 @@ def run_ours(args):
     def step(fields, ax, ay, precision, chunks=1):
         if precision == scsf.MIXED:  # the chosen form tunes its filter degrees
             params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32,
-                                 tol=w["tol"], seed=7 + rank, precision=precision)
+                                 tol=w["tol"], seed=7 + rank, precision=precision,
+                                 switch_tol=args.switch_tol)
         else:                        # the plain form keeps the workload's degree
             params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank,
                                  precision=precision)
@@ -373,6 +374,7 @@ def run_ours(args):
                    "chunks": args.chunks,
                    "degrees": ({"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}
                                if chosen == "mixed" else {"fp64": w["degree"]}),
+                   "switch_tol": args.switch_tol if chosen == "mixed" else None,
                    "field_law": "a = exp(0.5 f/8), f = sum of 8x8 cosine modes, N(0,1) coefficients",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": f"replicas over chains x{ws}"},
@@ -462,6 +464,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--degree-fp32", type=int, default=100, help="mixed form: FP32-phase degree")
     ap.add_argument("--degree-fp64", type=int, default=100, help="mixed form: FP64-phase degree")
+    ap.add_argument("--switch-tol", type=float, default=0.0,
+                    help="mixed form: wanted residual at which the FP32 phase hands over (0: off)")
     ap.add_argument("--chunks", type=int, default=8,
                     help="contiguous chunks of the sorted sequence solved as concurrent chains")
     ap.add_argument("--n-ops", type=int, default=None,

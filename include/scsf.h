@@ -129,6 +129,8 @@ typedef struct {
   int precision;     /* scsf_precision                                                    */
   uint64_t seed;     /* Philox seed of the random head block (Sec. 3.2, first problem)    */
   int degree_fp32;   /* SCSF_MIXED: Chebyshev degree of the FP32 phase (<= 0: degree)     */
+  double switch_tol; /* SCSF_MIXED: leave the FP32 phase once every wanted residual is at
+                        or below this (> 0), besides the FP32-floor and stall rules       */
 } scsf_params;
 
 typedef struct {

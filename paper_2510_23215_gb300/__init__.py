@@ -63,7 +63,8 @@ class _COperator(ctypes.Structure):
 class _CParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nex", ctypes.c_int), ("degree", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int),
+                ("switch_tol", ctypes.c_double)]
 
 
 class _CStats(ctypes.Structure):
@@ -242,10 +243,11 @@ class Params:
     precision: int = FP64
     seed: int = 0
     degree_fp32: int = 0   # MIXED: degree of the FP32 phase (0: same as degree)
+    switch_tol: float = 0.0  # MIXED: leave the FP32 phase at this wanted residual (0: off)
 
     def _c(self) -> _CParams:
         return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
-                        self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32)
+                        self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32, self.switch_tol)
 
     @property
     def kb(self) -> int:

@@ -569,7 +569,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       // eigendirection, which puts a floor of about c eps32 ||A|| / |theta_j| under its
       // relative residual (||A|| <= beta). Once every wanted vector is at its floor the
       // subspace has converged to FP32 accuracy and the FP64 phase takes over.
-      double score = 0.0;
+      double score = 0.0, max_r = 0.0;
       int at_floor = 0;
       for (int j = 0; j < kb; ++j) {
         theta_h[j] = h[j];
@@ -579,6 +579,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
           const double floor_j = 16.0 * 5.96e-8 * beta / std::max(std::fabs(theta_h[j]), 1e-300);
           at_floor += (r_h[j] <= std::max(floor_j, ch->p.tol)) ? 1 : 0;
           score += std::log(std::max(r_h[j], 1e-300));
+          max_r = std::max(max_r, r_h[j]);
         }
       }
       for (int j = 0; j < kb; ++j) ch->ritz[j] = theta_h[j];
@@ -586,6 +587,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       alpha = theta_h[kb - 1];
       record(it32, k, 0);
       if (at_floor == k) break;
+      if (ch->p.switch_tol > 0.0 && max_r <= ch->p.switch_tol) break;
       // safety: stop when the wanted residuals improve by less than 1.05x on average
       if (score > prev_score - k * std::log(1.05)) break;
       prev_score = score;
