@@ -43,56 +43,18 @@ BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 
 TRAFFIC_PER_LAUNCH = {}
 
 
-def isolated_filter_rates(scsf, ctx, dev, st, degree: int):
-    """Per-step device time of the filter kernels, each launched alone on the context's
-    stream: CUDA events around filters of degree m and m + 100, the difference over 100
-    (operator assembly and the end passes cancel). Shapes: one chain of the workload
-    (N = 16384, kb = 120), and for the FP32 step also N = 65536, kb = 480 (a 256 x 256
-    grid with k = 400), whose blocks do not fit in L2."""
-    import torch
-    w = WORKLOAD
+def isolated_filter_rates(degree: int, dev):
+    """Per-step device time of each filter kernel launched alone on the launching stream
+    (paper_2510_23215_gb300.filter_bench): at one chain of the workload (N = 16384,
+    kb = 120) and, for the FP32 step, at N = 65536, kb = 480, whose blocks exceed L2."""
+    from paper_2510_23215_gb300 import filter_bench as fb
     out = {}
-    m = max(degree, 20)
-
-    def per_step(run):
-        times = []
-        for deg in (m, m + 100):
-            run(deg)  # warm
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(3):
-                run(deg)
-            e1.record(st)
-            torch.cuda.synchronize(dev)
-            times.append(e0.elapsed_time(e1) / 3)
-        return (times[1] - times[0]) / 100 * 1e3  # us
-
-    n, kb = w["n"], scsf.block_width(w["k"])
-    op = scsf.Operator.from_workload(si.div_a_grad_chain(n, 1, seed=5)[0], dev)
-    lo, hi = scsf.assemble_bounds(op, ctx)
-    lam, alpha = lo + 1e-3 * (hi - lo), lo + 2.0 * kb / (n * n) * (hi - lo)
-    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
-    g = torch.Generator(device="cpu").manual_seed(0)
-    X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(dev)
-    X32 = X.float()
-    theta = torch.linspace(lam, alpha, kb, dtype=torch.float64, device=dev)
-    us = per_step(lambda d: scsf.cheb_filter_f32(op, X32, d, lam, c, e, ctx=ctx))
-    out["cheb_step_f32"] = {"avg_us_alone": us, "shape_alone": f"N = {n * n}, kb = {kb}"}
-    us = per_step(lambda d: scsf.cheb_filter_dc(op, X, theta, d, lam, c, e, ctx=ctx))
-    out["cheb_step_dc"] = {"avg_us_alone": us, "shape_alone": f"N = {n * n}, kb = {kb}"}
-    del X, X32
-    nb, kbb = 256, 480
-    opb = scsf.Operator.from_workload(si.lap_plus_v_chain(nb, 1, seed=2)[0], dev)
-    lo, hi = scsf.assemble_bounds(opb, ctx)
-    lam, alpha = lo + 1e-3 * (hi - lo), lo + 2.0 * kbb / (nb * nb) * (hi - lo)
-    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
-    Xb = torch.randn((nb * nb, kbb), generator=g, dtype=torch.float32).to(dev)
-    us = per_step(lambda d: scsf.cheb_filter_f32(opb, Xb, d, lam, c, e, ctx=ctx))
-    out["cheb_step_f32_256x256_kb480"] = {"avg_us_alone": us,
-                                           "bytes_per_launch": 12.0 * nb * nb * kbb}
-    del Xb
-    torch.cuda.synchronize(dev)
+    for name, kern in (("cheb_step_f32", "f32"), ("cheb_step_dc", "dc")):
+        r = fb.measure(kern, "128x120", dev, max(degree, 20))
+        out[name] = {"avg_us_alone": r["avg_us"], "shape_alone": "N = 16384, kb = 120"}
+    r = fb.measure("f32", "256x480", dev, 20)
+    out["cheb_step_f32_256x256_kb480"] = {"avg_us_alone": r["avg_us"],
+                                           "bytes_per_launch": r["bytes_per_launch"]}
     return out
 
 
@@ -324,7 +286,7 @@ def run_ours(args):
         kernels[name] = {"launches": nl, "avg_us_in_step": avg * 1e6,
                          "bytes_per_launch": BYTES_PER_ELEM[name] * elems[name] / nl,
                          "elems_per_launch": elems[name] / nl}
-    iso = isolated_filter_rates(scsf, ctx, dev, st, args.degree_fp32)
+    iso = isolated_filter_rates(args.degree_fp32, dev)
     for name, r in iso.items():
         if name in kernels:
             kernels[name].update(r)

@@ -1,0 +1,96 @@
+"""Time the Chebyshev filter kernels alone (CUDA events on the launching stream).
+
+A filter of degree m launches m stencil steps; the per-step device time is taken as
+(t(m + 100) - t(m)) / 100, so operator assembly and the end passes cancel. Shapes:
+
+* ``128x120``: one chain of the 128 x 128, k = 100 workload (N = 16384, k_b = 120);
+  its three blocks fit in L2, so the rate is an effective one;
+* ``256x480``: the 256 x 256, k = 400 block (N = 65536, k_b = 480, 3 x 126 MB in FP32),
+  which streams every step through DRAM.
+
+    python -m paper_2510_23215_gb300.filter_bench --kernel f32 --shape 256x480
+    python -m paper_2510_23215_gb300.filter_bench --kernel dc --shape 128x120 --degree 3 --once
+
+``--once`` runs one filter of the given degree and exits (a short command for profilers).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import Context, Operator, assemble_bounds, cheb_filter_dc, cheb_filter_f32
+
+# algorithmic bytes per (node, column) per step: read Y_i and Y_{i-1}, write Y_{i+1}
+# (FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
+BYTES_PER_ELEM = {"f32": 12.0, "dc": 16.0}
+
+
+def setup(kernel: str, shape: str, device, seed: int = 0):
+    """(runner(degree), elements per step) for the kernel at the shape."""
+    import scsf_inputs as si  # seeded operator generators (no method arithmetic)
+    n, kb = (int(v) for v in shape.split("x"))
+    if n == 256:
+        op = Operator.from_workload(si.lap_plus_v_chain(n, 1, seed=2)[0], device)
+    else:
+        op = Operator.from_workload(si.div_a_grad_chain(n, 1, seed=5)[0], device)
+    ctx = Context(device.index or 0, torch.cuda.current_stream(device))
+    lo, hi = assemble_bounds(op, ctx)
+    lam, alpha = lo + 1e-3 * (hi - lo), lo + 2.0 * kb / (n * n) * (hi - lo)
+    c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    if kernel == "f32":
+        X = torch.randn((n * n, kb), generator=g, dtype=torch.float32).to(device)
+        return (lambda d: cheb_filter_f32(op, X, d, lam, c, e, ctx=ctx)), n * n * kb
+    X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(device)
+    theta = torch.linspace(lam, alpha, kb, dtype=torch.float64, device=device)
+    return (lambda d: cheb_filter_dc(op, X, theta, d, lam, c, e, ctx=ctx)), n * n * kb
+
+
+def per_step_us(run, degree: int, device, reps: int = 3) -> float:
+    st = torch.cuda.current_stream(device)
+    times = []
+    for deg in (degree, degree + 100):
+        run(deg)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            run(deg)
+        e1.record(st)
+        torch.cuda.synchronize(device)
+        times.append(e0.elapsed_time(e1) / reps)
+    return (times[1] - times[0]) / 100 * 1e3
+
+
+def measure(kernel: str, shape: str, device, degree: int = 20) -> dict:
+    run, elems = setup(kernel, shape, device)
+    us = per_step_us(run, degree, device)
+    nbytes = BYTES_PER_ELEM[kernel] * elems
+    return {"kernel": kernel, "shape": shape, "avg_us": us, "bytes_per_launch": nbytes,
+            "gbs": nbytes / (us * 1e-6) / 1e9}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--kernel", choices=["f32", "dc"], default="f32")
+    ap.add_argument("--shape", default="128x120")
+    ap.add_argument("--degree", type=int, default=20)
+    ap.add_argument("--once", action="store_true")
+    a = ap.parse_args()
+    dev = torch.device("cuda", 0)
+    if a.once:
+        run, _ = setup(a.kernel, a.shape, dev)
+        run(a.degree)
+        torch.cuda.synchronize(dev)
+        print("ok")
+        return
+    r = measure(a.kernel, a.shape, dev, a.degree)
+    print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    np.set_printoptions(precision=4)
+    main()
