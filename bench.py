@@ -38,9 +38,9 @@ L2_FLUSH_BYTES = 512 << 20
 # algorithmic bytes per (node, column) per filter step: read Y_i and Y_{i-1}, write Y_{i+1}
 # (FP64: 24 B, FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
 BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 16.0}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of the current
-# kernels (None until captured)
-TRAFFIC_PER_LAUNCH = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
+# current kernels (profiles/cheb_step_*.md); kernels not captured at a shape are absent
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_step_dc": 15.94e6}
 
 
 def isolated_filter_rates(degree: int, dev):
