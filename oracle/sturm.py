@@ -10,6 +10,9 @@
   discrete sine modes in y into n symmetric tridiagonals
   L_x^a + mu_q diag(a(x_i)), mu_q = (4/h^2) sin^2(q pi h / 2); their union is
   the spectrum. Each tridiagonal is solved by bisection on the Sturm count.
+* Separable potential V = V1(x) + V2(y): -Lap + V is T1 (x) I + I (x) T2 with the 1-D
+  operators T = (1/h^2) tridiag(-1, 2, -1) + diag(V_r), so its eigenvalues are the sums
+  mu_i + nu_j of theirs.
 """
 from __future__ import annotations
 
@@ -103,3 +106,60 @@ def separable_smallest(n: int, ax_col: np.ndarray, a_nodes: np.ndarray, k: int) 
     for d, e in separable_tridiagonals(n, ax_col, a_nodes):
         vals.append(tridiagonal_eigenvalues_bisection(d, e, min(k, n)))
     return np.sort(np.concatenate(vals))[:k]
+
+
+def sturm_counts(d: np.ndarray, e: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    """sturm_count for every shift in xs at once (the same recurrence, vectorised over xs)."""
+    e2 = e * e
+    pivmin = np.finfo(float).tiny * max(1.0, float(np.max(e2)) if len(e2) else 1.0)
+    xs = np.asarray(xs, dtype=float)
+    q = d[0] - xs
+    q = np.where(np.abs(q) <= pivmin, -pivmin, q)
+    count = (q < 0).astype(np.int64)
+    for i in range(1, len(d)):
+        q = d[i] - xs - e2[i - 1] / q
+        q = np.where(np.abs(q) <= pivmin, -pivmin, q)
+        count += q < 0
+    return count
+
+
+def tridiagonal_smallest(d: np.ndarray, e: np.ndarray, k: int) -> np.ndarray:
+    """The k smallest eigenvalues of a symmetric tridiagonal: bisection on the Sturm count,
+    all k brackets advanced together (the same steps as tridiagonal_eigenvalues_bisection)."""
+    r = np.zeros(len(d))
+    r[:-1] += np.abs(e)
+    r[1:] += np.abs(e)
+    lo, hi = float(np.min(d - r)), float(np.max(d + r))
+    idx = np.arange(k)
+    a = np.full(k, lo)
+    b = np.full(k, hi)
+    for _ in range(200):
+        mid = 0.5 * (a + b)
+        above = sturm_counts(d, e, mid) > idx
+        b = np.where(above, mid, b)
+        a = np.where(above, a, mid)
+    return 0.5 * (a + b)
+
+
+def separable_smallest_fast(n: int, ax_col: np.ndarray, a_nodes: np.ndarray, k: int) -> np.ndarray:
+    """separable_smallest with the vectorised bisection."""
+    vals = [tridiagonal_smallest(d, e, min(k, n)) for d, e in separable_tridiagonals(n, ax_col, a_nodes)]
+    return np.sort(np.concatenate(vals))[:k]
+
+
+def separable_lap_plus_v_smallest(n: int, V: np.ndarray, k: int, m: int) -> np.ndarray:
+    """The k smallest eigenvalues of -Lap + V on the n x n grid for separable V[i, j] =
+    V1[i] + V2[j], from the m + 1 smallest eigenvalues of each 1-D operator. Raises if the
+    k-th sum is not provably below every sum that uses an eigenvalue beyond the m-th."""
+    v1 = V[:, 0].copy()
+    v2 = V[0, :] - V[0, 0]
+    if np.max(np.abs(V - (v1[:, None] + v2[None, :]))) > 1e-9 * max(1.0, np.max(np.abs(V))):
+        raise ValueError("V is not separable")
+    h = 1.0 / (n + 1)
+    e = np.full(n - 1, -1.0 / h**2)
+    mu = tridiagonal_smallest(2.0 / h**2 + v1, e, m + 1)
+    nu = tridiagonal_smallest(2.0 / h**2 + v2, e, m + 1)
+    sums = np.sort((mu[:m, None] + nu[None, :m]).ravel())[:k]
+    if not sums[-1] < min(mu[0] + nu[m], mu[m] + nu[0]):
+        raise ValueError("m too small for k")
+    return sums

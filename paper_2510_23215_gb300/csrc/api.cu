@@ -100,6 +100,7 @@ struct ChainBufs {
   double *theta, *res2;            // kb, 2*kb
   double *gemm_partials, *res_partials;
   void* eigh_scratch;
+  void* chol_wide;  // k_b > kSmallBlockWidth: blocked Cholesky working copy
   int* status;
   int* cols;
   // FP32 phase of the mixed form (null otherwise); in the FP64 phase V32 holds the
@@ -134,6 +135,7 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   b.gemm_partials = c.template take<double>((size_t)(kSplitTarget + T * T) * kGemmTile * kGemmTile);
   b.res_partials = c.template take<double>((size_t)resid_blocks(n) * 2 * kb);
   b.eigh_scratch = c.template take<char>(small_eigh_scratch_bytes(kb));
+  b.chol_wide = (kb > kSmallBlockWidth) ? c.template take<char>(chol_wide_scratch_bytes(kb)) : nullptr;
   b.status = c.template take<int>(4);
   b.cols = c.template take<int>(kb);
   b.V32 = b.d32 = b.we32 = b.wn32 = b.partials32 = nullptr;
@@ -538,7 +540,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       float* F2 = b.B32[(which + 2) % 3];
       for (int pass = 0; pass < 2; ++pass) {
         SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, Y, kb, b.G, kb, true, b.partials32, st));
-        SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + pass, st));
+        SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + pass, st,
+                                        b.chol_wide));
         SCSF_CUDA(ctx, launch_gemm_nn_f32(N, kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true, st));
         std::swap(Y, F1);
       }
@@ -640,7 +643,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
       // the first factor only has to precondition, so it is taken in FP32
       SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, pass == 0 && fp32_first, b.C, b.Rinv,
-                                      b.status + pass, st));
+                                      b.status + pass, st, b.chol_wide));
       SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
       std::swap(Y, F1);
       flops += 2.0 * N * ka * ka;

@@ -86,9 +86,7 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
 // x_i = -s_i / L_ii (x_j = 1 / L_jj), broadcasts it, and every lane adds L_ri x_i to
 // its rows r > i. L is staged 32 columns at a time ([k][33] tile, conflict-free).
 // T = float serves the first (preconditioning) Cholesky QR pass, T = double the second.
-constexpr int kTrinvRowsPerLane = (kMaxBlockWidth + 31) / 32;
-
-template <typename T>
+template <typename T, int kTrinvRowsPerLane>
 __global__ void __launch_bounds__(32)
 trinv_kernel(int k, const double* __restrict__ L, double* __restrict__ Rinv) {
   extern __shared__ unsigned char tile_raw[];
@@ -136,6 +134,166 @@ trinv_kernel(int k, const double* __restrict__ L, double* __restrict__ Rinv) {
   }
 }
 
+// ---- wide blocks (k > kSmallBlockWidth): blocked right-looking Cholesky in global memory.
+// The working copy M (T, k x k, lower triangle) lives in the scratch; per 32-column panel one
+// CTA factors the panel (diagonal block and the rows below it, staged in shared memory), then
+// a tiled kernel applies the panel's rank-32 update to the trailing lower triangle.
+constexpr int kPanel = 32;
+
+template <typename T>
+__global__ void chol_load_kernel(int k, const double* __restrict__ G, int ldg, double shift,
+                                 T* __restrict__ M) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)k * k) return;
+  const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+  if (j <= i) M[e] = (T)(G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+chol_panel_kernel(int k, T* __restrict__ M, int p, int* __restrict__ bad) {
+  extern __shared__ unsigned char praw[];
+  T* P = reinterpret_cast<T*>(praw);  // rows p..k-1, 33 columns (32 used)
+  __shared__ T dinv_s;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int rows = k - p, w = min(kPanel, k - p);
+  for (int e = t; e < rows * kPanel; e += nt) {
+    const int r = e / kPanel, c = e - r * kPanel;
+    P[r * 33 + c] = (c < w && c <= r) ? M[(size_t)(p + r) * k + p + c] : T(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (t == 0) {
+      T piv = P[j * 33 + j];
+      if (!(piv > T(0))) {
+        atomicMax(bad, 1);
+        piv = T(1);
+      }
+      const T l = sqrt(piv);
+      P[j * 33 + j] = l;
+      dinv_s = T(1) / l;
+    }
+    __syncthreads();
+    const T inv = dinv_s;
+    for (int r = j + 1 + t; r < rows; r += nt) P[r * 33 + j] *= inv;
+    __syncthreads();
+    // rank-1 update of the panel columns c in (j, w), rows r >= c
+    const int nc = w - j - 1;
+    if (nc > 0)
+      for (int e = t; e < (rows - j - 1) * nc; e += nt) {
+        const int r = j + 1 + e / nc, c = j + 1 + e % nc;
+        if (c <= r) P[r * 33 + c] -= P[r * 33 + j] * P[c * 33 + j];
+      }
+    __syncthreads();
+  }
+  for (int e = t; e < rows * kPanel; e += nt) {
+    const int r = e / kPanel, c = e - r * kPanel;
+    if (c < w && c <= r) M[(size_t)(p + r) * k + p + c] = P[r * 33 + c];
+  }
+}
+
+// M[r][c] -= sum_{q < 32} M[r][p + q] M[c][p + q] for p + 32 <= c <= r < k, one 32 x 32 tile
+// (tile row >= tile column) per CTA.
+template <typename T>
+__global__ void __launch_bounds__(1024)
+chol_trailing_kernel(int k, T* __restrict__ M, int p) {
+  __shared__ T Lr[32][33], Lc[32][33];
+  const int q0 = p + kPanel;
+  const int nt = (k - q0 + 31) / 32;
+  // blockIdx.x enumerates the lower-triangular tiles (ti >= tj)
+  int ti = 0, rem = blockIdx.x;
+  while (rem > ti) {
+    rem -= ti + 1;
+    ++ti;
+  }
+  const int tj = rem;
+  if (ti >= nt) return;
+  const int r0 = q0 + 32 * ti, c0 = q0 + 32 * tj;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  Lr[ty][tx] = (r0 + ty < k) ? M[(size_t)(r0 + ty) * k + p + tx] : T(0);
+  Lc[ty][tx] = (c0 + ty < k) ? M[(size_t)(c0 + ty) * k + p + tx] : T(0);
+  __syncthreads();
+  const int r = r0 + ty, c = c0 + tx;
+  if (r < k && c < k && c <= r) {
+    T acc = T(0);
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) acc = fma(Lr[ty][q], Lc[tx][q], acc);
+    M[(size_t)r * k + c] -= acc;
+  }
+}
+
+template <typename T>
+__global__ void chol_store_kernel(int k, const T* __restrict__ M, double* __restrict__ L) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)k * k) return;
+  const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+  L[e] = (j <= i) ? (double)M[e] : 0.0;
+}
+
+__global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) s += fabs(G[(size_t)i * ldg + i]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// Factor with the restart rule of chol_kernel (shift c_eps k trace(G) 100^(attempt-1)); the
+// host reads the failure flag after each attempt (wide blocks only).
+template <typename T>
+cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* status, double eps,
+                             void* scratch, cudaStream_t st) {
+  Carve cv(scratch, chol_wide_scratch_bytes(k));
+  T* M = cv.take<T>((size_t)k * k);
+  int* bad = cv.take<int>(4);
+  double* tr = cv.take<double>(1);
+  if (!cv.ok) return cudaErrorInvalidValue;
+  const size_t psmem = (size_t)k * 33 * sizeof(T);
+  cudaError_t e = ensure_dynamic_smem((const void*)chol_panel_kernel<T>, psmem);
+  if (e != cudaSuccess) return e;
+  chol_trace_kernel<<<1, 256, 0, st>>>(k, G, ldg, tr);
+  note_launch();
+  double trace = 0.0;
+  if ((e = cudaMemcpyAsync(&trace, tr, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  const long long kk = (long long)k * k;
+  const int eb = (int)((kk + 255) / 256);
+  int attempt = 0, h_bad = 0;
+  for (; attempt < 4; ++attempt) {
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    const double shift = (attempt == 0) ? 0.0 : eps * k * trace * pow(100.0, attempt - 1);
+    if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st)) != cudaSuccess) return e;
+    chol_load_kernel<T><<<eb, 256, 0, st>>>(k, G, ldg, shift, M);
+    note_launch();
+    for (int p = 0; p < k; p += kPanel) {
+      chol_panel_kernel<T><<<1, 1024, psmem, st>>>(k, M, p, bad);
+      note_launch();
+      const int nt = (k - p - kPanel + 31) / 32;
+      if (nt > 0) {
+        chol_trailing_kernel<T><<<nt * (nt + 1) / 2, dim3(32, 32), 0, st>>>(k, M, p);
+        note_launch();
+      }
+    }
+    if ((e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (h_bad == 0) break;
+  }
+  chol_store_kernel<T><<<eb, 256, 0, st>>>(k, M, L);
+  note_launch();
+  const int code = (h_bad != 0) ? 1000 : attempt;
+  if ((e = cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  // `code` lives on this stack frame: the copy must finish before it is popped
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* status, double eps,
                           cudaStream_t st) {
@@ -149,20 +307,42 @@ cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* statu
 
 }  // namespace
 
+size_t chol_wide_scratch_bytes(int k) {
+  return align256((size_t)k * k * sizeof(double)) + 512;
+}
+
 cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double* L, double* Rinv,
-                             int* status, cudaStream_t st) {
+                             int* status, cudaStream_t st, void* wide_scratch) {
   if (k <= 0 || k > kMaxBlockWidth) return cudaErrorInvalidValue;
-  cudaError_t e = fp32 ? launch_chol_t<float>(k, G, ldg, L, status, 1e-6, st)
-                       : launch_chol_t<double>(k, G, ldg, L, status, 1e-14, st);
-  if (e != cudaSuccess) return e;
-  if (fp32) {
-    const size_t smem = (size_t)k * 33 * sizeof(float);
-    if ((e = ensure_dynamic_smem((const void*)trinv_kernel<float>, smem)) != cudaSuccess) return e;
-    trinv_kernel<float><<<k, 32, smem, st>>>(k, L, Rinv);
+  cudaError_t e;
+  if (k <= kSmallBlockWidth) {
+    e = fp32 ? launch_chol_t<float>(k, G, ldg, L, status, 1e-6, st)
+             : launch_chol_t<double>(k, G, ldg, L, status, 1e-14, st);
   } else {
-    const size_t smem = (size_t)k * 33 * sizeof(double);
-    if ((e = ensure_dynamic_smem((const void*)trinv_kernel<double>, smem)) != cudaSuccess) return e;
-    trinv_kernel<double><<<k, 32, smem, st>>>(k, L, Rinv);
+    if (!wide_scratch) return cudaErrorInvalidValue;
+    e = fp32 ? launch_chol_wide<float>(k, G, ldg, L, status, 1e-6, wide_scratch, st)
+             : launch_chol_wide<double>(k, G, ldg, L, status, 1e-14, wide_scratch, st);
+  }
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)k * 33 * (fp32 ? sizeof(float) : sizeof(double));
+  if (k <= kSmallBlockWidth) {
+    constexpr int R = (kSmallBlockWidth + 31) / 32;
+    if (fp32) {
+      if ((e = ensure_dynamic_smem((const void*)trinv_kernel<float, R>, smem)) != cudaSuccess) return e;
+      trinv_kernel<float, R><<<k, 32, smem, st>>>(k, L, Rinv);
+    } else {
+      if ((e = ensure_dynamic_smem((const void*)trinv_kernel<double, R>, smem)) != cudaSuccess) return e;
+      trinv_kernel<double, R><<<k, 32, smem, st>>>(k, L, Rinv);
+    }
+  } else {
+    constexpr int R = (kMaxBlockWidth + 31) / 32;
+    if (fp32) {
+      if ((e = ensure_dynamic_smem((const void*)trinv_kernel<float, R>, smem)) != cudaSuccess) return e;
+      trinv_kernel<float, R><<<k, 32, smem, st>>>(k, L, Rinv);
+    } else {
+      if ((e = ensure_dynamic_smem((const void*)trinv_kernel<double, R>, smem)) != cudaSuccess) return e;
+      trinv_kernel<double, R><<<k, 32, smem, st>>>(k, L, Rinv);
+    }
   }
   note_launch();
   return cudaGetLastError();

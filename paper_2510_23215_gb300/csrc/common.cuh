@@ -7,9 +7,12 @@
 
 namespace scsf {
 
-// Largest block width k_b = k + nex accepted by the solver. The reduced
-// eigensolve keeps two k_b x k_b FP32 matrices in one CTA's shared memory.
-constexpr int kMaxBlockWidth = 160;
+// Largest block width k_b = k + nex accepted by the solver (the 256 x 256, k = 400
+// workload needs 480).
+constexpr int kMaxBlockWidth = 512;
+// Up to this width the reduced eigensolve and the Cholesky factor keep their k_b x k_b
+// matrices in one CTA's shared memory; wider blocks take the global-memory variants.
+constexpr int kSmallBlockWidth = 160;
 
 constexpr int kGemmTile = 32;     // output tile side of the FP64 block GEMMs
 constexpr int kSplitTarget = 304; // CTAs targeted by split-K Gram launches (2 per SM)

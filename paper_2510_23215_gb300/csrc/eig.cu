@@ -23,7 +23,10 @@
 namespace scsf {
 namespace {
 
+// Refinement steps: the FP32 Jacobi result of a wide matrix carries more accumulated
+// rounding (k - 1 rounds per sweep), so it gets two more quadratic steps.
 constexpr int kOaSteps = 2;
+constexpr int kOaStepsWide = 4;
 constexpr int kJacobiSweeps = 30;
 constexpr double kClusterFloor = 3e-3;  // relative gap below which pairs go to FP64 Jacobi
 constexpr double kCleanupTol = 1e-13;   // |P_pq| / ||G|| below which a pair counts as resolved
@@ -48,61 +51,8 @@ __device__ __forceinline__ void jacobi_angle(T app, T aqq, T apq, T& c, T& s) {
   s = tt * c;
 }
 
-// One round of rotations on A (k x k, stride ks) and the columns of V (stride
-// ldv), one warp per pair (a warp owns at most 3 pairs: k <= 160 and 32 warps).
-// `keep(apq, app, aqq)` decides whether a pair rotates. Rows, barrier, columns, barrier.
-template <typename T, typename Keep>
-__device__ __forceinline__ void jacobi_round(T* A, int ks, T* V, int ldv, int k, int kp, int round,
-                                             Keep keep) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int npairs = kp / 2;
-  T cs[3], sn[3];
-  bool act[3] = {false, false, false};
-  int pp[3], qq[3];
-#pragma unroll
-  for (int slot = 0; slot < 3; ++slot) {
-    const int pr = warp + slot * nwarps;
-    if (pr >= npairs) break;
-    int p, q;
-    circle_pair(pr, round, kp, p, q);
-    pp[slot] = p;
-    qq[slot] = q;
-    if (q < k) {
-      const T apq = A[p * ks + q], app = A[p * ks + p], aqq = A[q * ks + q];
-      if (keep(apq, app, aqq)) {
-        jacobi_angle(app, aqq, apq, cs[slot], sn[slot]);
-        act[slot] = true;
-      }
-    }
-    __syncwarp();
-    if (act[slot]) {
-      const T c = cs[slot], s = sn[slot];
-      for (int col = lane; col < k; col += 32) {
-        const T ap = A[p * ks + col], aq = A[q * ks + col];
-        A[p * ks + col] = c * ap - s * aq;
-        A[q * ks + col] = s * ap + c * aq;
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int slot = 0; slot < 3; ++slot) {
-    if (!act[slot]) continue;
-    const int p = pp[slot], q = qq[slot];
-    const T c = cs[slot], s = sn[slot];
-    for (int row = lane; row < k; row += 32) {
-      const T ap = A[row * ks + p], aq = A[row * ks + q];
-      A[row * ks + p] = c * ap - s * aq;
-      A[row * ks + q] = s * ap + c * aq;
-      const T vp = V[row * ldv + p], vq = V[row * ldv + q];
-      V[row * ldv + p] = c * vp - s * vq;
-      V[row * ldv + q] = s * vp + c * vq;
-    }
-  }
-  __syncthreads();
-}
-
-// The same round applied as one similarity step A' = J^T A J, V' = V J, with all k/2
+// One round of the circle method (k/2 disjoint rotations) applied as one similarity
+// step A' = J^T A J, V' = V J (A k x k with stride ks, V's columns with stride ldv), all k/2
 // rotations of the round forming J: for i, j with partners i', j' and coefficients
 // (alpha, beta) -- row_i' = alpha_i row_i + beta_i row_i'(partner), so alpha = c and
 // beta = -s for the first index of a pair, +s for the second, (1, 0) when the pair does
@@ -218,13 +168,16 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
   }
 }
 
+// kWide: A and V live in global scratch `wide` (blocks wider than kSmallBlockWidth, whose
+// two k x k FP32 matrices exceed shared memory); otherwise in dynamic shared memory.
+template <bool kWide>
 __global__ void __launch_bounds__(1024)
 jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, int ldz,
-                  double* __restrict__ lam, int max_sweeps) {
+                  double* __restrict__ lam, int max_sweeps, float* __restrict__ wide) {
   extern __shared__ float smf[];
   const int ks = odd_stride(k);
-  float* A = smf;           // k x ks
-  float* V = smf + k * ks;  // k x ks
+  float* A = kWide ? wide : smf;                      // k x ks
+  float* V = kWide ? wide + k * ks : smf + k * ks;    // k x ks
   __shared__ float red[64];
   __shared__ float s_al[kMaxBlockWidth + 1], s_be[kMaxBlockWidth + 1];
   __shared__ int s_pl[kMaxBlockWidth + 2];
@@ -324,14 +277,17 @@ oa_update_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Eplu
 // Exact FP64 Jacobi on P = Z^T S Z (left half of PQ, symmetrised on load) for
 // the pairs the refinement left coupled. Rotates the columns of Z (global, ld
 // ldz) along. Writes lam = diag(P).
+template <bool kWide>
 __global__ void __launch_bounds__(1024)
 jacobi_f64_cleanup_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Z, int ldz,
-                          double* __restrict__ lam, int max_sweeps) {
+                          double* __restrict__ lam, int max_sweeps, double* __restrict__ wide) {
   extern __shared__ double smd[];
   const int ks = odd_stride(k);
-  double* P = smd;  // k x ks
+  double* P = kWide ? wide : smd;  // k x ks
   __shared__ double nrm;
   __shared__ int nsig;
+  __shared__ double s_al[kMaxBlockWidth + 1], s_be[kMaxBlockWidth + 1];
+  __shared__ int s_pl[kMaxBlockWidth + 2];
   const int t = threadIdx.x, nt = blockDim.x;
   const int ld = 2 * k;
   for (int e = t; e < k * k; e += nt) {
@@ -359,8 +315,9 @@ jacobi_f64_cleanup_kernel(int k, const double* __restrict__ PQ, double* __restri
     __syncthreads();
     if (nsig == 0) break;
     for (int round = 0; round < kp - 1; ++round)
-      jacobi_round<double>(P, ks, Z, ldz, k, kp, round,
-                           [tol](double apq, double, double) { return fabs(apq) > tol; });
+      jacobi_round_blocks<double>(P, ks, Z, ldz, k, kp, round,
+                                  [tol](double apq, double, double) { return fabs(apq) > tol; },
+                                  s_al, s_be, s_pl);
   }
   for (int i = t; i < k; i += nt) lam[i] = P[i * ks + i];
 }
@@ -400,6 +357,8 @@ sort_pairs_kernel(int k, const double* __restrict__ lam, const double* __restric
 // Scratch: S (k x k); two k x 2k panels [T | Z]; PQ (k x 2k); Eplus (k x k); lam; partials.
 struct EighScratch {
   double *S, *TZ0, *TZ1, *PQ, *E, *lam, *partials;
+  float* wide32;   // k > kSmallBlockWidth: the FP32 Jacobi matrices (2 k ks)
+  double* wide64;  // k > kSmallBlockWidth: the FP64 clean-up matrix (k ks)
 };
 
 template <typename C>
@@ -413,6 +372,12 @@ EighScratch carve_eigh(C& c, int k) {
   s.E = c.template take<double>(kk);
   s.lam = c.template take<double>(k);
   s.partials = c.template take<double>(gemm_tn_partials(k, k, 2 * k, false));
+  s.wide32 = nullptr;
+  s.wide64 = nullptr;
+  if (k > kSmallBlockWidth) {
+    s.wide32 = c.template take<float>(2 * (size_t)k * odd_stride(k));
+    s.wide64 = c.template take<double>((size_t)k * odd_stride(k));
+  }
   return s;
 }
 
@@ -429,6 +394,34 @@ cudaError_t set_smem(const void* fn, size_t bytes) {
   return ensure_dynamic_smem(fn, bytes);
 }
 
+
+cudaError_t run_jacobi_f32(int k, const double* S, double* Z, int ldz, double* lam,
+                           const EighScratch& w, cudaStream_t st) {
+  cudaError_t e;
+  if (k <= kSmallBlockWidth) {
+    const size_t smem32 = 2 * (size_t)k * odd_stride(k) * sizeof(float);
+    if ((e = set_smem((const void*)jacobi_f32_kernel<false>, smem32)) != cudaSuccess) return e;
+    jacobi_f32_kernel<false><<<1, 1024, smem32, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, nullptr);
+  } else {
+    jacobi_f32_kernel<true><<<1, 1024, 0, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, w.wide32);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t run_cleanup_f64(int k, const double* PQ, double* Z, int ldz, double* lam,
+                            const EighScratch& w, cudaStream_t st) {
+  cudaError_t e;
+  if (k <= kSmallBlockWidth) {
+    const size_t smem64 = (size_t)k * odd_stride(k) * sizeof(double);
+    if ((e = set_smem((const void*)jacobi_f64_cleanup_kernel<false>, smem64)) != cudaSuccess) return e;
+    jacobi_f64_cleanup_kernel<false><<<1, 1024, smem64, st>>>(k, PQ, Z, ldz, lam, 6, nullptr);
+  } else {
+    jacobi_f64_cleanup_kernel<true><<<1, 1024, 0, st>>>(k, PQ, Z, ldz, lam, 10, w.wide64);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
 }  // namespace
 
 size_t small_eigh_scratch_bytes(int k) {
@@ -447,22 +440,19 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
   const int ld2 = 2 * k;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, S, lds, w.S);
   note_launch();
-  const size_t smem32 = 2 * (size_t)k * odd_stride(k) * sizeof(float);
-  if ((e = set_smem((const void*)jacobi_f32_kernel, smem32)) != cudaSuccess) return e;
   // Z lives in the right half of a [T | Z] panel (ld 2k)
   double* TZ = w.TZ0;
   double* TZn = w.TZ1;
-  jacobi_f32_kernel<<<1, 1024, smem32, st>>>(k, w.S, TZ + k, ld2, nullptr, kJacobiSweeps);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int step = 0; step <= kOaSteps; ++step) {
+  if ((e = run_jacobi_f32(k, w.S, TZ + k, ld2, nullptr, w, st)) != cudaSuccess) return e;
+  const int oa_steps = (k > kSmallBlockWidth) ? kOaStepsWide : kOaSteps;
+  for (int step = 0; step <= oa_steps; ++step) {
     // T = S Z into the left half; PQ = Z^T [T | Z]
     if ((e = launch_gemm_nn(k, k, k, 1.0, w.S, k, TZ + k, ld2, 0.0, TZ, ld2, false, st)) != cudaSuccess)
       return e;
     if ((e = launch_gemm_tn(k, k, 2 * k, TZ + k, ld2, TZ, ld2, w.PQ, ld2, false, w.partials, st)) !=
         cudaSuccess)
       return e;
-    if (step == kOaSteps) break;
+    if (step == oa_steps) break;
     oa_update_kernel<<<1, 1024, 0, st>>>(k, w.PQ, w.E, w.lam, kClusterFloor);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -473,11 +463,7 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
     std::swap(TZ, TZn);
   }
   // exact FP64 rotations for the pairs the refinement treated as clusters
-  const size_t smem64 = (size_t)k * odd_stride(k) * sizeof(double);
-  if ((e = set_smem((const void*)jacobi_f64_cleanup_kernel, smem64)) != cudaSuccess) return e;
-  jacobi_f64_cleanup_kernel<<<1, 1024, smem64, st>>>(k, w.PQ, TZ + k, ld2, w.lam, 6);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = run_cleanup_f64(k, w.PQ, TZ + k, ld2, w.lam, w, st)) != cudaSuccess) return e;
   sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, TZ + k, ld2, evals, Zout, ldz);
   note_launch();
   return cudaGetLastError();
@@ -496,11 +482,7 @@ cudaError_t launch_small_eigh_f32(int k, const double* S, int lds, double* evals
   cudaError_t e;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, S, lds, w.S);
   note_launch();
-  const size_t smem32 = 2 * (size_t)k * odd_stride(k) * sizeof(float);
-  if ((e = set_smem((const void*)jacobi_f32_kernel, smem32)) != cudaSuccess) return e;
-  jacobi_f32_kernel<<<1, 1024, smem32, st>>>(k, w.S, w.TZ0, k, w.lam, kJacobiSweeps);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = run_jacobi_f32(k, w.S, w.TZ0, k, w.lam, w, st)) != cudaSuccess) return e;
   sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, w.TZ0, k, evals, Zout, ldz);
   note_launch();
   return cudaGetLastError();

@@ -56,11 +56,15 @@ cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, con
 cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A, int lda,
                            const double* M, int ldm, double beta, double* C, int ldc, bool upper,
                            cudaStream_t st);
-// Cholesky QR factor (chol.cu): G = L L^T (FP32 or FP64, one CTA, shifted
-// restarts on breakdown) and Rinv = (L^T)^{-1} (upper, ld k, multi-CTA).
-// L: k x k scratch. status[0]: shifted restarts used, 1000 = failed.
+// Cholesky QR factor (chol.cu): G = L L^T (FP32 or FP64, shifted restarts on
+// breakdown) and Rinv = (L^T)^{-1} (upper, ld k, one warp per column).
+// L: k x k scratch. status[0]: shifted restarts used, 1000 = failed. Up to
+// kSmallBlockWidth the factor runs in one CTA's shared memory; wider matrices take a
+// blocked factorisation in wide_scratch (chol_wide_scratch_bytes(k)) and synchronise
+// the stream once per attempt.
+size_t chol_wide_scratch_bytes(int k);
 cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double* L, double* Rinv,
-                             int* status, cudaStream_t st);
+                             int* status, cudaStream_t st, void* wide_scratch = nullptr);
 // out[i*ld_out + j] = in[i*ld_in + j], i < rows, j < cols.
 cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, double* out, int ld_out,
                           cudaStream_t st);

@@ -140,18 +140,20 @@ __global__ void dc_combine_kernel(int rows, int ncols, const double* __restrict_
 }
 
 // Per-column ||(A X)_j - theta_j X_j||^2 and ||(A X)_j||^2 (FP32 products, FP64 sums).
+// blockIdx.y selects a slice of kSmallBlockWidth columns.
 constexpr int kRows32 = 8;
 __global__ void __launch_bounds__(32 * kRows32)
 residual_norms_f32_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int ncols,
                           const double* __restrict__ theta, double* __restrict__ partials) {
-  constexpr int kChunks = kMaxBlockWidth / 32;
+  constexpr int kChunks = kSmallBlockWidth / 32;
   const int n = A.n, N = n * n;
+  const int c0 = blockIdx.y * kSmallBlockWidth;
   double rr[kChunks], aa[kChunks];
   float th[kChunks];
 #pragma unroll
   for (int q = 0; q < kChunks; ++q) {
     rr[q] = aa[q] = 0.0;
-    const int c = threadIdx.x + 32 * q;
+    const int c = c0 + threadIdx.x + 32 * q;
     th[q] = (c < ncols) ? (float)theta[c] : 0.f;
   }
   for (int I = blockIdx.x * kRows32 + threadIdx.y; I < N; I += gridDim.x * kRows32) {
@@ -161,7 +163,7 @@ residual_norms_f32_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int
     const float* row = X + (size_t)I * ldx;
 #pragma unroll
     for (int q = 0; q < kChunks; ++q) {
-      const int c = threadIdx.x + 32 * q;
+      const int c = c0 + threadIdx.x + 32 * q;
       if (c < ncols) {
         const float x = row[c];
         float off = 0.f;
@@ -176,26 +178,24 @@ residual_norms_f32_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int
       }
     }
   }
-  __shared__ double s_r[kRows32][kMaxBlockWidth];
-  __shared__ double s_a[kRows32][kMaxBlockWidth];
+  __shared__ double s_r[kRows32][kSmallBlockWidth];
+  __shared__ double s_a[kRows32][kSmallBlockWidth];
 #pragma unroll
   for (int q = 0; q < kChunks; ++q) {
-    const int c = threadIdx.x + 32 * q;
-    if (c < ncols) {
-      s_r[threadIdx.y][c] = rr[q];
-      s_a[threadIdx.y][c] = aa[q];
-    }
+    const int lc = threadIdx.x + 32 * q;
+    s_r[threadIdx.y][lc] = rr[q];
+    s_a[threadIdx.y][lc] = aa[q];
   }
   __syncthreads();
   if (threadIdx.y == 0) {
-    for (int c = threadIdx.x; c < ncols; c += 32) {
+    for (int lc = threadIdx.x; lc < kSmallBlockWidth && c0 + lc < ncols; lc += 32) {
       double sr = 0.0, sa = 0.0;
       for (int y = 0; y < kRows32; ++y) {
-        sr += s_r[y][c];
-        sa += s_a[y][c];
+        sr += s_r[y][lc];
+        sa += s_a[y][lc];
       }
-      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c] = sr;
-      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c] = sa;
+      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c0 + lc] = sr;
+      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c0 + lc] = sa;
     }
   }
 }
@@ -405,7 +405,8 @@ cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ld
                                       cudaStream_t st) {
   if (ncols > kMaxBlockWidth) return cudaErrorInvalidValue;
   const int nb = resid_blocks(A.n);
-  residual_norms_f32_kernel<<<nb, dim3(32, kRows32), 0, st>>>(A, X, ldx, ncols, theta, partials);
+  const dim3 grid(nb, (ncols + kSmallBlockWidth - 1) / kSmallBlockWidth);
+  residual_norms_f32_kernel<<<grid, dim3(32, kRows32), 0, st>>>(A, X, ldx, ncols, theta, partials);
   note_launch();
   colsum_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
   note_launch();

@@ -11,7 +11,7 @@ namespace {
 
 constexpr int kAsmThreads = 256;
 constexpr int kRowsPerBlock = 8;   // nodes per CTA in the stencil kernels (blockDim.y)
-constexpr int kMaxColChunks = kMaxBlockWidth / 32;
+constexpr int kMaxColChunks = kSmallBlockWidth / 32;  // per column slice (blockIdx.y)
 
 __global__ void assemble_kernel(int kind, int n, const double* __restrict__ ax,
                                 const double* __restrict__ ay, const double* __restrict__ v,
@@ -142,6 +142,7 @@ residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncol
                       const double* __restrict__ theta, double* __restrict__ partials,
                       float* __restrict__ R32, int ldr) {
   const int N = A.n * A.n;
+  const int c0 = blockIdx.y * kSmallBlockWidth;  // this CTA's column slice
   double rr[kMaxColChunks], aa[kMaxColChunks];
 #pragma unroll
   for (int q = 0; q < kMaxColChunks; ++q) rr[q] = aa[q] = 0.0;
@@ -150,7 +151,7 @@ residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncol
     const double* row = X + (size_t)I * ldx;
 #pragma unroll
     for (int q = 0; q < kMaxColChunks; ++q) {
-      const int c = threadIdx.x + 32 * q;
+      const int c = c0 + threadIdx.x + 32 * q;
       if (c < ncols) {
         const double x = row[c];
         const double ax = fma(k.d, x, -offdiag_sum(k, A.n, row, (size_t)ldx, c));
@@ -161,26 +162,24 @@ residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncol
       }
     }
   }
-  __shared__ double s_r[kRowsPerBlock][kMaxBlockWidth];
-  __shared__ double s_a[kRowsPerBlock][kMaxBlockWidth];
+  __shared__ double s_r[kRowsPerBlock][kSmallBlockWidth];
+  __shared__ double s_a[kRowsPerBlock][kSmallBlockWidth];
 #pragma unroll
   for (int q = 0; q < kMaxColChunks; ++q) {
-    const int c = threadIdx.x + 32 * q;
-    if (c < ncols) {
-      s_r[threadIdx.y][c] = rr[q];
-      s_a[threadIdx.y][c] = aa[q];
-    }
+    const int lc = threadIdx.x + 32 * q;
+    s_r[threadIdx.y][lc] = rr[q];
+    s_a[threadIdx.y][lc] = aa[q];
   }
   __syncthreads();
   if (threadIdx.y == 0) {
-    for (int c = threadIdx.x; c < ncols; c += 32) {
+    for (int lc = threadIdx.x; lc < kSmallBlockWidth && c0 + lc < ncols; lc += 32) {
       double sr = 0.0, sa = 0.0;
       for (int y = 0; y < kRowsPerBlock; ++y) {
-        sr += s_r[y][c];
-        sa += s_a[y][c];
+        sr += s_r[y][lc];
+        sa += s_a[y][lc];
       }
-      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c] = sr;
-      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c] = sa;
+      partials[((size_t)blockIdx.x * 2 + 0) * ncols + c0 + lc] = sr;
+      partials[((size_t)blockIdx.x * 2 + 1) * ncols + c0 + lc] = sa;
     }
   }
 }
@@ -237,8 +236,9 @@ cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, in
                                   cudaStream_t st, float* R32, int ldr) {
   if (ncols > kMaxBlockWidth || (R32 && ldr < ncols)) return cudaErrorInvalidValue;
   const int nb = resid_blocks(A.n);
-  residual_norms_kernel<<<nb, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta, partials,
-                                                                R32, ldr);
+  const dim3 grid(nb, (ncols + kSmallBlockWidth - 1) / kSmallBlockWidth);
+  residual_norms_kernel<<<grid, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta,
+                                                                  partials, R32, ldr);
   note_launch();
   column_partials_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
   note_launch();

@@ -140,6 +140,18 @@ def constant_div_a_grad(n: int, value: float = 1.0) -> DivAGradOp:
                       np.full((n, n), value))
 
 
+def separable_lap_plus_v(n: int, seed: int, M: int = 12, amplitude: float = 10.0) -> LapPlusVOp:
+    """-Lap u + V u with V = amplitude (g1(x) + g2(y)), g = sum_p xi_p cos(p pi x),
+    xi ~ N(0, 1) (g1's M coefficients drawn first)."""
+    rng = np.random.default_rng(seed)
+    xi1 = rng.standard_normal(M)
+    xi2 = rng.standard_normal(M)
+    nodes, _ = _grids(n)
+    c = np.cos(np.pi * np.outer(nodes, np.arange(M)))
+    V = amplitude * ((c @ xi1)[:, None] + (c @ xi2)[None, :])
+    return LapPlusVOp(n, np.ascontiguousarray(V))
+
+
 def separable_div_a_grad(n: int, seed: int, M: int = 8) -> DivAGradOp:
     """a = a(x) only: a = exp(0.5 g(x) / M), g = sum_p xi_p cos(p pi x)."""
     rng = np.random.default_rng(seed)

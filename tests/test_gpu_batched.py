@@ -59,6 +59,6 @@ def test_batched_rejects_unsupported_chain():
     dev = need_gpu()
     import paper_2510_23215_gb300 as scsf
     chains, _ = _chains(dev, scsf.FP64, SPECS[:2])
-    chains.append((chains[0][0], scsf.Params(k=300)))  # block width over the limit
+    chains.append((chains[0][0], scsf.Params(k=430)))  # block width 516 over the limit
     with pytest.raises(ValueError):
         scsf.solve_batched(chains, concurrency=2)

@@ -165,7 +165,7 @@ def test_not_converged_and_invalid_arguments():
         chain.step(op)
     assert ei.value.status == scsf.ERR_NOT_CONVERGED
     with pytest.raises(ValueError):
-        scsf.Chain(scsf.Params(k=200), 32, device=dev)
+        scsf.Chain(scsf.Params(k=430), 32, device=dev)  # k_b = 516 > 512
     other = to_dev(si.div_a_grad_chain(20, 1, seed=1), dev)[0]
     with pytest.raises(scsf.ScsfError):
         chain.step(other)

@@ -33,7 +33,7 @@ def test_library_loads_and_exports_every_symbol():
     assert set(scsf.EXPORTED_SYMBOLS) <= declared_functions()
     L = scsf.library()
     assert L.scsf_version() >= 100
-    assert L.scsf_max_block_width() == 160
+    assert L.scsf_max_block_width() == 512
 
 
 def test_workspace_queries_without_gpu():
@@ -43,7 +43,9 @@ def test_workspace_queries_without_gpu():
     p = scsf.Params(k=100, degree=20)._c()
     ws = L.scsf_solve_workspace_size(ctypes.byref(p), 128)
     assert ws >= 4 * 128 * 128 * 120 * 8
-    too_big = scsf.Params(k=200)._c()
+    wide = scsf.Params(k=400)._c()  # k_b = 480: the wide-block path
+    assert L.scsf_solve_workspace_size(ctypes.byref(wide), 256) >= 4 * 256 * 256 * 480 * 8
+    too_big = scsf.Params(k=430)._c()  # k_b = 516 > 512
     assert L.scsf_solve_workspace_size(ctypes.byref(too_big), 128) == 0
     assert L.scsf_sort_workspace_size(200, 8) >= 200 * 8 * 8 * 16
 

@@ -124,6 +124,39 @@ def test_sturm_bisection_closed_form():
     np.testing.assert_allclose(w, sturm.laplacian_1d_eigenvalues(n)[:10], rtol=1e-13)
 
 
+def test_vectorised_bisection_matches_scalar_and_library():
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(30) * 5
+    e = rng.standard_normal(29)
+    w = np.linalg.eigvalsh(np.diag(d) + np.diag(e, 1) + np.diag(e, -1))[:12]
+    v = sturm.tridiagonal_smallest(d, e, 12)
+    np.testing.assert_allclose(v, w, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v, sturm.tridiagonal_eigenvalues_bisection(d, e, 12), rtol=1e-14,
+                               atol=1e-14)
+    xs = np.array([-3.0, 0.0, 2.5])
+    assert list(sturm.sturm_counts(d, e, xs)) == [sturm.sturm_count(d, e, x) for x in xs]
+
+
+def test_separable_fast_matches_dense():
+    n = 12
+    op = si.separable_div_a_grad(n, seed=6)
+    w = np.linalg.eigvalsh(operators.assemble(op).toarray())[:30]
+    np.testing.assert_allclose(sturm.separable_smallest_fast(n, op.ax[:, 0], op.P[:, 0], 30), w,
+                               rtol=1e-12)
+
+
+def test_separable_potential_matches_dense_and_rejects_short_lists():
+    n = 12
+    op = si.separable_lap_plus_v(n, seed=4)
+    w = np.linalg.eigvalsh(operators.assemble(op).toarray())[:40]
+    np.testing.assert_allclose(sturm.separable_lap_plus_v_smallest(n, op.V, 40, m=11), w,
+                               rtol=1e-11, atol=1e-9)
+    with pytest.raises(ValueError):
+        sturm.separable_lap_plus_v_smallest(n, op.V, 40, m=3)
+    with pytest.raises(ValueError):
+        sturm.separable_lap_plus_v_smallest(n, op.V + np.eye(n), 10, m=11)
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_inertia_count_matches_dense(seed):
     n = 9
