@@ -62,7 +62,8 @@ __device__ __forceinline__ void jacobi_angle(T app, T aqq, T apq, T& c, T& s) {
 // second barrier, with all 1024 threads busy in the block pass.
 template <typename T, typename Keep>
 __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv, int k, int kp,
-                                                    int round, Keep keep, T* al, T* be, int* plist) {
+                                                    int round, Keep keep, T* al, T* be, int* plist,
+                                                    int* nrot = nullptr) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
   const int npairs = kp / 2;
@@ -78,6 +79,7 @@ __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv,
       if (keep(apq, app, aqq)) {
         jacobi_angle(app, aqq, apq, c, sn);
         act = true;
+        if (nrot) atomicAdd(nrot, 1);
       }
     }
     al[p] = act ? c : T(1);
@@ -97,6 +99,8 @@ __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv,
       const int pb = plist[2 * b], qb = plist[2 * b + 1];
       const bool hb = qb < k;
       const T c_p = al[pb], d_p = be[pb];
+      // a block between two pairs that do not rotate stays as it is
+      if (b_p == T(0) && d_p == T(0)) continue;
       const T c_q = hb ? al[qb] : T(1), d_q = hb ? be[qb] : T(0);
       const T s_pp = A[pa * ks + pb];
       const T s_pq = hb ? A[pa * ks + qb] : T(0);
@@ -181,6 +185,7 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
   __shared__ float red[64];
   __shared__ float s_al[kMaxBlockWidth + 1], s_be[kMaxBlockWidth + 1];
   __shared__ int s_pl[kMaxBlockWidth + 2];
+  __shared__ int s_nrot;
   const int t = threadIdx.x, nt = blockDim.x;
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
@@ -204,12 +209,16 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
     // The refinement's cluster threshold scales with this residue, so it must be small.
     if (off <= 1e-13f * all || (off < 1e-10f * all && off > 0.5f * prev_off)) break;
     prev_off = off;
+    if (t == 0) s_nrot = 0;
+    __syncthreads();
     for (int round = 0; round < kp - 1; ++round)
       // threshold Jacobi: entries already at FP32 rounding level relative to their
       // diagonal pair are left alone, so late sweeps rotate (and move) little
       jacobi_round_blocks<float>(A, ks, V, ks, k, kp, round, [](float apq, float app, float aqq) {
         return fabsf(apq) > 3e-8f * (fabsf(app) + fabsf(aqq)) && apq != 0.f;
-      }, s_al, s_be, s_pl);
+      }, s_al, s_be, s_pl, &s_nrot);
+    // a sweep without a single rotation above the threshold leaves nothing to do
+    if (s_nrot == 0) break;
   }
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
