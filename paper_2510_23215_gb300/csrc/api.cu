@@ -38,7 +38,10 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
-constexpr size_t kPinnedDoubles = 4 * kMaxBlockWidth + 64;
+// FP32-phase filters of up to this degree replay a captured graph (scalars in a device table)
+constexpr int kMaxGraphSteps = 1024;
+constexpr size_t kPinnedCoefOffset = 4 * kMaxBlockWidth + 64;  // doubles before the float table
+constexpr size_t kPinnedDoubles = kPinnedCoefOffset + (3 * kMaxGraphSteps + 1) / 2;
 
 scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -106,6 +109,7 @@ struct ChainBufs {
   // FP32 phase of the mixed form (null otherwise); in the FP64 phase V32 holds the
   // FP32 residual block of the defect-corrected filter, B32 its remainder blocks
   float *V32, *B32[3], *d32, *we32, *wn32, *partials32;
+  float* coef32;  // [kMaxGraphSteps][3] scalars of the captured FP32 filter
   float* ytab;  // [degree][kb] scalar filter values at the Ritz values
   double* ym;   // [2][kb] recurrence state; y_m in the second row
 };
@@ -142,7 +146,9 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   b.B32[0] = b.B32[1] = b.B32[2] = nullptr;
   b.ytab = nullptr;
   b.ym = nullptr;
+  b.coef32 = nullptr;
   if (mixed) {
+    b.coef32 = c.template take<float>(3 * (size_t)kMaxGraphSteps);
     b.ytab = c.template take<float>((size_t)std::max(degree, 1) * kb);
     b.ym = c.template take<double>(2 * (size_t)kb);
     b.V32 = c.template take<float>(blk);
@@ -297,6 +303,44 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
   return launch_dc_combine(A.n * A.n, ncols, X, ldx, ystate + ncols, zb[cur], ldz, Y, ldy, st);
 }
 
+// Launch width of the FP32 filter step per (n, k_b): the first chain of a shape times
+// 128 / 256 / 512 / 1024 threads per CTA over 16 steps each on its own buffers (CUDA events
+// on its stream) and keeps the fastest for the process.
+int tuned_f32_threads(const Stencil32& A, const float* X, int kb, float* out, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> best;
+  const std::pair<int, int> key(A.n, kb);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = best.find(key);
+    if (it != best.end()) return it->second;
+  }
+  int pick = 256;
+  float pick_ms = INFINITY;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    for (int threads : {128, 256, 512, 1024}) {
+      launch_cheb_step_f32(A, X, kb, nullptr, 0, out, kb, kb, 1.f, 0.f, 0.f, st, threads);
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 16; ++r)
+        launch_cheb_step_f32(A, X, kb, nullptr, 0, out, kb, kb, 1.f, 0.f, 0.f, st, threads);
+      cudaEventRecord(e1, st);
+      float ms = INFINITY;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+          ms < pick_ms) {
+        pick_ms = ms;
+        pick = threads;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> g(mu);
+  best.emplace(key, pick);
+  return pick;
+}
+
 }  // namespace
 
 struct scsf_chain {
@@ -306,7 +350,76 @@ struct scsf_chain {
   ChainBufs b{};
   bool has_block = false;
   std::vector<double> ritz;  // Ritz values of the kept block (warm start)
+  // captured FP32-phase filter (a11): m table-driven steps on fixed buffers
+  cudaGraphExec_t g32 = nullptr;
+  int g32_m = 0, g32_threads = 0;
+  ~scsf_chain() {
+    if (g32) cudaGraphExecDestroy(g32);
+  }
 };
+
+namespace {
+
+// The FP32 filter of the mixed form's FP32 phase as a replay of a captured graph: the m
+// steps' scalars go to the device table b.coef32 (one small copy), the graph (captured
+// once per chain and degree, on the chain's fixed buffers) runs the m table-driven steps.
+// Y_i lands in B32[(i - 1) % 3] exactly as in run_filter_f32.
+cudaError_t run_filter_f32_graph(scsf_chain* ch, const Stencil32& A, int m, double lam, double c,
+                                 double e, int* which, cudaStream_t st) {
+  ChainBufs& b = ch->b;
+  const int kb = ch->kb;
+  // the legacy default stream cannot be captured: plain launches there
+  if (m > kMaxGraphSteps || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+    return run_filter_f32(A, b.V32, kb, kb, m, lam, c, e, b.B32, kb, which, st);
+  cudaError_t err;
+  if (!ch->g32 || ch->g32_m != m) {
+    if (ch->g32) {
+      cudaGraphExecDestroy(ch->g32);
+      ch->g32 = nullptr;
+    }
+    const int threads = tuned_f32_threads(A, b.V32, kb, b.B32[0], st);
+    if ((err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
+    const float* prev = nullptr;
+    const float* cur = b.V32;
+    for (int i = 0; i < m; ++i) {
+      float* out = b.B32[i % 3];
+      err = launch_cheb_step_f32_tab(A, cur, kb, prev, kb, out, kb, kb, b.coef32 + 3 * i, threads, st);
+      if (err != cudaSuccess) break;
+      prev = cur;
+      cur = out;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(st, &graph);
+    if (err == cudaSuccess) err = end;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&ch->g32, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return err;
+    ch->g32_m = m;
+    ch->g32_threads = threads;
+  }
+  float* h = reinterpret_cast<float*>(ch->ctx->pinned + kPinnedCoefOffset);
+  const double sigma1 = e / (lam - c);
+  double sigma = sigma1;
+  h[0] = (float)(sigma1 / e);
+  h[1] = (float)(-sigma1 * c / e);
+  h[2] = 0.f;
+  for (int i = 1; i < m; ++i) {
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    h[3 * i] = (float)(2.0 * sigma_next / e);
+    h[3 * i + 1] = (float)(-2.0 * sigma_next * c / e);
+    h[3 * i + 2] = (float)(-sigma_next * sigma);
+    sigma = sigma_next;
+  }
+  if ((err = cudaMemcpyAsync(b.coef32, h, 3 * (size_t)m * sizeof(float), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+    return err;
+  if ((err = cudaGraphLaunch(ch->g32, st)) != cudaSuccess) return err;
+  for (int i = 0; i < m; ++i) note_launch();
+  *which = (m - 1) % 3;
+  return cudaSuccess;
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -531,7 +644,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
       int which = 0;
       SCSF_CUDA(ctx, mark(0));
-      SCSF_CUDA(ctx, run_filter_f32(A32, b.V32, kb, kb, m32, lam, c, e, b.B32, kb, &which, st));
+      SCSF_CUDA(ctx, run_filter_f32_graph(ch, A32, m32, lam, c, e, &which, st));
       SCSF_CUDA(ctx, mark(1));
       filter32_steps += m32;
       felems32 += (double)m32 * N * kb;

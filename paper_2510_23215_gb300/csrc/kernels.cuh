@@ -91,7 +91,12 @@ cudaError_t launch_block_f64_to_f32(int rows, int cols, const double* in, int ld
                                     int ld_out, cudaStream_t st);
 cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, const float* prev,
                                  int ldp, float* out, int ldo, int ncols, float s1, float s2,
-                                 float s3, cudaStream_t st);
+                                 float s3, cudaStream_t st, int threads = 256);
+// The step with {s1, s2, s3} read from device memory at coef (for captured graphs; the
+// caller counts the launch). prev is read whenever non-null.
+cudaError_t launch_cheb_step_f32_tab(const Stencil32& A, const float* cur, int ldc,
+                                     const float* prev, int ldp, float* out, int ldo, int ncols,
+                                     const float* coef, int threads, cudaStream_t st);
 cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ldx, int ncols,
                                       const double* theta, double* partials, double* out2,
                                       cudaStream_t st);

@@ -44,10 +44,10 @@ __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
 }
 
 // out = s1 (A cur) + s2 cur + s3 prev, one float4 of one node row per thread.
-__global__ void __launch_bounds__(kThreads)
-cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
-                     const float* __restrict__ prev, int ldp, float* __restrict__ out, int ldo,
-                     int quads, float s1, float s2, float s3) {
+__device__ __forceinline__ void cheb_step_f32_body(const Stencil32& A, const float* __restrict__ cur,
+                                                   int ldc, const float* __restrict__ prev, int ldp,
+                                                   float* __restrict__ out, int ldo, int quads,
+                                                   float s1, float s2, float s3) {
   const int n = A.n;
   const long long N = (long long)n * n;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,6 +67,22 @@ cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
                          fmaf(-s1, acc.z, diag * y.z), fmaf(-s1, acc.w, diag * y.w));
   if (prev) r = fma4(s3, ld4(prev + (size_t)I * ldp + c), r);
   st4(out + (size_t)I * ldo + c, r);
+}
+
+__global__ void __launch_bounds__(1024)
+cheb_step_f32_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
+                     const float* __restrict__ prev, int ldp, float* __restrict__ out, int ldo,
+                     int quads, float s1, float s2, float s3) {
+  cheb_step_f32_body(A, cur, ldc, prev, ldp, out, ldo, quads, s1, s2, s3);
+}
+
+// The same step with its scalars read from a device table (coef = {s1, s2, s3}), so that a
+// captured graph of the whole filter can be replayed with new scalars every iteration.
+__global__ void __launch_bounds__(1024)
+cheb_step_f32_tab_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
+                         const float* __restrict__ prev, int ldp, float* __restrict__ out, int ldo,
+                         int quads, const float* __restrict__ coef) {
+  cheb_step_f32_body(A, cur, ldc, prev, ldp, out, ldo, quads, coef[0], coef[1], coef[2]);
 }
 
 // ---- defect-corrected filter ------------------------------------------------
@@ -390,13 +406,26 @@ cudaError_t launch_block_f64_to_f32(int rows, int cols, const double* in, int ld
 
 cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, const float* prev,
                                  int ldp, float* out, int ldo, int ncols, float s1, float s2,
-                                 float s3, cudaStream_t st) {
+                                 float s3, cudaStream_t st, int threads) {
   if (ncols % 4 || ldc % 4 || ldo % 4 || (prev && ldp % 4)) return cudaErrorInvalidValue;
+  if (threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
   const int quads = ncols / 4;
   const long long tot = (long long)A.n * A.n * quads;
-  cheb_step_f32_kernel<<<blocks_for(tot, kThreads), kThreads, 0, st>>>(
+  cheb_step_f32_kernel<<<blocks_for(tot, threads), threads, 0, st>>>(
       A, cur, ldc, (s3 != 0.f) ? prev : nullptr, ldp, out, ldo, quads, s1, s2, s3);
   note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step_f32_tab(const Stencil32& A, const float* cur, int ldc,
+                                     const float* prev, int ldp, float* out, int ldo, int ncols,
+                                     const float* coef, int threads, cudaStream_t st) {
+  if (ncols % 4 || ldc % 4 || ldo % 4 || (prev && ldp % 4)) return cudaErrorInvalidValue;
+  if (threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
+  const int quads = ncols / 4;
+  const long long tot = (long long)A.n * A.n * quads;
+  cheb_step_f32_tab_kernel<<<blocks_for(tot, threads), threads, 0, st>>>(A, cur, ldc, prev, ldp,
+                                                                         out, ldo, quads, coef);
   return cudaGetLastError();
 }
 
