@@ -752,25 +752,62 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       }
       flops += 8.0 * N * nl * ka;
     }
-    for (int pass = 0; pass < 2; ++pass) {
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
-      // the first factor only has to precondition, so it is taken in FP32
-      SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, pass == 0 && fp32_first, b.C, b.Rinv,
-                                      b.status + pass, st, b.chol_wide));
+    if (!mixed) {
+      for (int pass = 0; pass < 2; ++pass) {
+        SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+        // the first factor only has to precondition, so it is taken in FP32
+        SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, pass == 0 && fp32_first, b.C, b.Rinv,
+                                        b.status + pass, st, b.chol_wide));
+        SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
+        std::swap(Y, F1);
+        flops += 2.0 * N * ka * ka;
+      }
+      SCSF_CUDA(ctx, mark(2));
+      // Rayleigh quotient G = Q^T A Q on the active columns
+      SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+      SCSF_CUDA(ctx, mark(3));
+      // reduced eigenproblem and rotation back
+      SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, mark(4));
+      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
+      SCSF_CUDA(ctx, mark(5));
+    } else {
+      // Mixed form: the same Cholesky QR2, Rayleigh-Ritz and rotation with two FP64 block
+      // products fewer. Pass 1's Gram matrix is taken in FP32 when its factor is (both only
+      // precondition); pass 2 only factors Q1^T Q1 = R2^T R2, and R2^{-1} is folded into the
+      // small matrices: H = R2^{-T} (Q1^T A Q1) R2^{-1}, X = Q1 (R2^{-1} Z), the same H and X
+      // as with Q = Q1 R2^{-1}.
+      if (fp32_first) {
+        SCSF_CUDA(ctx, launch_block_f64_to_f32(N, ka, Y, kb, b.B32[0], kb, st));
+        SCSF_CUDA(ctx, launch_gemm_tn_f32(N, ka, ka, b.B32[0], kb, b.B32[0], kb, b.G, ka, true,
+                                          b.partials32, st));
+      } else {
+        SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+      }
+      SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, fp32_first, b.C, b.Rinv, b.status, st,
+                                      b.chol_wide));
       SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
-      std::swap(Y, F1);
-      flops += 2.0 * N * ka * ka;
+      std::swap(Y, F1);  // Y = Q1
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+      SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, false, b.C, b.Rinv, b.status + 1, st,
+                                      b.chol_wide));
+      flops += 1.5 * N * ka * ka;
+      SCSF_CUDA(ctx, mark(2));
+      SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+      // H = R2^{-T} (H1 R2^{-1}) with T = H1 R2^{-1} in b.G
+      SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.H, ka, b.Rinv, ka, 0.0, b.G, ka, true, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(ka, ka, ka, b.Rinv, ka, b.G, ka, b.H, ka, false, b.gemm_partials,
+                                    st));
+      SCSF_CUDA(ctx, mark(3));
+      SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, mark(4));
+      // X = Q1 M, M = R2^{-1} Z in b.C
+      SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.Rinv, ka, b.Z, ka, 0.0, b.C, ka, false, st));
+      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.C, ka, 0.0, b.V + nl, kb, false, st));
+      SCSF_CUDA(ctx, mark(5));
     }
-    SCSF_CUDA(ctx, mark(2));
-    // Rayleigh quotient G = Q^T A Q on the active columns
-    SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
-    SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
-    SCSF_CUDA(ctx, mark(3));
-    // reduced eigenproblem and rotation back
-    SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
-    SCSF_CUDA(ctx, mark(4));
-    SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
-    SCSF_CUDA(ctx, mark(5));
     rot_launches += 1;
     rot_flops += 2.0 * N * ka * ka;
     // residuals of the new Ritz pairs (App. D.5), then lock a converged prefix

@@ -115,6 +115,8 @@ __global__ void dc_ytab_kernel(const double* __restrict__ theta, int ncols, DcSt
 }
 
 constexpr int kDcRows = 8;
+constexpr int kDcUnroll = 4;  // column chunks of 32 in flight per thread
+template <bool kCur, bool kPrev>
 __global__ void __launch_bounds__(32 * kDcRows)
 cheb_step_dc_kernel(Stencil32 A, const float* __restrict__ cur, const float* __restrict__ prev,
                     int ld, const float* __restrict__ R, int ldr, const float* __restrict__ ycol,
@@ -122,24 +124,48 @@ cheb_step_dc_kernel(Stencil32 A, const float* __restrict__ cur, const float* __r
   const int n = A.n, N = n * n;
   for (int I = blockIdx.x * kDcRows + threadIdx.y; I < N; I += gridDim.x * kDcRows) {
     const int i = I / n, j = I - i * n;
-    const float d = A.d[I];
-    const float wS = (i < n - 1) ? A.we[I] : 0.f, wN = (i > 0) ? A.we[I - n] : 0.f;
-    const float wE = (j < n - 1) ? A.wn[I] : 0.f, wW = (j > 0) ? A.wn[I - 1] : 0.f;
+    float d = 0.f, wS = 0.f, wN = 0.f, wE = 0.f, wW = 0.f;
+    if (kCur) {
+      d = A.d[I];
+      wS = (i < n - 1) ? A.we[I] : 0.f;
+      wN = (i > 0) ? A.we[I - n] : 0.f;
+      wE = (j < n - 1) ? A.wn[I] : 0.f;
+      wW = (j > 0) ? A.wn[I - 1] : 0.f;
+    }
     const size_t o = (size_t)I * ld;
-    for (int c = threadIdx.x; c < ncols; c += 32) {
-      float r = s1 * R[(size_t)I * ldr + c] * ycol[c];
-      if (cur) {
-        const float* row = cur + o + c;
-        float acc = 0.f;
-        if (i < n - 1) acc = fmaf(wS, row[(size_t)n * ld], acc);
-        if (i > 0) acc = fmaf(wN, row[-(long long)n * ld], acc);
-        if (j < n - 1) acc = fmaf(wE, row[ld], acc);
-        if (j > 0) acc = fmaf(wW, row[-(long long)ld], acc);
-        const float y = row[0];
-        r = fmaf(s1, fmaf(d, y, -acc), fmaf(s2, y, r));
+    const float* rrow = R + (size_t)I * ldr;
+    for (int c0 = threadIdx.x; c0 < ncols; c0 += 32 * kDcUnroll) {
+      // all loads of kDcUnroll chunks first, then the arithmetic and the stores
+      float rv[kDcUnroll], yc[kDcUnroll], y0[kDcUnroll], ys[kDcUnroll], yn[kDcUnroll],
+          ye[kDcUnroll], yw[kDcUnroll], yp[kDcUnroll];
+#pragma unroll
+      for (int u = 0; u < kDcUnroll; ++u) {
+        const int c = c0 + 32 * u;
+        const bool ok = c < ncols;
+        rv[u] = ok ? rrow[c] : 0.f;
+        yc[u] = ok ? ycol[c] : 0.f;
+        if (kCur) {
+          const float* row = cur + o + c;
+          y0[u] = ok ? row[0] : 0.f;
+          ys[u] = (ok && i < n - 1) ? row[(size_t)n * ld] : 0.f;
+          yn[u] = (ok && i > 0) ? row[-(long long)n * ld] : 0.f;
+          ye[u] = (ok && j < n - 1) ? row[ld] : 0.f;
+          yw[u] = (ok && j > 0) ? row[-(long long)ld] : 0.f;
+        }
+        if (kPrev) yp[u] = ok ? prev[o + c] : 0.f;
       }
-      if (prev) r = fmaf(s3, prev[o + c], r);
-      out[o + c] = r;
+#pragma unroll
+      for (int u = 0; u < kDcUnroll; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= ncols) break;
+        float r = s1 * rv[u] * yc[u];
+        if (kCur) {
+          const float acc = fmaf(wW, yw[u], fmaf(wE, ye[u], fmaf(wN, yn[u], wS * ys[u])));
+          r = fmaf(s1, fmaf(d, y0[u], -acc), fmaf(s2, y0[u], r));
+        }
+        if (kPrev) r = fmaf(s3, yp[u], r);
+        out[o + c] = r;
+      }
     }
   }
 }
@@ -487,8 +513,16 @@ cudaError_t launch_cheb_step_dc(const Stencil32& A, const float* cur, const floa
   if (ncols < 1 || ld < ncols || ldr < ncols) return cudaErrorInvalidValue;
   const long long N = (long long)A.n * A.n;
   const int nb = (int)std::min<long long>((N + kDcRows - 1) / kDcRows, 152LL * 16);
-  cheb_step_dc_kernel<<<nb, dim3(32, kDcRows), 0, st>>>(A, cur, (s3 != 0.f) ? prev : nullptr, ld,
-                                                        R, ldr, ycol, out, ncols, s1, s2, s3);
+  const dim3 block(32, kDcRows);
+  if (!cur)
+    cheb_step_dc_kernel<false, false><<<nb, block, 0, st>>>(A, cur, nullptr, ld, R, ldr, ycol, out,
+                                                             ncols, s1, s2, s3);
+  else if (!prev || s3 == 0.f)
+    cheb_step_dc_kernel<true, false><<<nb, block, 0, st>>>(A, cur, nullptr, ld, R, ldr, ycol, out,
+                                                            ncols, s1, s2, s3);
+  else
+    cheb_step_dc_kernel<true, true><<<nb, block, 0, st>>>(A, cur, prev, ld, R, ldr, ycol, out, ncols,
+                                                           s1, s2, s3);
   note_launch();
   return cudaGetLastError();
 }
