@@ -256,10 +256,21 @@ void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3
 // Defect-corrected filter of the FP64 phase (mixed form): X (FP64, ncols active
 // columns) with its residual block R = A X - X diag(theta) (FP32) and Ritz values theta
 // (device). The remainder Z runs through zb; Y = X diag(y_m) + Z_m lands in Y (FP64).
+// Optional deflation of the remainder against locked columns before the combine: the
+// active X is already orthogonal to them, so only Z carries locked components; removing
+// them here with FP32 products (one classical Gram-Schmidt pass) leaves one FP64 pass for
+// the caller instead of two.
+struct DcDeflate {
+  const float* V32 = nullptr;  // FP32 copies of the locked columns (ld ldv)
+  int ldv = 0, nl = 0;
+  double* C = nullptr;         // nl x ncols
+  float* partials = nullptr;   // gemm_tn_f32 partial sums
+};
+
 cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const float* R, int ldr,
                           const double* theta, int ncols, int degree, double lam, double c,
                           double e, float* const zb[3], int ldz, float* ytab, double* ystate,
-                          double* Y, int ldy, cudaStream_t st) {
+                          double* Y, int ldy, cudaStream_t st, const DcDeflate* defl = nullptr) {
   // coefficients of step i (Y_i -> Y_{i+1}): s1 A Y_i + s2 Y_i + s3 Y_{i-1}
   std::vector<double> s1(degree), s2(degree), s3(degree);
   const double sigma1 = e / (lam - c);
@@ -299,6 +310,15 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
     if (err != cudaSuccess) return err;
     prev = zb[cur];
     cur = nxt;
+  }
+  if (defl && defl->nl > 0) {
+    const int N = A.n * A.n;
+    err = launch_gemm_tn_f32(N, defl->nl, ncols, defl->V32, defl->ldv, zb[cur], ldz, defl->C, ncols,
+                             false, defl->partials, st);
+    if (err != cudaSuccess) return err;
+    err = launch_gemm_nn_f32(N, defl->nl, ncols, -1.f, defl->V32, defl->ldv, defl->C, ncols, 1.f,
+                             zb[cur], ldz, false, st);
+    if (err != cudaSuccess) return err;
   }
   return launch_dc_combine(A.n * A.n, ncols, X, ldx, ystate + ncols, zb[cur], ldz, Y, ldy, st);
 }
@@ -729,8 +749,15 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     const bool dc = mixed && have_R;
     SCSF_CUDA(ctx, mark(0));
     if (dc) {
+      // locked columns [0, nl) of b.V32 hold FP32 copies of the locked vectors
+      DcDeflate defl;
+      defl.V32 = b.V32;
+      defl.ldv = kb;
+      defl.nl = nl;
+      defl.C = b.C;
+      defl.partials = b.partials32;
       SCSF_CUDA(ctx, run_filter_dc(A32, b.V + nl, kb, b.V32 + nl, kb, dc_theta, ka, m, lam, c, e,
-                                   b.B32, kb, b.ytab, b.ym, bufs[0], kb, st));
+                                   b.B32, kb, b.ytab, b.ym, bufs[0], kb, st, &defl));
       dc_steps += m;
       dc_elems += (double)m * N * ka;
     } else {
@@ -746,11 +773,13 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     double* F2 = bufs[(which + 2) % 3];
     // orthonormalise [locked | active]: CGS2 against the locked block, then CholQR2
     if (nl > 0) {
-      for (int pass = 0; pass < 2; ++pass) {
+      // the defect-corrected filter already took the first pass (in FP32, on Z)
+      const int passes = dc ? 1 : 2;
+      for (int pass = 0; pass < passes; ++pass) {
         SCSF_CUDA(ctx, launch_gemm_tn(N, nl, ka, b.V, kb, Y, kb, b.C, ka, false, b.gemm_partials, st));
         SCSF_CUDA(ctx, launch_gemm_nn(N, nl, ka, -1.0, b.V, kb, b.C, ka, 1.0, Y, kb, false, st));
       }
-      flops += 8.0 * N * nl * ka;
+      flops += 4.0 * passes * N * nl * ka;
     }
     if (!mixed) {
       for (int pass = 0; pass < 2; ++pass) {
@@ -849,6 +878,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       locked_res.push_back(r_h[j]);
     }
     for (int j = 0; j < ka; ++j) ch->ritz[nl + j] = theta_h[j];
+    if (mixed && nconv > 0)  // FP32 copies of the newly locked vectors (deflation of Z)
+      SCSF_CUDA(ctx, launch_block_f64_to_f32(N, nconv, b.V + nl, kb, b.V32 + nl, kb, st));
     nl += nconv;
     have_R = mixed;
     dc_theta = b.theta + nconv;
