@@ -78,6 +78,12 @@ int scsf_version(void);
 size_t scsf_sort_workspace_size(int64_t n_ops, int p0);
 scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
                       int start, void* workspace, size_t workspace_bytes, int32_t* perm_out);
+/* scsf_sort that also writes dist_out [n_ops] (FP64, device): the squared feature distance
+ * from each visited problem to its predecessor in the chain (0 for the first); the
+ * learned proposal uses it to find far steps. Same arguments and limits otherwise. */
+scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                           int start, void* workspace, size_t workspace_bytes, int32_t* perm_out,
+                           double* dist_out);
 
 /* scsf_sort without a caller workspace, for callers that cannot allocate device
  * memory where they sort (a host framework that owns all device memory through

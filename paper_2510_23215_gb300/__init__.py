@@ -45,7 +45,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_param_count", "scsf_proposal_workspace_size", "scsf_proposal_init",
     "scsf_proposal_forward", "scsf_proposal_train_step", "scsf_proposal_target_scratch",
     "scsf_proposal_targets", "scsf_proposal_prolong",
-    "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc",
+    "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist",
 ]
 
 
@@ -111,6 +111,8 @@ def library() -> ctypes.CDLL:
     L.scsf_sort_workspace_size.argtypes = [i64, i32]
     L.scsf_sort_workspace_size.restype = sz
     L.scsf_sort.argtypes = [vp, vp, i64, i32, i32, i32, vp, sz, vp]
+    L.scsf_sort_dist.argtypes = [vp, vp, i64, i32, i32, i32, vp, sz, vp, vp]
+    L.scsf_sort_dist.restype = ctypes.c_int
     L.scsf_max_block_width.restype = i32
     L.scsf_solve_workspace_size.argtypes = [ctypes.POINTER(_CParams), i32]
     L.scsf_solve_workspace_size.restype = sz
@@ -312,8 +314,10 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] = None) -> torch.Tensor:
-    """Alg. 2: visiting order of the problems (int32 [n_ops]) from fields [n_ops, p, p] FP64."""
+def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] = None,
+         return_distances: bool = False):
+    """Alg. 2: visiting order of the problems (int32 [n_ops]) from fields [n_ops, p, p] FP64;
+    with return_distances also the squared feature distance of each step (FP64 [n_ops])."""
     _check(fields, "fields")
     if fields.dim() != 3 or fields.shape[1] != fields.shape[2]:
         raise ValueError("fields must be [n_ops, p, p]")
@@ -322,9 +326,14 @@ def sort(fields: torch.Tensor, p0: int, start: int = 0, ctx: Optional[Context] =
     n_ops, p = int(fields.shape[0]), int(fields.shape[1])
     ws = _workspace(L.scsf_sort_workspace_size(n_ops, p0), fields.device)
     perm = torch.empty(n_ops, dtype=torch.int32, device=fields.device)
-    c.check(L.scsf_sort(c.handle, fields.data_ptr(), n_ops, p, p0, start, ws.data_ptr(),
-                        ws.numel(), perm.data_ptr()))
-    return perm
+    if not return_distances:
+        c.check(L.scsf_sort(c.handle, fields.data_ptr(), n_ops, p, p0, start, ws.data_ptr(),
+                            ws.numel(), perm.data_ptr()))
+        return perm
+    dist = torch.empty(n_ops, dtype=torch.float64, device=fields.device)
+    c.check(L.scsf_sort_dist(c.handle, fields.data_ptr(), n_ops, p, p0, start, ws.data_ptr(),
+                             ws.numel(), perm.data_ptr(), dist.data_ptr()))
+    return perm, dist
 
 
 def sort_noalloc(fields: torch.Tensor, p0: int, start: int = 0,

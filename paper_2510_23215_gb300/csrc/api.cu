@@ -495,8 +495,9 @@ size_t scsf_sort_workspace_size(int64_t n_ops, int p0) {
   return sort_workspace_bytes(n_ops, p0);
 }
 
-scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0, int start,
-                      void* workspace, size_t workspace_bytes, int32_t* perm_out) {
+scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                           int start, void* workspace, size_t workspace_bytes, int32_t* perm_out,
+                           double* dist_out) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!fields || !perm_out || !workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
   if (n_ops < 1 || n_ops > 65536) return fail(ctx, SCSF_ERR_INVALID_ARG, "n_ops out of [1, 65536]");
@@ -509,8 +510,15 @@ scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p,
   if (workspace_bytes < sort_workspace_bytes(n_ops, p0))
     return fail(ctx, SCSF_ERR_NO_MEMORY, "sort workspace too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
-  SCSF_CUDA(ctx, launch_sort(fields, n_ops, p, p0, start, workspace, perm_out, ctx->stream));
+  SCSF_CUDA(ctx, launch_sort(fields, n_ops, p, p0, start, workspace, perm_out, ctx->stream,
+                             dist_out));
   return SCSF_OK;
+}
+
+scsf_status scsf_sort(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0, int start,
+                      void* workspace, size_t workspace_bytes, int32_t* perm_out) {
+  return scsf_sort_dist(ctx, fields, n_ops, p, p0, start, workspace, workspace_bytes, perm_out,
+                        nullptr);
 }
 
 size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {

@@ -135,7 +135,9 @@ cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64
 
 // ---- sort (sort.cu) ------------------------------------------------------
 size_t sort_workspace_bytes(int64_t n_ops, int p0);
+// dist (optional, n_ops): squared feature distance from each sorted problem to its
+// predecessor (0 for the first).
 cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int start,
-                        void* workspace, int32_t* perm, cudaStream_t st);
+                        void* workspace, int32_t* perm, cudaStream_t st, double* dist = nullptr);
 
 }  // namespace scsf

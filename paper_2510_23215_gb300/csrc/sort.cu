@@ -79,7 +79,8 @@ __device__ __forceinline__ bool lex_less(double da, int ja, double db, int jb) {
 
 __global__ void __launch_bounds__(kChainThreads)
 greedy_chain_kernel(const double* __restrict__ feats, int n_ops, int flen, int start,
-                    unsigned char* __restrict__ visited, int32_t* __restrict__ perm) {
+                    unsigned char* __restrict__ visited, int32_t* __restrict__ perm,
+                    double* __restrict__ dist) {
   extern __shared__ double tail[];  // [flen]
   __shared__ double red_d[32];
   __shared__ int red_j[32];
@@ -89,6 +90,7 @@ greedy_chain_kernel(const double* __restrict__ feats, int n_ops, int flen, int s
   if (t == 0) {
     s_tail = start;
     perm[0] = start;
+    if (dist) dist[0] = 0.0;
   }
   __syncthreads();
   if (t == 0) visited[start] = 1;
@@ -134,6 +136,7 @@ greedy_chain_kernel(const double* __restrict__ feats, int n_ops, int flen, int s
           jb = red_j[w];
         }
       perm[step] = jb;
+      if (dist) dist[step] = b;
       visited[jb] = 1;
       s_tail = jb;
     }
@@ -148,7 +151,7 @@ size_t sort_workspace_bytes(int64_t n_ops, int p0) {
 }
 
 cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int start,
-                        void* workspace, int32_t* perm, cudaStream_t st) {
+                        void* workspace, int32_t* perm, cudaStream_t st, double* dist) {
   double* feats = static_cast<double*>(workspace);
   unsigned char* visited = reinterpret_cast<unsigned char*>(
       static_cast<char*>(workspace) + align256((size_t)n_ops * p0 * p0 * 2 * sizeof(double)));
@@ -160,7 +163,7 @@ cudaError_t launch_sort(const double* fields, int64_t n_ops, int p, int p0, int 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int flen = 2 * p0 * p0;
   greedy_chain_kernel<<<1, kChainThreads, flen * sizeof(double), st>>>(feats, (int)n_ops, flen,
-                                                                       start, visited, perm);
+                                                                       start, visited, perm, dist);
   note_launch();
   return cudaGetLastError();
 }

@@ -20,7 +20,7 @@ import time
 import numpy as np
 import torch
 
-from . import Chain, Operator, Params, Proposal, solve_batched
+from . import Chain, Operator, Params, Proposal, solve_batched, sort
 
 
 def label(ops, n: int, params: Params, device, chunk: int = 256, chain_len: int = 16,
@@ -71,6 +71,31 @@ def head_iterations(prop: Proposal, ops, fields, n: int, params: Params, device)
         out["resid_random"] = max(out["resid_random"], float(r1.max()))
         out["resid_proposal"] = max(out["resid_proposal"], float(r2.max()))
     return out
+
+
+def solve_chain_with_proposal(ops, prop: Proposal, params: Params, device, p0: int = 8,
+                              quantile: float = 0.9):
+    """Sort the operators (Alg. 2) and solve them in that order as one warm-started chain,
+    seeding the head and every far step -- a step whose squared feature distance to its
+    predecessor is above the given quantile of the chain's step distances -- from the
+    proposal block instead of the predecessor's. Returns (perm, seeded positions,
+    [(evals, resid, stats)] in chain order)."""
+    n = ops[0].n
+    fields = torch.as_tensor(np.stack([o.P for o in ops]), device=device)
+    perm, dist = sort(fields, p0=p0, return_distances=True)
+    perm = perm.cpu().tolist()
+    dist = dist.cpu().numpy()
+    thr = float(np.quantile(dist[1:], quantile)) if len(ops) > 1 else float("inf")
+    ch = Chain(params, n, device=device)
+    seeded, out = [], []
+    for pos, j in enumerate(perm):
+        if pos == 0 or dist[pos] > thr:
+            block, ritz = prop.head_block(fields[j], n, params.kb, seed=j)
+            ch.seed(block, ritz)
+            seeded.append(pos)
+        ev, rs, _, st = ch.step(Operator.from_workload(ops[j], device), want_vectors=False)
+        out.append((ev, rs, st))
+    return perm, seeded, out
 
 
 def run(n: int, n_train: int, n_test: int, steps: int, degree: int, lr: float, seed: int,

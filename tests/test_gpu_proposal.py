@@ -156,3 +156,25 @@ def test_trained_proposal_gain_on_heldout_heads():
     assert bounds < 0.02
     assert r["resid_random"] <= 1e-8 and r["resid_proposal"] <= 1e-8
     assert r["mean_iters_proposal"] <= r["mean_iters_random"] + 1.0
+
+
+def test_chain_seeds_head_and_far_steps_from_the_proposal():
+    """The far-step rule: the head and the steps whose sort distance is above the 90th
+    percentile start from the proposal block; every problem still meets the tolerance."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    from paper_2510_23215_gb300 import proposal_train
+    ops = si.div_a_grad_chain(64, 21, seed=9)
+    prop = scsf.Proposal(seed=2, device=dev)
+    params = scsf.Params(k=64, degree=20, tol=1e-8, max_iter=200)
+    perm, seeded, out = proposal_train.solve_chain_with_proposal(ops, prop, params, dev)
+    assert sorted(perm) == list(range(21))
+    # 20 step distances, 90th percentile: the two largest are above it
+    assert seeded[0] == 0 and len(seeded) == 3
+    _, dist = scsf.sort(torch.as_tensor(np.stack([o.P for o in ops]), device=dev), p0=8,
+                        return_distances=True)
+    d = host(dist)
+    assert d[0] == 0.0
+    assert set(seeded[1:]) == set(int(i) + 1 for i in np.argsort(d[1:])[-2:])
+    for ev, rs, st in out:
+        assert float(rs.max()) <= 1e-8 and st["converged"]

@@ -71,3 +71,18 @@ def test_sort_rejects_bad_arguments():
         scsf.sort(f, p0=2, start=4)
     with pytest.raises(ValueError):
         scsf.sort(f.cpu().cuda().transpose(1, 2), p0=2)
+
+
+def test_sort_distances_match_oracle_features():
+    """scsf_sort_dist: the permutation of scsf_sort and, per step, the squared distance of
+    the oracle's truncated-DFT features between consecutive problems."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(32, 40, seed=3)
+    F = np.stack([o.P for o in ops])
+    perm, dist = scsf.sort(torch.as_tensor(F, device=dev), p0=8, return_distances=True)
+    perm, dist = host(perm), host(dist)
+    assert np.array_equal(perm, host(scsf.sort(torch.as_tensor(F, device=dev), p0=8)))
+    feats = osort.features(F, 8)
+    ref = [0.0] + [osort.squared_distance(feats[perm[i - 1]], feats[perm[i]]) for i in range(1, 40)]
+    np.testing.assert_allclose(dist, ref, rtol=1e-12, atol=0)
