@@ -327,9 +327,15 @@ __global__ void gemm_tn_f32_reduce_kernel(int m, int n, int nchunk, bool symmetr
     si = j;
     sj = i;
   }
-  double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += (double)partials[(size_t)c * m * n + (size_t)si * n + sj];
-  C[(size_t)i * ldc + j] = s;
+  // compensated FP32 sum of the chunk partials (the FP64 pipe is 1/60 of FP32 on GB300)
+  float s = 0.f, comp = 0.f;
+  for (int c = 0; c < nchunk; ++c) {
+    const float y = partials[(size_t)c * m * n + (size_t)si * n + sj] - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  C[(size_t)i * ldc + j] = (double)s;
 }
 
 struct Plan32 {
