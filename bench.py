@@ -65,6 +65,18 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_time_pairs(ms: float, pairs: float, world_size: int, device):
+    """Whole-job figures over the ranks: the slowest rank's time and the sum of the pairs."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    if world_size > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(p[0])
+
+
 def _workload_ops(rank: int):
     w = WORKLOAD
     return si.div_a_grad_chain(w["n"], w["n_ops"], seed=w["seed"] + 1000 * rank)
@@ -222,12 +234,7 @@ def run_ours(args):
                 "clocks": clk.summary() if clk else None}
 
     def reduce_max_sum(ms, pairs):
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        p = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        return float(t[0]), float(p[0])
+        return reduce_time_pairs(ms, pairs, ws, dev)
 
     main = timed(forms[chosen], args.steps, args.warmup, sample_clocks=True, chunks=args.chunks)
     total_ms, pairs = reduce_max_sum(main["ms"], main["pairs"])
