@@ -688,7 +688,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       }
       SCSF_CUDA(ctx, mark(2));
       SCSF_CUDA(ctx, launch_cheb_step_f32(A32, Y, kb, nullptr, 0, F2, kb, kb, 1.f, 0.f, 0.f, st));
-      SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, F2, kb, b.H, kb, false, b.partials32, st));
+      // Q^T (A Q) is symmetric (A is): only its upper tiles are formed, then mirrored
+      SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, F2, kb, b.H, kb, true, b.partials32, st));
       SCSF_CUDA(ctx, mark(3));
       SCSF_CUDA(ctx, launch_small_eigh_f32(kb, b.H, kb, b.theta, b.Z, kb, b.eigh_scratch, st));
       SCSF_CUDA(ctx, mark(4));
@@ -802,7 +803,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       SCSF_CUDA(ctx, mark(2));
       // Rayleigh quotient G = Q^T A Q on the active columns
       SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, true, b.gemm_partials, st));
       SCSF_CUDA(ctx, mark(3));
       // reduced eigenproblem and rotation back
       SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
@@ -832,7 +833,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       flops += 1.5 * N * ka * ka;
       SCSF_CUDA(ctx, mark(2));
       SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, false, b.gemm_partials, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, true, b.gemm_partials, st));
       // H = R2^{-T} (H1 R2^{-1}) with T = H1 R2^{-1} in b.G
       SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.H, ka, b.Rinv, ka, 0.0, b.G, ka, true, st));
       SCSF_CUDA(ctx, launch_gemm_tn(ka, ka, ka, b.Rinv, ka, b.G, ka, b.H, ka, false, b.gemm_partials,

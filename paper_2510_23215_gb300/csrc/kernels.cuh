@@ -46,7 +46,8 @@ cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, in
 
 // ---- FP64 block BLAS (blas64.cu) ----------------------------------------
 // C[m x n] = A^T B over `rows` rows, A: rows x m (lda), B: rows x n (ldb).
-// symmetric: A == B and only the upper tiles are computed, then mirrored.
+// symmetric: C is known to be symmetric (A == B, or A^T B with B = S A for a symmetric S):
+// only the upper tiles are computed, then mirrored.
 size_t gemm_tn_partials(int rows, int m, int n, bool symmetric);
 cudaError_t launch_gemm_tn(int rows, int m, int n, const double* A, int lda, const double* B,
                            int ldb, double* C, int ldc, bool symmetric, double* partials,
