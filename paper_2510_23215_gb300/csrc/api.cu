@@ -204,6 +204,25 @@ cudaError_t run_filter(const Stencil& A, const double* Y0, int ld0, int ncols, i
 }
 
 // The same recurrence on FP32 blocks (scalars computed in FP64, applied in FP32).
+// The m step scalars {s1, s2, s3} of the scaled recurrence (Alg. 1), as FP32, into the host
+// staging array h and then into the device table dev.
+cudaError_t upload_filter_coefs(int m, double lam, double c, double e, float* h, float* dev,
+                                cudaStream_t st) {
+  const double sigma1 = e / (lam - c);
+  double sigma = sigma1;
+  h[0] = (float)(sigma1 / e);
+  h[1] = (float)(-sigma1 * c / e);
+  h[2] = 0.f;
+  for (int i = 1; i < m; ++i) {
+    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
+    h[3 * i] = (float)(2.0 * sigma_next / e);
+    h[3 * i + 1] = (float)(-2.0 * sigma_next * c / e);
+    h[3 * i + 2] = (float)(-sigma_next * sigma);
+    sigma = sigma_next;
+  }
+  return cudaMemcpyAsync(dev, h, 3 * (size_t)m * sizeof(float), cudaMemcpyHostToDevice, st);
+}
+
 cudaError_t run_filter_f32(const Stencil32& A, const float* Y0, int ld0, int ncols, int degree,
                            double lam, double c, double e, float* const bufs[3], int ld,
                            int* which, cudaStream_t st) {
@@ -388,6 +407,20 @@ cudaError_t run_filter_f32_graph(scsf_chain* ch, const Stencil32& A, int m, doub
                                  double e, int* which, cudaStream_t st) {
   ChainBufs& b = ch->b;
   const int kb = ch->kb;
+  // preferred: the whole filter in one launch, resident in cluster shared memory
+  if (m <= kMaxGraphSteps) {
+    float* h = reinterpret_cast<float*>(ch->ctx->pinned + kPinnedCoefOffset);
+    cudaError_t err = upload_filter_coefs(m, lam, c, e, h, b.coef32, st);
+    if (err != cudaSuccess) return err;
+    const int w = (m - 1) % 3;
+    err = launch_cheb_filter_f32_resident(A, b.V32, kb, b.B32[w], kb, kb, m, b.coef32, st);
+    if (err == cudaSuccess) {
+      *which = w;
+      return cudaSuccess;
+    }
+    if (err != cudaErrorNotSupported) return err;
+    cudaGetLastError();
+  }
   // the legacy default stream cannot be captured: plain launches there
   if (m > kMaxGraphSteps || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
     return run_filter_f32(A, b.V32, kb, kb, m, lam, c, e, b.B32, kb, which, st);
@@ -418,21 +451,7 @@ cudaError_t run_filter_f32_graph(scsf_chain* ch, const Stencil32& A, int m, doub
     ch->g32_threads = threads;
   }
   float* h = reinterpret_cast<float*>(ch->ctx->pinned + kPinnedCoefOffset);
-  const double sigma1 = e / (lam - c);
-  double sigma = sigma1;
-  h[0] = (float)(sigma1 / e);
-  h[1] = (float)(-sigma1 * c / e);
-  h[2] = 0.f;
-  for (int i = 1; i < m; ++i) {
-    const double sigma_next = 1.0 / (2.0 / sigma1 - sigma);
-    h[3 * i] = (float)(2.0 * sigma_next / e);
-    h[3 * i + 1] = (float)(-2.0 * sigma_next * c / e);
-    h[3 * i + 2] = (float)(-sigma_next * sigma);
-    sigma = sigma_next;
-  }
-  if ((err = cudaMemcpyAsync(b.coef32, h, 3 * (size_t)m * sizeof(float), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess)
-    return err;
+  if ((err = upload_filter_coefs(m, lam, c, e, h, b.coef32, st)) != cudaSuccess) return err;
   if ((err = cudaGraphLaunch(ch->g32, st)) != cudaSuccess) return err;
   for (int i = 0; i < m; ++i) note_launch();
   *which = (m - 1) % 3;
@@ -1067,6 +1086,7 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
   float* wn32 = cv.take<float>(N);
   double* part = cv.take<double>(2 * (size_t)assemble_blocks(n));
   double* bnd = cv.take<double>(2);
+  float* coefd = cv.take<float>(3 * (size_t)degree);
   if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -1075,6 +1095,15 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
   SCSF_CUDA(ctx, launch_to_f32(we, we32, N, st));
   SCSF_CUDA(ctx, launch_to_f32(wn, wn32, N, st));
   const Stencil32 A{d32, we32, wn32, n};
+  // the cluster-resident filter where the grid fits, else one launch per step
+  {
+    std::vector<float> hc(3 * (size_t)degree);
+    SCSF_CUDA(ctx, upload_filter_coefs(degree, lambda, c, e, hc.data(), coefd, st));
+    const cudaError_t er = launch_cheb_filter_f32_resident(A, X, ldx, Y, ncols, ncols, degree, coefd, st);
+    if (er == cudaSuccess) return SCSF_OK;
+    if (er != cudaErrorNotSupported) SCSF_CUDA(ctx, er);
+    cudaGetLastError();
+  }
   // Y_i goes to rot[(i-1) % 3]; copy at the end if Y_m did not land in Y
   float* rot[3] = {s0, s1, Y};
   int which = 0;

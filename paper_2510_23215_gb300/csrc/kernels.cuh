@@ -93,6 +93,13 @@ cudaError_t launch_block_f64_to_f32(int rows, int cols, const double* in, int ld
 cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, const float* prev,
                                  int ldp, float* out, int ldo, int ncols, float s1, float s2,
                                  float s3, cudaStream_t st, int threads = 256);
+// The whole m-step FP32 filter in one launch, each 4-column group held in the shared memory
+// of a thread-block cluster (coef: device [m][3] step scalars; Y_m written to out).
+// Returns cudaErrorNotSupported when the grid is too large for the cluster's shared memory
+// or the widths are not multiples of 4 (the caller then uses per-step launches).
+cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0, int ld0, float* out,
+                                            int ldo, int ncols, int m, const float* coef,
+                                            cudaStream_t st);
 // The step with {s1, s2, s3} read from device memory at coef (for captured graphs; the
 // caller counts the launch). prev is read whenever non-null.
 cudaError_t launch_cheb_step_f32_tab(const Stencil32& A, const float* cur, int ldc,

@@ -9,6 +9,8 @@
 // stay FP64 so the shared Cholesky and eigensolve kernels serve both phases.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace scsf {
@@ -83,6 +85,102 @@ cheb_step_f32_tab_kernel(Stencil32 A, const float* __restrict__ cur, int ldc,
                          const float* __restrict__ prev, int ldp, float* __restrict__ out, int ldo,
                          int quads, const float* __restrict__ coef) {
   cheb_step_f32_body(A, cur, ldc, prev, ldp, out, ldo, quads, coef[0], coef[1], coef[2]);
+}
+
+// ---- cluster-resident FP32 filter ----------------------------------------------
+// The whole m-step recurrence for one group of 4 columns runs in one thread-block cluster:
+// the kClu CTAs of the cluster split the n grid rows into bands, and each keeps its band of
+// both recurrence levels (float4 per node, plus one halo row above and below) and its
+// stencil coefficients in shared memory for all m steps. After every step the cluster
+// synchronises and each CTA copies its neighbours' boundary rows of the new level into its
+// halo rows through distributed shared memory. Global memory is touched only to load Y_0
+// and the coefficients and to store Y_m; per step the traffic is the halo exchange.
+namespace cg = cooperative_groups;
+
+template <int kClu>
+__device__ __forceinline__ int band_begin(int rank, int n) { return rank * n / kClu; }
+
+template <int kClu>
+__global__ void __launch_bounds__(1024)
+cheb_filter_f32_cluster_kernel(Stencil32 A, const float* __restrict__ Y0, int ld0,
+                               float* __restrict__ out, int ldo, int m,
+                               const float* __restrict__ coef) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = A.n;
+  const int r0 = band_begin<kClu>(rank, n), r1 = band_begin<kClu>(rank + 1, n);
+  const int rows = r1 - r0;
+  const int hrm = (n + kClu - 1) / kClu + 2;  // local rows incl. halos (same on every rank)
+  const int cg4 = 4 * blockIdx.y;             // first column of this cluster's group
+  const int t = threadIdx.x, nt = blockDim.x;
+  extern __shared__ float4 sm4[];
+  float4* L0 = sm4;
+  float4* L1 = sm4 + (size_t)hrm * n;
+  float* cd = reinterpret_cast<float*>(sm4 + 2 * (size_t)hrm * n);  // d, rows x n
+  float* cwe = cd + (size_t)(hrm - 2) * n;  // we of global rows r0-1 .. r1-1, (rows+1) x n
+  float* cwn = cwe + (size_t)(hrm - 1) * n; // wn, rows x n
+  for (int e = t; e < rows * n; e += nt) {
+    const int I = r0 * n + e;
+    cd[e] = A.d[I];
+    cwn[e] = A.wn[I];
+  }
+  for (int e = t; e < (rows + 1) * n; e += nt) {
+    const int gi = r0 - 1 + e / n;
+    cwe[e] = (gi >= 0) ? A.we[gi * n + (e - (e / n) * n)] : 0.f;
+  }
+  // Y_0: own rows and both halo rows (zero outside the grid); local row lr <-> global r0-1+lr
+  for (int e = t; e < (rows + 2) * n; e += nt) {
+    const int lr = e / n, j = e - lr * n, gi = r0 - 1 + lr;
+    L0[e] = (gi >= 0 && gi < n) ? ld4(Y0 + (size_t)(gi * n + j) * ld0 + cg4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  float4* C = L0;
+  float4* P = L1;
+  const int rows_above = (rank > 0) ? r0 - band_begin<kClu>(rank - 1, n) : 0;
+  for (int s = 0; s < m; ++s) {
+    const float s1 = coef[3 * s], s2 = coef[3 * s + 1], s3 = coef[3 * s + 2];
+    for (int e = t; e < rows * n; e += nt) {
+      const int q = e / n, j = e - q * n, lr = q + 1, gi = r0 + q;
+      const float4* row = C + (size_t)lr * n + j;
+      const float4 y = row[0];
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gi < n - 1) acc = fma4(cwe[(size_t)(q + 1) * n + j], row[n], acc);
+      if (gi > 0) acc = fma4(cwe[(size_t)q * n + j], row[-n], acc);
+      if (j < n - 1) acc = fma4(cwn[e], row[1], acc);
+      if (j > 0) acc = fma4(cwn[e - 1], row[-1], acc);
+      const float diag = fmaf(s1, cd[e], s2);
+      float4 r = make_float4(fmaf(-s1, acc.x, diag * y.x), fmaf(-s1, acc.y, diag * y.y),
+                             fmaf(-s1, acc.z, diag * y.z), fmaf(-s1, acc.w, diag * y.w));
+      if (s > 0) r = fma4(s3, P[(size_t)lr * n + j], r);
+      P[(size_t)lr * n + j] = r;
+    }
+    cluster.sync();  // every band of the new level is final
+    if (rank > 0) {
+      const float4* up = cluster.map_shared_rank(P, rank - 1);
+      for (int j = t; j < n; j += nt) P[j] = up[(size_t)rows_above * n + j];
+    }
+    if (rank < kClu - 1) {
+      const float4* dn = cluster.map_shared_rank(P, rank + 1);
+      for (int j = t; j < n; j += nt) P[(size_t)(rows + 1) * n + j] = dn[(size_t)n + j];
+    }
+    __syncthreads();
+    float4* tmp = C;
+    C = P;
+    P = tmp;
+  }
+  for (int e = t; e < rows * n; e += nt) {
+    const int q = e / n, j = e - q * n;
+    st4(out + (size_t)((r0 + q) * n + j) * ldo + cg4, C[(size_t)(q + 1) * n + j]);
+  }
+  // no CTA may leave while a neighbour can still read its shared memory
+  cluster.sync();
+}
+
+template <int kClu>
+size_t cluster_filter_smem(int n) {
+  const size_t hrm = (size_t)(n + kClu - 1) / kClu + 2;
+  return 2 * hrm * n * sizeof(float4) + (3 * (hrm - 2) + 1) * (size_t)n * sizeof(float);
 }
 
 // ---- defect-corrected filter ------------------------------------------------
@@ -538,6 +636,51 @@ cudaError_t launch_dc_combine(int rows, int ncols, const double* X, int ldx, con
   const long long tot = (long long)rows * ncols;
   const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
   dc_combine_kernel<<<nb, 256, 0, st>>>(rows, ncols, X, ldx, ym, Z, ldz, Y, ldy);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0, int ld0, float* out,
+                                            int ldo, int ncols, int m, const float* coef,
+                                            cudaStream_t st) {
+  if (ncols % 4 || ld0 % 4 || ldo % 4 || m < 1) return cudaErrorNotSupported;
+  const int n = A.n;
+  constexpr size_t kMaxSmem = 227 * 1024;
+  int clu = 0;
+  size_t smem = 0;
+  if (n >= 8 && cluster_filter_smem<4>(n) <= kMaxSmem) {
+    clu = 4;
+    smem = cluster_filter_smem<4>(n);
+  } else if (n >= 16 && cluster_filter_smem<8>(n) <= kMaxSmem) {
+    clu = 8;
+    smem = cluster_filter_smem<8>(n);
+  } else {
+    return cudaErrorNotSupported;
+  }
+  const void* fn = (clu == 4) ? (const void*)cheb_filter_f32_cluster_kernel<4>
+                              : (const void*)cheb_filter_f32_cluster_kernel<8>;
+  cudaError_t e = ensure_dynamic_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clu, ncols / 4, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = clu;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (clu == 4)
+    e = cudaLaunchKernelEx(&cfg, cheb_filter_f32_cluster_kernel<4>, A, Y0, ld0, out, ldo, m, coef);
+  else
+    e = cudaLaunchKernelEx(&cfg, cheb_filter_f32_cluster_kernel<8>, A, Y0, ld0, out, ldo, m, coef);
+  if (e != cudaSuccess) {  // a cluster shape the device cannot place: per-step launches instead
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
   note_launch();
   return cudaGetLastError();
 }
