@@ -194,7 +194,7 @@ def run_ours(args):
         # App. D.6: contiguous chunks of the sorted sequence, one chain each, all in flight
         bounds = np.linspace(0, len(dops), chunks + 1).round().astype(int)
         chains = [(dops[a:b], params) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
-        res = scsf.solve_batched(chains, concurrency=len(chains), ctx=ctx)
+        res = scsf.solve_batched(chains, concurrency=args.concurrency or len(chains), ctx=ctx)
         ev = torch.cat([r[0] for r in res])
         rs = torch.cat([r[1] for r in res])
         stats = [s for r in res for s in r[3]]
@@ -344,6 +344,7 @@ def run_ours(args):
                        f"; sorted sequence cut into {args.chunks} chains solved concurrently"
                        if args.chunks > 1 else "; one sequential chain"),
                    "chunks": args.chunks,
+                   "concurrency": args.concurrency or args.chunks,
                    "degrees": ({"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}
                                if chosen == "mixed" else {"fp64": w["degree"]}),
                    "switch_tol": args.switch_tol if chosen == "mixed" else None,
@@ -442,6 +443,9 @@ def main():
                     help="mixed form: wanted residual at which the FP32 phase hands over (0: off)")
     ap.add_argument("--chunks", type=int, default=8,
                     help="contiguous chunks of the sorted sequence solved as concurrent chains")
+    ap.add_argument("--concurrency", type=int, default=0,
+                    help="chains in flight at once (0: all chunks; more chunks than slots "
+                         "balance uneven chains)")
     ap.add_argument("--n-ops", type=int, default=None,
                     help="problems per batch (default 200; smaller only for profiler captures)")
     args = ap.parse_args()

@@ -254,7 +254,7 @@ template <typename Cv>
 void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3], double** d,
                      double** we, double** wn, float** d32, float** we32, float** wn32,
                      double** part, double** bnd, double** rpart, double** res2, float** ytab,
-                     double** ym) {
+                     double** ym, float** coef) {
   const size_t N = (size_t)n * n;
   *R = cv.template take<float>(N * ncols);
   for (int i = 0; i < 3; ++i) z[i] = cv.template take<float>(N * ncols);
@@ -270,6 +270,7 @@ void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3
   *res2 = cv.template take<double>(2 * (size_t)ncols);
   *ytab = cv.template take<float>((size_t)std::max(degree, 1) * ncols);
   *ym = cv.template take<double>(2 * (size_t)ncols);
+  *coef = cv.template take<float>(3 * (size_t)std::max(degree, 1));
 }
 
 // Defect-corrected filter of the FP64 phase (mixed form): X (FP64, ncols active
@@ -289,7 +290,8 @@ struct DcDeflate {
 cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const float* R, int ldr,
                           const double* theta, int ncols, int degree, double lam, double c,
                           double e, float* const zb[3], int ldz, float* ytab, double* ystate,
-                          double* Y, int ldy, cudaStream_t st, const DcDeflate* defl = nullptr) {
+                          double* Y, int ldy, cudaStream_t st, const DcDeflate* defl = nullptr,
+                          float* coef_dev = nullptr, float* coef_host = nullptr) {
   // coefficients of step i (Y_i -> Y_{i+1}): s1 A Y_i + s2 Y_i + s3 Y_{i-1}
   std::vector<double> s1(degree), s2(degree), s3(degree);
   const double sigma1 = e / (lam - c);
@@ -316,12 +318,28 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
     }
     if ((err = launch_dc_ytab(theta, ncols, P, ytab, ystate, st)) != cudaSuccess) return err;
   }
+  int cur = 0;
+  bool resident = false;
+  if (coef_dev && coef_host) {  // the whole recurrence in one cluster-resident launch
+    for (int i = 0; i < degree; ++i) {
+      coef_host[3 * i] = (float)s1[i];
+      coef_host[3 * i + 1] = (float)s2[i];
+      coef_host[3 * i + 2] = (float)s3[i];
+    }
+    err = cudaMemcpyAsync(coef_dev, coef_host, 3 * (size_t)degree * sizeof(float),
+                          cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return err;
+    err = launch_dc_filter_resident(A, R, ldr, ncols, ytab, coef_dev, degree, zb[0], ldz, st);
+    if (err == cudaSuccess) resident = true;
+    else if (err != cudaErrorNotSupported) return err;
+    else cudaGetLastError();
+  }
+  if (!resident) {
   // Z_1 = s1 R diag(y_0), y_0 = 1; Z_0 = 0
   err = launch_cheb_step_dc(A, nullptr, nullptr, ldz, R, ldr, ytab, zb[0], ncols, (float)s1[0],
                             0.f, 0.f, st);
   if (err != cudaSuccess) return err;
   const float* prev = nullptr;
-  int cur = 0;
   for (int i = 1; i < degree; ++i) {
     const int nxt = i % 3;
     err = launch_cheb_step_dc(A, zb[cur], prev, ldz, R, ldr, ytab + (size_t)i * ncols, zb[nxt],
@@ -329,6 +347,7 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
     if (err != cudaSuccess) return err;
     prev = zb[cur];
     cur = nxt;
+  }
   }
   if (defl && defl->nl > 0) {
     const int N = A.n * A.n;
@@ -785,7 +804,9 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       defl.C = b.C;
       defl.partials = b.partials32;
       SCSF_CUDA(ctx, run_filter_dc(A32, b.V + nl, kb, b.V32 + nl, kb, dc_theta, ka, m, lam, c, e,
-                                   b.B32, kb, b.ytab, b.ym, bufs[0], kb, st, &defl));
+                                   b.B32, kb, b.ytab, b.ym, bufs[0], kb, st, &defl,
+                                   (m <= kMaxGraphSteps) ? b.coef32 : nullptr,
+                                   reinterpret_cast<float*>(ctx->pinned + kPinnedCoefOffset)));
       dc_steps += m;
       dc_elems += (double)m * N * ka;
     } else {
@@ -1117,10 +1138,10 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
 size_t scsf_cheb_filter_dc_scratch(int n, int ncols, int degree) {
   if (n < 1 || ncols < 1 || ncols > kMaxBlockWidth || degree < 1) return 0;
   SizeCarve sc;
-  float *R, *z[3], *d32, *we32, *wn32, *ytab;
+  float *R, *z[3], *d32, *we32, *wn32, *ytab, *coef;
   double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
   carve_filter_dc(sc, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
-                  &rpart, &res2, &ytab, &ym);
+                  &rpart, &res2, &ytab, &ym, &coef);
   return sc.used + 256;
 }
 
@@ -1136,10 +1157,10 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 160, ld >= ncols, valid filter parameters");
   const int n = op->n;
   Carve cv(scratch, scratch_bytes);
-  float *R, *z[3], *d32, *we32, *wn32, *ytab;
+  float *R, *z[3], *d32, *we32, *wn32, *ytab, *coef;
   double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
   carve_filter_dc(cv, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
-                  &rpart, &res2, &ytab, &ym);
+                  &rpart, &res2, &ytab, &ym, &coef);
   if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -1151,8 +1172,10 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   const Stencil A{d, we, wn, n};
   const Stencil32 A32{d32, we32, wn32, n};
   SCSF_CUDA(ctx, launch_residual_norms(A, X, ldx, ncols, theta, rpart, res2, st, R, ncols));
+  std::vector<float> hcoef(3 * (size_t)degree);
   SCSF_CUDA(ctx, run_filter_dc(A32, X, ldx, R, ncols, theta, ncols, degree, lambda, c, e, z, ncols,
-                               ytab, ym, Y, ldy, st));
+                               ytab, ym, Y, ldy, st, nullptr, coef, hcoef.data()));
+  SCSF_CUDA(ctx, cudaStreamSynchronize(st));  // hcoef is the source of an asynchronous copy
   return SCSF_OK;
 }
 

@@ -100,6 +100,12 @@ cudaError_t launch_cheb_step_f32(const Stencil32& A, const float* cur, int ldc, 
 cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0, int ld0, float* out,
                                             int ldo, int ncols, int m, const float* coef,
                                             cudaStream_t st);
+// The whole defect-corrected remainder recurrence (Z_m, FP32, into out with ld ldo) in one
+// launch, resident in cluster shared memory like the FP32 filter. coef: device [m][3] step
+// scalars; ytab: device [m][ncols]. cudaErrorNotSupported: use the per-step kernels.
+cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ldr, int ncols,
+                                      const float* ytab, const float* coef, int m, float* out,
+                                      int ldo, cudaStream_t st);
 // The step with {s1, s2, s3} read from device memory at coef (for captured graphs; the
 // caller counts the launch). prev is read whenever non-null.
 cudaError_t launch_cheb_step_f32_tab(const Stencil32& A, const float* cur, int ldc,

@@ -177,6 +177,109 @@ cheb_filter_f32_cluster_kernel(Stencil32 A, const float* __restrict__ Y0, int ld
   cluster.sync();
 }
 
+// The defect-corrected recurrence Z_{i+1} = s1 A Z_i + s2 Z_i + s3 Z_{i-1} + s1 R diag(y_i),
+// Z_0 = 0, resident the same way: per 4-column group, the cluster's bands keep both Z levels,
+// the band of R and the stencil coefficients in shared memory; coef: [m][3] step scalars,
+// ytab: [m][ncols] scalar values y_i. Columns >= ncols of the last group are padding.
+template <int kClu>
+__global__ void __launch_bounds__(1024)
+dc_filter_cluster_kernel(Stencil32 A, const float* __restrict__ R, int ldr, int ncols,
+                         const float* __restrict__ ytab, const float* __restrict__ coef, int m,
+                         float* __restrict__ out, int ldo) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = A.n;
+  const int r0 = band_begin<kClu>(rank, n), r1 = band_begin<kClu>(rank + 1, n);
+  const int rows = r1 - r0;
+  const int hrm = (n + kClu - 1) / kClu + 2;
+  const int c0 = 4 * blockIdx.y;
+  const int t = threadIdx.x, nt = blockDim.x;
+  extern __shared__ float4 sm4[];
+  float4* L0 = sm4;
+  float4* L1 = sm4 + (size_t)hrm * n;
+  float4* Rb = sm4 + 2 * (size_t)hrm * n;                                    // rows x n
+  float* cd = reinterpret_cast<float*>(sm4 + (size_t)(3 * hrm - 2) * n);    // rows x n
+  float* cwe = cd + (size_t)(hrm - 2) * n;                                  // (rows+1) x n
+  float* cwn = cwe + (size_t)(hrm - 1) * n;                                 // rows x n
+  // the float section is padded to whole float4s so that yt stays 16-byte aligned
+  const size_t fl = ((size_t)(3 * (hrm - 2) + 1) * n + 3) & ~(size_t)3;
+  float4* yt = reinterpret_cast<float4*>(cd + fl);                          // m
+  for (int e = t; e < rows * n; e += nt) {
+    const int I = r0 * n + e;
+    cd[e] = A.d[I];
+    cwn[e] = A.wn[I];
+    const float* rr = R + (size_t)I * ldr + c0;
+    Rb[e] = make_float4(rr[0], (c0 + 1 < ncols) ? rr[1] : 0.f, (c0 + 2 < ncols) ? rr[2] : 0.f,
+                        (c0 + 3 < ncols) ? rr[3] : 0.f);
+  }
+  for (int e = t; e < (rows + 1) * n; e += nt) {
+    const int gi = r0 - 1 + e / n;
+    cwe[e] = (gi >= 0) ? A.we[gi * n + (e - (e / n) * n)] : 0.f;
+  }
+  for (int i = t; i < m; i += nt) {
+    const float* y = ytab + (size_t)i * ncols + c0;
+    yt[i] = make_float4(y[0], (c0 + 1 < ncols) ? y[1] : 0.f, (c0 + 2 < ncols) ? y[2] : 0.f,
+                        (c0 + 3 < ncols) ? y[3] : 0.f);
+  }
+  for (int e = t; e < (rows + 2) * n; e += nt) L0[e] = make_float4(0.f, 0.f, 0.f, 0.f);  // Z_0
+  __syncthreads();
+  float4* C = L0;
+  float4* P = L1;
+  const int rows_above = (rank > 0) ? r0 - band_begin<kClu>(rank - 1, n) : 0;
+  for (int s = 0; s < m; ++s) {
+    const float s1 = coef[3 * s], s2 = coef[3 * s + 1], s3 = coef[3 * s + 2];
+    const float4 ys = yt[s];
+    for (int e = t; e < rows * n; e += nt) {
+      const int q = e / n, j = e - q * n, lr = q + 1, gi = r0 + q;
+      const float4* row = C + (size_t)lr * n + j;
+      const float4 z = row[0];
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gi < n - 1) acc = fma4(cwe[(size_t)(q + 1) * n + j], row[n], acc);
+      if (gi > 0) acc = fma4(cwe[(size_t)q * n + j], row[-n], acc);
+      if (j < n - 1) acc = fma4(cwn[e], row[1], acc);
+      if (j > 0) acc = fma4(cwn[e - 1], row[-1], acc);
+      const float diag = fmaf(s1, cd[e], s2);
+      const float4 rv = Rb[e];
+      float4 r = make_float4(fmaf(-s1, acc.x, fmaf(diag, z.x, s1 * rv.x * ys.x)),
+                             fmaf(-s1, acc.y, fmaf(diag, z.y, s1 * rv.y * ys.y)),
+                             fmaf(-s1, acc.z, fmaf(diag, z.z, s1 * rv.z * ys.z)),
+                             fmaf(-s1, acc.w, fmaf(diag, z.w, s1 * rv.w * ys.w)));
+      if (s > 0) r = fma4(s3, P[(size_t)lr * n + j], r);
+      P[(size_t)lr * n + j] = r;
+    }
+    cluster.sync();
+    if (rank > 0) {
+      const float4* up = cluster.map_shared_rank(P, rank - 1);
+      for (int j = t; j < n; j += nt) P[j] = up[(size_t)rows_above * n + j];
+    }
+    if (rank < kClu - 1) {
+      const float4* dn = cluster.map_shared_rank(P, rank + 1);
+      for (int j = t; j < n; j += nt) P[(size_t)(rows + 1) * n + j] = dn[(size_t)n + j];
+    }
+    __syncthreads();
+    float4* tmp = C;
+    C = P;
+    P = tmp;
+  }
+  for (int e = t; e < rows * n; e += nt) {
+    const int q = e / n, j = e - q * n;
+    const float4 v = C[(size_t)(q + 1) * n + j];
+    float* o = out + (size_t)((r0 + q) * n + j) * ldo + c0;
+    o[0] = v.x;
+    if (c0 + 1 < ncols) o[1] = v.y;
+    if (c0 + 2 < ncols) o[2] = v.z;
+    if (c0 + 3 < ncols) o[3] = v.w;
+  }
+  cluster.sync();
+}
+
+template <int kClu>
+size_t cluster_dc_smem(int n, int m) {
+  const size_t hrm = (size_t)(n + kClu - 1) / kClu + 2;
+  const size_t fl = ((3 * (hrm - 2) + 1) * (size_t)n + 3) & ~(size_t)3;
+  return (3 * hrm - 2) * n * sizeof(float4) + fl * sizeof(float) + (size_t)m * sizeof(float4);
+}
+
 template <int kClu>
 size_t cluster_filter_smem(int n) {
   const size_t hrm = (size_t)(n + kClu - 1) / kClu + 2;
@@ -678,6 +781,51 @@ cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0,
   else
     e = cudaLaunchKernelEx(&cfg, cheb_filter_f32_cluster_kernel<8>, A, Y0, ld0, out, ldo, m, coef);
   if (e != cudaSuccess) {  // a cluster shape the device cannot place: per-step launches instead
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ldr, int ncols,
+                                      const float* ytab, const float* coef, int m, float* out,
+                                      int ldo, cudaStream_t st) {
+  if (ncols < 1 || m < 1) return cudaErrorNotSupported;
+  const int n = A.n;
+  constexpr size_t kMaxSmem = 227 * 1024;
+  int clu = 0;
+  size_t smem = 0;
+  if (n >= 8 && cluster_dc_smem<4>(n, m) <= kMaxSmem) {
+    clu = 4;
+    smem = cluster_dc_smem<4>(n, m);
+  } else if (n >= 16 && cluster_dc_smem<8>(n, m) <= kMaxSmem) {
+    clu = 8;
+    smem = cluster_dc_smem<8>(n, m);
+  } else {
+    return cudaErrorNotSupported;
+  }
+  const void* fn = (clu == 4) ? (const void*)dc_filter_cluster_kernel<4>
+                              : (const void*)dc_filter_cluster_kernel<8>;
+  cudaError_t e = ensure_dynamic_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clu, (ncols + 3) / 4, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = clu;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (clu == 4)
+    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<4>, A, R, ldr, ncols, ytab, coef, m, out, ldo);
+  else
+    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<8>, A, R, ldr, ncols, ytab, coef, m, out, ldo);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return cudaErrorNotSupported;
   }
