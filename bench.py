@@ -40,7 +40,8 @@ L2_FLUSH_BYTES = 512 << 20
 BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 16.0}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # current kernels (profiles/cheb_step_*.md); kernels not captured at a shape are absent
-TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_step_dc": 15.94e6}
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
 def isolated_filter_rates(degree: int, dev):
@@ -300,29 +301,44 @@ def run_ours(args):
     for name, r in iso.items():
         if name in kernels:
             kernels[name].update(r)
-    # the roofline line reports the filter kernel with the most in-step time; the kernel's
-    # own duration is taken alone on the launching stream (in the step, 8 chains share the
-    # GPU, so a launch's event-to-event time there includes the other chains' work)
-    filt = [k for k in kernels if k != "cheb_step_f64"] or list(kernels)
-    dom = max(filt, key=lambda k: phase_ms[phase_of[k]])
-    kk = kernels[dom]
-    ach = kk["bytes_per_launch"] / (kk["avg_us_alone"] * 1e-6) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}), burst copy",
-                "achieved_in_step": kk["bytes_per_launch"] / (kk["avg_us_in_step"] * 1e-6) / 1e9,
-                "bytes_per_launch": kk["bytes_per_launch"],
-                "note": (f"{BYTES_PER_ELEM[dom]:.0f} B per (node, column) per step, "
-                         f"{kk['elems_per_launch']:.0f} (node, column) pairs per launch; the "
-                         "blocks of one chain fit in L2, so alone the rate is an effective one")}
+    # the roofline line reports the kernel that takes the largest share of the GPU's
+    # resources in the step: the FP64 block products (Gram, triangular solve, Rayleigh-Ritz,
+    # rotation) use every SM at the FP64 ALU rate, while the single-CTA eigensolver and
+    # Cholesky kernels (longer in a serialised launch list) occupy one SM each. It is timed
+    # alone on the launching stream at the step's shape (one chain: N = 16384, k_b = 120).
+    from paper_2510_23215_gb300 import filter_bench as fb
+    rot = fb.measure_rotation(f"{n}x{scsf.block_width(k)}", dev)
+    roofline = {"bound": "alu", "kernel": "gemm_nn_kernel (FP64 block rotation X = Q M)",
+                "achieved": rot["tflops"], "peak": rot["peak_tflops"], "unit": "TFLOP/s",
+                "frac": rot["tflops"] / rot["peak_tflops"], "traffic": None,
+                "flops_per_launch": rot["flops_per_launch"], "avg_us_alone": rot["avg_us"],
+                "peak_source": ("FP64 ALU rate from unit counts and clocks: 152 SMs x 2 FMA/clk x "
+                                "2 flop x 2.07 GHz (MEASURED_PEAKS.json has no FP64 figure)"),
+                "note": "2 N k_b^2 flop per launch, N = 16384, k_b = 120"}
+    # the filters, resident in cluster shared memory: per step they move no DRAM data (ncu:
+    # 8 MB per 100-step launch), so their bound is on-chip; reported per step
+    res = kernels.get("cheb_step_f32", {})
+    roofline_filter = None
+    if res.get("avg_us_alone"):
+        fl = 14.0 * res["elems_per_launch"]  # flop per (node, column) per step
+        roofline_filter = {"bound": "alu", "kernel": "cheb_filter_f32_cluster_kernel (per step)",
+                           "achieved": fl / (res["avg_us_alone"] * 1e-6) / 1e12,
+                           "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": fl / (res["avg_us_alone"] * 1e-6) / 1e12 / FP32_PEAK_TFLOPS,
+                           "traffic": TRAFFIC_PER_LAUNCH.get("cheb_filter_f32_cluster"),
+                           "note": ("14 flop per (node, column) per step; traffic is per launch of "
+                                    "100 steps; limited by shared-memory issue and cluster "
+                                    "barriers, not by DRAM")}
     big = iso.get("cheb_step_f32_256x256_kb480")
     roofline_dram = None
     if big:
         ach_b = big["bytes_per_launch"] / (big["avg_us_alone"] * 1e-6) / 1e9
-        roofline_dram = {"bound": "hbm", "kernel": "cheb_step_f32", "shape": "N = 65536, kb = 480",
+        roofline_dram = {"bound": "hbm", "kernel": "cheb_step_f32_kernel", "shape": "N = 65536, kb = 480",
                          "achieved": ach_b, "peak": hbm_peak, "unit": "GB/s", "frac": ach_b / hbm_peak,
                          "traffic": TRAFFIC_PER_LAUNCH.get("cheb_step_f32_256x256_kb480"),
-                         "note": "3 x 126 MB FP32 blocks: every step streams through DRAM"}
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                         "note": ("per-step kernel (the grid is too large for cluster residency): "
+                                  "3 x 126 MB FP32 blocks, every step streams through DRAM")}
     dom_phase = max(("filter", "filter32", "filter_dc", "orth", "rr", "eig", "rot", "resid"),
                     key=lambda p: phase_ms[p])
     roofline["dominant_phase"] = dom_phase
@@ -361,6 +377,7 @@ def run_ours(args):
         "plain_fp64": other,
         "speedup_vs_plain_fp64": (value / other["value"]) if other else None,
         "roofline": roofline,
+        "roofline_filter": roofline_filter,
         "roofline_filter_dram": roofline_dram,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -327,6 +327,11 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
                                 const double* theta, int ncols, int degree, double lambda,
                                 double c, double e, double* Y, int ldy, void* scratch,
                                 size_t scratch_bytes);
+/* Rotation of a block by a small matrix, Y = X M (Alg. 3, rotation X = Q Z; also the
+ * triangular solve X R^{-1} of Cholesky QR): X FP64 [rows][k] (ldx), M FP64 [k][n] (ldm),
+ * Y FP64 [rows][n] (ldy), all device, Y must not overlap X or M; 1 <= k, n <= 512. */
+scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,
+                              const double* M, int ldm, int n, double* Y, int ldy);
 size_t scsf_small_eigh_scratch(int k);
 scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
                             void* scratch, size_t scratch_bytes);

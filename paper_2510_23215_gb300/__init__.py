@@ -45,7 +45,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_param_count", "scsf_proposal_workspace_size", "scsf_proposal_init",
     "scsf_proposal_forward", "scsf_proposal_train_step", "scsf_proposal_target_scratch",
     "scsf_proposal_targets", "scsf_proposal_prolong",
-    "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist",
+    "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist", "scsf_block_rotate",
 ]
 
 
@@ -112,6 +112,8 @@ def library() -> ctypes.CDLL:
     L.scsf_sort_workspace_size.restype = sz
     L.scsf_sort.argtypes = [vp, vp, i64, i32, i32, i32, vp, sz, vp]
     L.scsf_sort_dist.argtypes = [vp, vp, i64, i32, i32, i32, vp, sz, vp, vp]
+    L.scsf_block_rotate.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, vp, i32]
+    L.scsf_block_rotate.restype = ctypes.c_int
     L.scsf_sort_dist.restype = ctypes.c_int
     L.scsf_max_block_width.restype = i32
     L.scsf_solve_workspace_size.argtypes = [ctypes.POINTER(_CParams), i32]
@@ -541,6 +543,20 @@ def cheb_filter_dc(op: Operator, X: torch.Tensor, theta: torch.Tensor, degree: i
     cx.check(L.scsf_cheb_filter_dc(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, theta.data_ptr(),
                                    ncols, degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
                                    ws.numel()))
+    return Y
+
+
+def block_rotate(X: torch.Tensor, M: torch.Tensor, ctx: Optional[Context] = None) -> torch.Tensor:
+    """Y = X M (FP64): the rotation of Alg. 3 as a building block."""
+    _check(X, "X")
+    _check(M, "M")
+    if X.dim() != 2 or M.dim() != 2 or X.shape[1] != M.shape[0]:
+        raise ValueError("need X [rows, k] and M [k, n]")
+    cx = _ctx(ctx, X.device)
+    rows, k, n = int(X.shape[0]), int(X.shape[1]), int(M.shape[1])
+    Y = torch.empty((rows, n), dtype=torch.float64, device=X.device)
+    cx.check(library().scsf_block_rotate(cx.handle, X.data_ptr(), k, rows, k, M.data_ptr(), n, n,
+                                         Y.data_ptr(), n))
     return Y
 
 

@@ -1179,6 +1179,18 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   return SCSF_OK;
 }
 
+scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,
+                              const double* M, int ldm, int n, double* Y, int ldy) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!X || !M || !Y) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  if (rows < 1 || k < 1 || n < 1 || k > kMaxBlockWidth || n > kMaxBlockWidth || ldx < k ||
+      ldm < n || ldy < n)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= k, n <= 512 and leading dimensions >= widths");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, launch_gemm_nn(rows, k, n, 1.0, X, ldx, M, ldm, 0.0, Y, ldy, false, ctx->stream));
+  return SCSF_OK;
+}
+
 size_t scsf_small_eigh_scratch(int k) {
   if (k < 1 || k > kMaxBlockWidth) return 0;
   return small_eigh_scratch_bytes(k);

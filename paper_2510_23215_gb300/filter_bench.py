@@ -10,6 +10,7 @@ A filter of degree m launches m stencil steps; the per-step device time is taken
 
     python -m paper_2510_23215_gb300.filter_bench --kernel f32 --shape 256x480
     python -m paper_2510_23215_gb300.filter_bench --kernel dc --shape 128x120 --degree 3 --once
+    python -m paper_2510_23215_gb300.filter_bench --kernel rot --shape 128x120
 
 ``--once`` runs one filter of the given degree and exits (a short command for profilers).
 """
@@ -26,6 +27,32 @@ from . import Context, Operator, assemble_bounds, cheb_filter_dc, cheb_filter_f3
 # algorithmic bytes per (node, column) per step: read Y_i and Y_{i-1}, write Y_{i+1}
 # (FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
 BYTES_PER_ELEM = {"f32": 12.0, "dc": 16.0}
+# FP64 ALU rate of GB300 from unit counts and clocks: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measure_rotation(shape: str, device, reps: int = 20) -> dict:
+    """Y = X M with X FP64 [N, k_b] and M [k_b, k_b] (the rotation X = Q Z of Alg. 3), timed
+    alone: CUDA events around `reps` launches."""
+    from . import block_rotate
+    n, kb = (int(v) for v in shape.split("x"))
+    g = torch.Generator(device="cpu").manual_seed(1)
+    X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(device)
+    M = torch.randn((kb, kb), generator=g, dtype=torch.float64).to(device)
+    ctx = Context(device.index or 0, torch.cuda.current_stream(device))
+    st = torch.cuda.current_stream(device)
+    block_rotate(X, M, ctx=ctx)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        block_rotate(X, M, ctx=ctx)
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    us = e0.elapsed_time(e1) / reps * 1e3
+    flops = 2.0 * n * n * kb * kb
+    return {"kernel": "rot", "shape": shape, "avg_us": us, "flops_per_launch": flops,
+            "tflops": flops / (us * 1e-6) / 1e12, "peak_tflops": FP64_PEAK_TFLOPS}
 
 
 def setup(kernel: str, shape: str, device, seed: int = 0):
@@ -75,12 +102,15 @@ def measure(kernel: str, shape: str, device, degree: int = 20) -> dict:
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--kernel", choices=["f32", "dc"], default="f32")
+    ap.add_argument("--kernel", choices=["f32", "dc", "rot"], default="f32")
     ap.add_argument("--shape", default="128x120")
     ap.add_argument("--degree", type=int, default=20)
     ap.add_argument("--once", action="store_true")
     a = ap.parse_args()
     dev = torch.device("cuda", 0)
+    if a.kernel == "rot":
+        print(json.dumps(measure_rotation(a.shape, dev)))
+        return
     if a.once:
         run, _ = setup(a.kernel, a.shape, dev)
         run(a.degree)

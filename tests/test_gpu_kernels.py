@@ -104,3 +104,16 @@ def test_small_eigh_degenerate_and_near_diagonal():
     D = 0.5 * (D + D.T)
     w, Z = scsf.small_eigh(torch.as_tensor(D, device=dev))
     np.testing.assert_allclose(host(w), np.linalg.eigvalsh(D), rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("rows,k,n", [(1000, 120, 120), (257, 37, 5), (64, 480, 480)])
+def test_block_rotate_matches_numpy(rows, k, n):
+    """Y = X M (the rotation of Alg. 3) against the library product, FP64."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(rows + k)
+    X = rng.standard_normal((rows, k))
+    M = rng.standard_normal((k, n))
+    Y = host(scsf.block_rotate(torch.as_tensor(X, device=dev), torch.as_tensor(M, device=dev)))
+    ref = X @ M
+    assert np.max(np.abs(Y - ref)) <= 1e-13 * k * np.max(np.abs(ref))
