@@ -40,7 +40,8 @@ L2_FLUSH_BYTES = 512 << 20
 BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 16.0}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # current kernels (profiles/cheb_step_*.md); kernels not captured at a shape are absent
-TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6}
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6,
+                      "gemm_nn_rotation": 15.85e6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
@@ -310,7 +311,8 @@ def run_ours(args):
     rot = fb.measure_rotation(f"{n}x{scsf.block_width(k)}", dev)
     roofline = {"bound": "alu", "kernel": "gemm_nn_kernel (FP64 block rotation X = Q M)",
                 "achieved": rot["tflops"], "peak": rot["peak_tflops"], "unit": "TFLOP/s",
-                "frac": rot["tflops"] / rot["peak_tflops"], "traffic": None,
+                "frac": rot["tflops"] / rot["peak_tflops"],
+                "traffic": TRAFFIC_PER_LAUNCH.get("gemm_nn_rotation"),
                 "flops_per_launch": rot["flops_per_launch"], "avg_us_alone": rot["avg_us"],
                 "peak_source": ("FP64 ALU rate from unit counts and clocks: 152 SMs x 2 FMA/clk x "
                                 "2 flop x 2.07 GHz (MEASURED_PEAKS.json has no FP64 figure)"),
