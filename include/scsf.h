@@ -124,6 +124,14 @@ typedef struct {
   const double* v;
 } scsf_operator;
 
+/* SCSF_FP64: Alg. 3 as written, every step in FP64.
+ * SCSF_MIXED (not in the paper; its filter runs in one precision): an FP32 phase (filter,
+ *   Cholesky QR2, Rayleigh-Ritz, rotation in FP32, no locking) until the wanted residuals
+ *   reach the FP32 floor or stall, then FP64 iterations with locking whose filter is
+ *   defect-corrected (the recurrence on Z = Y - X diag(y(theta)) runs in FP32, driven by the
+ *   FP64 residual block) and whose orthonormalisation and Rayleigh-Ritz are FP64. Every
+ *   returned pair meets tol in FP64 exactly as in SCSF_FP64. Needs k_b % 4 == 0.
+ * Both forms: 1 <= k_b = k + nex <= scsf_max_block_width() (512) and k_b <= N. */
 typedef enum { SCSF_FP64 = 0, SCSF_MIXED = 1 } scsf_precision;
 
 typedef struct {

@@ -1154,7 +1154,7 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
   if (ncols < 1 || ncols > kMaxBlockWidth || ldx < ncols || ldy < ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
-    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 160, ld >= ncols, valid filter parameters");
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 512, ld >= ncols, valid filter parameters");
   const int n = op->n;
   Carve cv(scratch, scratch_bytes);
   float *R, *z[3], *d32, *we32, *wn32, *ytab, *coef;

@@ -1,4 +1,5 @@
-// Reduced symmetric eigensolve G W = W Lambda (Alg. 3, reduced eigensolve) for k <= 160.
+// Reduced symmetric eigensolve G W = W Lambda (Alg. 3, reduced eigensolve) for k <= 512
+// (shared-memory kernels up to k = 160, global-memory variants above).
 //
 // GB300 runs FP32 about 60x faster than FP64, so the decomposition is found
 // in FP32 and then refined to FP64 accuracy:
