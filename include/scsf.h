@@ -212,7 +212,8 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max);
  * scsf_chain_step: solves one problem whose grid side equals the chain's n.
  *   evals  : [k] FP64 ascending eigenvalues
  *   resid  : [k] FP64 relative residuals (App. D.5)
- *   evecs  : [N][k] FP64 row-major (column j is eigenvector j) or NULL
+ *   evecs  : [N][k] FP64 row-major (column j is eigenvector j, unit 2-norm, signed so that
+ *            its largest-magnitude entry, lowest row on ties, is positive) or NULL
  *   stats  : host pointer or NULL
  *   On SCSF_ERR_NOT_CONVERGED the locked pairs come first, the other
  *   eigenvalue slots hold NaN, and the warm start is kept for the next step. */

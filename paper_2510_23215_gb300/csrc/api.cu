@@ -973,6 +973,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, cudaMemcpyAsync(b.cols, h + 2 * kMaxBlockWidth, k * sizeof(int),
                                    cudaMemcpyHostToDevice, st));
     SCSF_CUDA(ctx, launch_gather_cols(N, k, b.V, kb, b.cols, evecs, k, st));
+    SCSF_CUDA(ctx, launch_normalize_signs(N, k, evecs, k, st));
   }
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));  // staging buffer is reused by the next call
   if (stats) {

@@ -242,4 +242,49 @@ cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in,
   return cudaGetLastError();
 }
 
+namespace {
+// Sign convention of the returned eigenvectors: each column is flipped so that its entry of
+// largest magnitude (the lowest row index among equal magnitudes) is positive. One CTA per
+// column: a (magnitude, index) reduction, then the flip.
+__global__ void __launch_bounds__(256)
+normalize_signs_kernel(int rows, double* __restrict__ V, int ldv) {
+  __shared__ double s_m[256];
+  __shared__ int s_i[256];
+  const int c = blockIdx.x, t = threadIdx.x;
+  double m = -1.0;
+  int mi = 0x7fffffff;
+  for (int r = t; r < rows; r += blockDim.x) {
+    const double a = fabs(V[(size_t)r * ldv + c]);
+    if (a > m || (a == m && r < mi)) {
+      m = a;
+      mi = r;
+    }
+  }
+  s_m[t] = m;
+  s_i[t] = mi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      const double om = s_m[t + o];
+      const int oi = s_i[t + o];
+      if (om > s_m[t] || (om == s_m[t] && oi < s_i[t])) {
+        s_m[t] = om;
+        s_i[t] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = V[(size_t)s_i[0] * ldv + c] < 0.0;
+  if (flip)
+    for (int r = t; r < rows; r += blockDim.x) V[(size_t)r * ldv + c] = -V[(size_t)r * ldv + c];
+}
+}  // namespace
+
+cudaError_t launch_normalize_signs(int rows, int ncols, double* V, int ldv, cudaStream_t st) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  normalize_signs_kernel<<<ncols, 256, 0, st>>>(rows, V, ldv);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace scsf

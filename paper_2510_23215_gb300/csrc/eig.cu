@@ -91,12 +91,19 @@ __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv,
     }
   }
   __syncthreads();
-  for (int a = warp; a < npairs; a += nwarps) {
+  // the npairs (npairs + 1) / 2 blocks a <= b, dealt evenly over all threads: block index
+  // idx = b (b + 1) / 2 + a with 0 <= a <= b
+  const int nblk = npairs * (npairs + 1) / 2;
+  for (int idx = t; idx < nblk; idx += nt) {
+    int b = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+    while (b * (b + 1) / 2 > idx) --b;
+    while ((b + 1) * (b + 2) / 2 <= idx) ++b;
+    const int a = idx - b * (b + 1) / 2;
     const int pa = plist[2 * a], qa = plist[2 * a + 1];
     const bool ha = qa < k;
     const T a_p = al[pa], b_p = be[pa];
     const T a_q = ha ? al[qa] : T(1), b_q = ha ? be[qa] : T(0);
-    for (int b = a + lane; b < npairs; b += 32) {
+    {
       const int pb = plist[2 * b], qb = plist[2 * b + 1];
       const bool hb = qb < k;
       const T c_p = al[pb], d_p = be[pb];

@@ -72,6 +72,9 @@ cudaError_t launch_copy2d(int rows, int cols, const double* in, int ld_in, doubl
 // Gathers columns: out[r][j] = in[r][cols[j]] (cols: device int32 [ncols]).
 cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in, const int* cols,
                                double* out, int ld_out, cudaStream_t st);
+// Flip each column of V [rows][ncols] so that its largest-magnitude entry (lowest row on
+// ties) is positive.
+cudaError_t launch_normalize_signs(int rows, int ncols, double* V, int ldv, cudaStream_t st);
 
 // ---- reduced eigensolve (eig.cu) ----------------------------------------
 size_t small_eigh_scratch_bytes(int k);

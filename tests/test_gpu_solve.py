@@ -172,3 +172,19 @@ def test_not_converged_and_invalid_arguments():
     with pytest.raises(ValueError):
         scsf.solve([scsf.Operator(scsf.DIV_A_GRAD, 16, ax=op.ax.cpu(), ay=op.ay.cpu())],
                    scsf.Params(k=4))
+
+
+def test_eigenvector_sign_convention():
+    """Returned eigenvectors: the largest-magnitude entry (lowest row on ties) is positive,
+    and the sign flip leaves residuals and orthonormality intact."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(24, 3, seed=12)
+    ev, rs, vec, _ = scsf.solve(to_dev(ops, dev), scsf.Params(k=10, degree=16, tol=1e-8),
+                                want_vectors=True)
+    ev, rs, vec = host(ev), host(rs), host(vec)
+    for j, op in enumerate(ops):
+        V = vec[j]
+        idx = np.argmax(np.abs(V), axis=0)  # first maximum: lowest row on ties
+        assert np.all(V[idx, np.arange(V.shape[1])] > 0)
+        _check_result(op, ev[j], rs[j], V, 10)
