@@ -113,15 +113,27 @@ scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops
  *   ay: [n][n+1] FP64, ay[i][g] = a on the y-face between nodes (i, g-1), (i, g)
  * SCSF_OP_LAP_PLUS_V: -Lap u + V u (same stencil with a == 1, plus diag V)
  *   v : [n][n] FP64
- * Unused pointers may be NULL. */
-typedef enum { SCSF_OP_DIV_A_GRAD = 0, SCSF_OP_LAP_PLUS_V = 1 } scsf_op_kind;
+ * SCSF_OP_CSR: any real symmetric matrix of `rows` rows in CSR form (device arrays):
+ *   row_ptr [rows + 1] int32 (row_ptr[0] = 0, nondecreasing), col [nnz] int32 in
+ *   [0, rows), val [nnz] FP64, nnz = row_ptr[rows] < 2^31; duplicate (row, col)
+ *   entries add. Symmetry is not checked: a nonsymmetric matrix gives meaningless
+ *   output, not an error. n is ignored. Only SCSF_FP64 solves take it (the mixed
+ *   form's FP32 and defect-corrected filters are stencil kernels), on chains made
+ *   by scsf_chain_create_rows; scsf_cheb_filter and scsf_assemble_bounds take it,
+ *   scsf_cheb_filter_f32 / _dc return SCSF_ERR_INVALID_ARG.
+ * Unused pointers may be NULL; rows / row_ptr / col / val are read only for SCSF_OP_CSR. */
+typedef enum { SCSF_OP_DIV_A_GRAD = 0, SCSF_OP_LAP_PLUS_V = 1, SCSF_OP_CSR = 2 } scsf_op_kind;
 
 typedef struct {
-  int kind;          /* scsf_op_kind                   */
-  int n;             /* interior grid side, N = n*n    */
+  int kind;          /* scsf_op_kind                           */
+  int n;             /* interior grid side, N = n*n (stencils) */
   const double* ax;
   const double* ay;
   const double* v;
+  int64_t rows;            /* SCSF_OP_CSR: N = rows, 1 <= rows < 2^31 */
+  const int32_t* row_ptr;  /* SCSF_OP_CSR                              */
+  const int32_t* col;      /* SCSF_OP_CSR                              */
+  const double* val;       /* SCSF_OP_CSR                              */
 } scsf_operator;
 
 /* SCSF_FP64: Alg. 3 as written, every step in FP64.
@@ -193,6 +205,9 @@ int scsf_max_block_width(void);
 
 /* Device workspace (bytes) for problems with grid side <= n_max under params. */
 size_t scsf_solve_workspace_size(const scsf_params* params, int n_max);
+/* Device workspace (bytes) for SCSF_OP_CSR problems of <= rows rows (SCSF_FP64 only;
+ * 0 for SCSF_MIXED or rows out of range). */
+size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows);
 
 /* ---------------------------------------------------------------------------
  * Chain solve (Alg. 3 applied along a sorted sequence, Sec. 3.2).
@@ -206,10 +221,15 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max);
  * scsf_chain_create: allocates only a small host-side handle; `workspace`
  *   (device, >= scsf_solve_workspace_size(params, n) bytes, 256-byte aligned)
  *   must stay alive and untouched by the caller until scsf_chain_destroy.
+ * scsf_chain_create_rows: the same for SCSF_OP_CSR operators of `rows` rows
+ *   (workspace >= scsf_solve_workspace_size_rows(params, rows)); SCSF_FP64 only,
+ *   SCSF_ERR_INVALID_ARG otherwise. A chain takes only the operator kind it was made
+ *   for (stencil chains: stencils of side n; row chains: CSR of `rows` rows).
  * scsf_chain_seed: replaces the warm start by a caller block (device
  *   [N][k_b] FP64, row-major) and its Ritz values (host [k_b] FP64); both are
  *   copied. Used to resume a chain or to inject a proposed subspace.
- * scsf_chain_step: solves one problem whose grid side equals the chain's n.
+ * scsf_chain_step: solves one problem whose grid side equals the chain's n (CSR: whose
+ *   row count equals the chain's rows).
  *   evals  : [k] FP64 ascending eigenvalues
  *   resid  : [k] FP64 relative residuals (App. D.5)
  *   evecs  : [N][k] FP64 row-major (column j is eigenvector j, unit 2-norm, signed so that
@@ -220,12 +240,15 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max);
 typedef struct scsf_chain scsf_chain;
 scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n,
                               void* workspace, size_t workspace_bytes, scsf_chain** out);
+scsf_status scsf_chain_create_rows(scsf_ctx* ctx, const scsf_params* params, int64_t rows,
+                                   void* workspace, size_t workspace_bytes, scsf_chain** out);
 scsf_status scsf_chain_seed(scsf_chain* chain, const double* block, const double* ritz_host);
 scsf_status scsf_chain_step(scsf_chain* chain, const scsf_operator* op, double* evals,
                             double* resid, double* evecs, scsf_stats* stats);
 void scsf_chain_destroy(scsf_chain* chain);
 
-/* Solve n_ops problems (same n) in the given order as one chain.
+/* Solve n_ops problems (same n; or all SCSF_OP_CSR with the same rows) in the given
+ * order as one chain.
  * ops    : host array of n_ops operator descriptors (device pointers inside)
  * evals  : [n_ops][k], resid: [n_ops][k], evecs: [n_ops][N][k] or NULL,
  * stats  : host [n_ops] or NULL. Returns the first non-OK status, after
@@ -247,7 +270,8 @@ scsf_status scsf_solve(scsf_ctx* ctx, const scsf_operator* ops, int64_t n_ops,
  * concurrency) bytes, 256-byte aligned; it is split into one slot per worker.
  * Inputs must be ready on the context's stream when the call is made. */
 typedef struct {
-  const scsf_operator* ops;  /* host array of n_ops descriptors in solve order (same n)  */
+  const scsf_operator* ops;  /* host array of n_ops descriptors in solve order (same n,
+                                or all CSR with the same rows)                          */
   int64_t n_ops;
   scsf_params params;
   double* evals;             /* [n_ops][k]                                             */

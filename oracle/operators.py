@@ -55,7 +55,9 @@ def assemble_lap_plus_v(n: int, V: np.ndarray) -> sp.csr_matrix:
 
 
 def assemble(op) -> sp.csr_matrix:
-    """Dispatch on the workload type (duck-typed: .ax/.ay or .V)."""
+    """Dispatch on the workload type (duck-typed: .ax/.ay, .V, or CSR arrays taken as given)."""
+    if hasattr(op, "row_ptr"):
+        return sp.csr_matrix((op.val, op.col, op.row_ptr), shape=(op.rows, op.rows))
     if hasattr(op, "ax"):
         return assemble_div_a_grad(op.n, op.ax, op.ay)
     return assemble_lap_plus_v(op.n, op.V)

@@ -31,13 +31,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "libscsf.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NO_MEMORY = range(7)
-DIV_A_GRAD, LAP_PLUS_V = 0, 1
+DIV_A_GRAD, LAP_PLUS_V, CSR = 0, 1, 2
 FP64, MIXED = 0, 1
 
 EXPORTED_SYMBOLS = [
     "scsf_create", "scsf_destroy", "scsf_last_error", "scsf_version",
     "scsf_sort_workspace_size", "scsf_sort", "scsf_max_block_width",
     "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
+    "scsf_solve_workspace_size_rows", "scsf_chain_create_rows",
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
     "scsf_sort_noalloc_capacity", "scsf_sort_noalloc", "scsf_cheb_filter_f32",
@@ -57,7 +58,8 @@ class ScsfError(RuntimeError):
 
 class _COperator(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("ax", ctypes.c_void_p),
-                ("ay", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+                ("ay", ctypes.c_void_p), ("v", ctypes.c_void_p), ("rows", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
 class _CParams(ctypes.Structure):
@@ -118,6 +120,10 @@ def library() -> ctypes.CDLL:
     L.scsf_max_block_width.restype = i32
     L.scsf_solve_workspace_size.argtypes = [ctypes.POINTER(_CParams), i32]
     L.scsf_solve_workspace_size.restype = sz
+    L.scsf_solve_workspace_size_rows.argtypes = [ctypes.POINTER(_CParams), i64]
+    L.scsf_solve_workspace_size_rows.restype = sz
+    L.scsf_chain_create_rows.argtypes = [vp, ctypes.POINTER(_CParams), i64, vp, sz,
+                                         ctypes.POINTER(vp)]
     L.scsf_chain_create.argtypes = [vp, ctypes.POINTER(_CParams), i32, vp, sz, ctypes.POINTER(vp)]
     L.scsf_chain_seed.argtypes = [vp, vp, ctypes.POINTER(dbl)]
     L.scsf_chain_step.argtypes = [vp, ctypes.POINTER(_COperator), vp, vp, vp, ctypes.POINTER(_CStats)]
@@ -201,16 +207,35 @@ def block_width(k: int, nex: int = -1) -> int:
 
 @dataclass
 class Operator:
-    """One discretised operator on the n x n interior grid (device FP64 tensors)."""
+    """One discretised operator on the n x n interior grid (device FP64 tensors), or a
+    general symmetric matrix in CSR form (kind CSR; n = 0, N = rows)."""
     kind: int
     n: int
     ax: Optional[torch.Tensor] = None   # [n+1, n]
     ay: Optional[torch.Tensor] = None   # [n, n+1]
     v: Optional[torch.Tensor] = None    # [n, n]
+    rows: int = 0
+    row_ptr: Optional[torch.Tensor] = None  # [rows + 1] int32
+    col: Optional[torch.Tensor] = None      # [nnz] int32
+    val: Optional[torch.Tensor] = None      # [nnz] FP64
+
+    @staticmethod
+    def csr(row_ptr, col, val, device="cuda") -> "Operator":
+        """A symmetric matrix from CSR arrays (host or device; copied to the device)."""
+        rp = torch.as_tensor(row_ptr, dtype=torch.int32, device=device).contiguous()
+        return Operator(CSR, 0, rows=int(rp.numel()) - 1, row_ptr=rp,
+                        col=torch.as_tensor(col, dtype=torch.int32, device=device).contiguous(),
+                        val=torch.as_tensor(val, dtype=torch.float64, device=device).contiguous())
+
+    @property
+    def N(self) -> int:
+        return self.rows if self.kind == CSR else self.n * self.n
 
     @staticmethod
     def from_workload(op, device="cuda") -> "Operator":
         """Uploads an ``scsf_inputs`` operator (numpy) to the device."""
+        if hasattr(op, "row_ptr"):
+            return Operator.csr(op.row_ptr, op.col, op.val, device)
         if hasattr(op, "ax"):
             return Operator(DIV_A_GRAD, op.n,
                             ax=torch.as_tensor(op.ax, dtype=torch.float64, device=device).contiguous(),
@@ -228,13 +253,20 @@ class Operator:
             _check(self.v, "v")
             if tuple(self.v.shape) != (self.n, self.n):
                 raise ValueError("v must be [n, n]")
+        elif self.kind == CSR:
+            _check(self.val, "val")
+            _check(self.row_ptr, "row_ptr", dtype=torch.int32, device=self.val.device)
+            _check(self.col, "col", dtype=torch.int32, device=self.val.device)
+            if self.row_ptr.numel() != self.rows + 1 or self.col.numel() != self.val.numel():
+                raise ValueError("row_ptr must have rows + 1 entries and col / val nnz each")
         else:
             raise ValueError(f"unknown operator kind {self.kind}")
-        return _COperator(self.kind, self.n, _ptr(self.ax), _ptr(self.ay), _ptr(self.v))
+        return _COperator(self.kind, self.n, _ptr(self.ax), _ptr(self.ay), _ptr(self.v),
+                          self.rows, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val))
 
     @property
     def device(self):
-        return (self.ax if self.kind == DIV_A_GRAD else self.v).device
+        return {DIV_A_GRAD: self.ax, LAP_PLUS_V: self.v, CSR: self.val}[self.kind].device
 
 
 @dataclass
@@ -368,26 +400,34 @@ def launch_count() -> int:
 class Chain:
     """A warm-started sequence of solves on one grid size (Alg. 3 along a sorted chain)."""
 
-    def __init__(self, params: Params, n: int, device="cuda", ctx: Optional[Context] = None):
+    def __init__(self, params: Params, n: int, device="cuda", ctx: Optional[Context] = None,
+                 rows: Optional[int] = None):
+        """A chain of n x n stencil operators, or (n = 0, rows given) of CSR operators."""
         self.ctx = _ctx(ctx, device)
         self.params = params
         self.n = n
+        self.N = rows if rows is not None else n * n
         L = library()
         cp = params._c()
-        nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), n)
+        if rows is not None:
+            nbytes = L.scsf_solve_workspace_size_rows(ctypes.byref(cp), rows)
+        else:
+            nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), n)
         if nbytes == 0:
-            raise ValueError("unsupported parameters (block width or grid)")
+            raise ValueError("unsupported parameters (block width, size or precision)")
         self.workspace = _workspace(nbytes, self.ctx.device)
         h = ctypes.c_void_p()
-        self.ctx.check(L.scsf_chain_create(self.ctx.handle, ctypes.byref(cp), n,
-                                           self.workspace.data_ptr(), self.workspace.numel(),
-                                           ctypes.byref(h)))
+        ws = (self.workspace.data_ptr(), self.workspace.numel(), ctypes.byref(h))
+        if rows is not None:
+            self.ctx.check(L.scsf_chain_create_rows(self.ctx.handle, ctypes.byref(cp), rows, *ws))
+        else:
+            self.ctx.check(L.scsf_chain_create(self.ctx.handle, ctypes.byref(cp), n, *ws))
         self._h = h
 
     def seed(self, block: torch.Tensor, ritz: Sequence[float]):
         _check(block, "block", device=self.ctx.device)
         kb = self.params.kb
-        if tuple(block.shape) != (self.n * self.n, kb) or len(ritz) != kb:
+        if tuple(block.shape) != (self.N, kb) or len(ritz) != kb:
             raise ValueError("block must be [N, k_b] with k_b Ritz values")
         arr = (ctypes.c_double * kb)(*[float(x) for x in ritz])
         self.ctx.check(library().scsf_chain_seed(self._h, block.data_ptr(), arr))
@@ -396,7 +436,7 @@ class Chain:
              history: bool = False):
         """Solves the next problem. With history=True, stats["history"] lists per outer
         iteration (max residual, median residual of the wanted unlocked pairs, locked)."""
-        k, N = self.params.k, self.n * self.n
+        k, N = self.params.k, self.N
         dev = self.ctx.device
         evals = torch.empty(k, dtype=torch.float64, device=dev)
         resid = torch.empty(k, dtype=torch.float64, device=dev)
@@ -435,13 +475,15 @@ def solve(ops: List[Operator], params: Params, want_vectors: bool = False,
         raise ValueError("no operators")
     c = _ctx(ctx, ops[0].device)
     L = library()
-    n = ops[0].n
     cp = params._c()
-    nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), n)
+    if ops[0].kind == CSR:
+        nbytes = L.scsf_solve_workspace_size_rows(ctypes.byref(cp), ops[0].rows)
+    else:
+        nbytes = L.scsf_solve_workspace_size(ctypes.byref(cp), ops[0].n)
     if nbytes == 0:
-        raise ValueError("unsupported parameters (block width or grid)")
+        raise ValueError("unsupported parameters (block width, size or precision)")
     ws = _workspace(nbytes, c.device)
-    n_ops, k, N = len(ops), params.k, n * n
+    n_ops, k, N = len(ops), params.k, ops[0].N
     evals = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
     resid = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
     evecs = torch.empty((n_ops, N, k), dtype=torch.float64, device=c.device) if want_vectors else None
@@ -465,7 +507,7 @@ def solve_batched(chains, concurrency: int = 8, want_vectors: bool = False,
     for ops, params in chains:
         if not ops:
             raise ValueError("empty chain")
-        n_ops, k, N = len(ops), params.k, ops[0].n * ops[0].n
+        n_ops, k, N = len(ops), params.k, ops[0].N
         evals = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
         resid = torch.empty((n_ops, k), dtype=torch.float64, device=c.device)
         evecs = torch.empty((n_ops, N, k), dtype=torch.float64, device=c.device) if want_vectors else None
@@ -495,8 +537,8 @@ def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float
     _check(X, "X")
     cx = _ctx(ctx, X.device)
     N, ncols = int(X.shape[0]), int(X.shape[1])
-    if N != op.n * op.n:
-        raise ValueError("X must have n*n rows")
+    if N != op.N:
+        raise ValueError("X must have N rows")
     Y = torch.empty_like(X)
     ws = _workspace(8 * (2 * N * ncols + 3 * N + 2 * 2048) + 8192, X.device)
     cop = op._c()
@@ -512,8 +554,8 @@ def cheb_filter_f32(op: Operator, X: torch.Tensor, degree: int, lam: float, c: f
     _check(X, "X", dtype=torch.float32)
     cx = _ctx(ctx, X.device)
     N, ncols = int(X.shape[0]), int(X.shape[1])
-    if N != op.n * op.n:
-        raise ValueError("X must have n*n rows")
+    if N != op.N:
+        raise ValueError("X must have N rows")
     Y = torch.empty_like(X)
     ws = _workspace(4 * 2 * N * ncols + 8 * 6 * N + (64 << 10), X.device)
     cop = op._c()
@@ -563,7 +605,7 @@ def block_rotate(X: torch.Tensor, M: torch.Tensor, ctx: Optional[Context] = None
 def assemble_bounds(op: Operator, ctx: Optional[Context] = None):
     """Gershgorin bounds (lo, hi) of the assembled operator."""
     cx = _ctx(ctx, op.device)
-    N = op.n * op.n
+    N = op.N
     ws = _workspace(8 * (3 * N + 2 * 2048) + 8192, op.device)
     out = (ctypes.c_double * 2)()
     cop = op._c()

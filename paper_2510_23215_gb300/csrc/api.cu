@@ -87,11 +87,30 @@ int block_width(const scsf_params* p) {
   return p->k + nex;
 }
 
+constexpr int64_t kMaxCsrRows = 0x7fffffff - 1;
+
 bool op_ok(const scsf_operator* op) {
-  if (!op || op->n < 2) return false;
+  if (!op) return false;
+  if (op->kind == SCSF_OP_CSR)
+    return op->rows >= 1 && op->rows <= kMaxCsrRows && op->row_ptr && op->col && op->val;
+  if (op->n < 2) return false;
   if (op->kind == SCSF_OP_DIV_A_GRAD) return op->ax && op->ay;
   if (op->kind == SCSF_OP_LAP_PLUS_V) return op->v != nullptr;
   return false;
+}
+
+// Rows of the operator's matrix (N = n^2 for the stencils).
+size_t op_rows(const scsf_operator& op) {
+  return op.kind == SCSF_OP_CSR ? (size_t)op.rows : (size_t)op.n * op.n;
+}
+
+// The CSR arrays of a SCSF_OP_CSR operator attached to a stencil descriptor.
+Stencil with_csr(Stencil A, const scsf_operator& op) {
+  A.rp = op.row_ptr;
+  A.ci = op.col;
+  A.val = op.val;
+  A.rows = (int)op.rows;
+  return A;
 }
 
 // Device buffers of one chain, carved from the caller's workspace.
@@ -115,8 +134,7 @@ struct ChainBufs {
 };
 
 template <typename Cv>
-void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
-  const size_t N = (size_t)n * n;
+void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, ChainBufs& b) {
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
   const int T = (kb + kGemmTile - 1) / kGemmTile;
@@ -127,7 +145,7 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   b.d = c.template take<double>(N);
   b.we = c.template take<double>(N);
   b.wn = c.template take<double>(N);
-  b.asm_partials = c.template take<double>(2 * (size_t)assemble_blocks(n));
+  b.asm_partials = c.template take<double>(2 * (size_t)assemble_blocks_rows((long long)N));
   b.bounds = c.template take<double>(2);
   b.G = c.template take<double>(kk);
   b.Rinv = c.template take<double>(kk);
@@ -137,7 +155,7 @@ void carve_chain(Cv& c, int n, int kb, bool mixed, int degree, ChainBufs& b) {
   b.theta = c.template take<double>(kb);
   b.res2 = c.template take<double>(2 * (size_t)kb);
   b.gemm_partials = c.template take<double>((size_t)(kSplitTarget + T * T) * kGemmTile * kGemmTile);
-  b.res_partials = c.template take<double>((size_t)resid_blocks(n) * 2 * kb);
+  b.res_partials = c.template take<double>((size_t)resid_blocks_rows((long long)N) * 2 * kb);
   b.eigh_scratch = c.template take<char>(small_eigh_scratch_bytes(kb));
   b.chol_wide = (kb > kSmallBlockWidth) ? c.template take<char>(chol_wide_scratch_bytes(kb)) : nullptr;
   b.status = c.template take<int>(4);
@@ -565,12 +583,27 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, n_max, kb, params->precision == SCSF_MIXED, params->degree, b);
+  carve_chain(c, (size_t)n_max * n_max, kb, params->precision == SCSF_MIXED, params->degree, b);
   return c.used;
 }
 
-scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, void* workspace,
-                              size_t workspace_bytes, scsf_chain** out) {
+size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows) {
+  if (!params || rows < 1 || rows > kMaxCsrRows || params->precision != SCSF_FP64) return 0;
+  const int kb = block_width(params);
+  if (kb < 1 || kb > kMaxBlockWidth) return 0;
+  SizeCarve c;
+  ChainBufs b;
+  carve_chain(c, (size_t)rows, kb, false, params->degree, b);
+  return c.used;
+}
+
+}  // extern "C"
+
+namespace {
+
+// n >= 2: a chain of n x n stencil operators; n == 0: a chain of CSR operators of N rows.
+scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long long N,
+                         void* workspace, size_t workspace_bytes, scsf_chain** out) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!params || !out || !workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
   *out = nullptr;
@@ -578,12 +611,14 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
   if (params->k < 1 || kb > kMaxBlockWidth)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "need 1 <= k and k + nex <= " + std::to_string(kMaxBlockWidth));
-  if (n < 2 || (long long)n * n < kb)
-    return fail(ctx, SCSF_ERR_INVALID_ARG, "grid too small for the block width");
+  if (N < kb) return fail(ctx, SCSF_ERR_INVALID_ARG, "operator too small for the block width");
   if (params->degree < 1 || !(params->tol > 0.0) || params->max_iter < 1)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need degree >= 1, tol > 0, max_iter >= 1");
   if (params->precision != SCSF_FP64 && params->precision != SCSF_MIXED)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "precision must be SCSF_FP64 or SCSF_MIXED");
+  if (params->precision == SCSF_MIXED && n == 0)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "SCSF_MIXED needs a stencil operator (its FP32 filters are stencil kernels)");
   if (params->precision == SCSF_MIXED && kb % 4 != 0)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "SCSF_MIXED needs k + nex divisible by 4 (float4 block rows)");
@@ -594,10 +629,10 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
   ch->ctx = ctx;
   ch->p = *params;
   ch->n = n;
-  ch->N = n * n;
+  ch->N = (int)N;
   ch->kb = kb;
   Carve c(workspace, workspace_bytes);
-  carve_chain(c, n, kb, params->precision == SCSF_MIXED, params->degree, ch->b);
+  carve_chain(c, (size_t)N, kb, params->precision == SCSF_MIXED, params->degree, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -605,6 +640,25 @@ scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, v
   ch->ritz.assign(kb, 0.0);
   *out = ch;
   return SCSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n, void* workspace,
+                              size_t workspace_bytes, scsf_chain** out) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (n < 2) return fail(ctx, SCSF_ERR_INVALID_ARG, "grid too small for the block width");
+  return chain_create(ctx, params, n, (long long)n * n, workspace, workspace_bytes, out);
+}
+
+scsf_status scsf_chain_create_rows(scsf_ctx* ctx, const scsf_params* params, int64_t rows,
+                                   void* workspace, size_t workspace_bytes, scsf_chain** out) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (rows < 1 || rows > kMaxCsrRows)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "rows must be in [1, 2^31 - 2]");
+  return chain_create(ctx, params, 0, rows, workspace, workspace_bytes, out);
 }
 
 void scsf_chain_destroy(scsf_chain* chain) { delete chain; }
@@ -627,17 +681,25 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   scsf_ctx* ctx = ch->ctx;
   cudaStream_t st = ctx->stream;
   if (!op_ok(op)) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad operator descriptor");
-  if (op->n != ch->n) return fail(ctx, SCSF_ERR_INVALID_ARG, "operator grid differs from the chain's");
+  const bool csr = op->kind == SCSF_OP_CSR;
+  if (csr != (ch->n == 0))
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                csr ? "CSR operator on a stencil chain" : "stencil operator on a CSR chain");
+  if (csr ? op->rows != ch->N : op->n != ch->n)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "operator size differs from the chain's");
   if (!evals || !resid) return fail(ctx, SCSF_ERR_INVALID_ARG, "null output pointer");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   const int n = ch->n, N = ch->N, kb = ch->kb, k = ch->p.k, m = ch->p.degree;
   ChainBufs& b = ch->b;
-  const Stencil A = stencil_of(b, n);
+  const Stencil A = csr ? with_csr(stencil_of(b, n), *op) : stencil_of(b, n);
   double* h = ctx->pinned;
 
   // operator coefficients and Gershgorin bounds
-  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, b.d, b.we, b.wn,
-                                 b.asm_partials, b.bounds, st));
+  if (csr)
+    SCSF_CUDA(ctx, launch_csr_bounds(N, op->row_ptr, op->col, op->val, b.asm_partials, b.bounds, st));
+  else
+    SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, b.d, b.we, b.wn,
+                                   b.asm_partials, b.bounds, st));
   SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));
   const double lo = h[0], hi = h[1];
@@ -1011,10 +1073,13 @@ scsf_status scsf_solve(scsf_ctx* ctx, const scsf_operator* ops, int64_t n_ops,
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!ops || n_ops < 1) return fail(ctx, SCSF_ERR_INVALID_ARG, "no operators");
   scsf_chain* ch = nullptr;
-  scsf_status s = scsf_chain_create(ctx, params, ops[0].n, workspace, workspace_bytes, &ch);
+  scsf_status s =
+      ops[0].kind == SCSF_OP_CSR
+          ? scsf_chain_create_rows(ctx, params, ops[0].rows, workspace, workspace_bytes, &ch)
+          : scsf_chain_create(ctx, params, ops[0].n, workspace, workspace_bytes, &ch);
   if (s != SCSF_OK) return s;
   const int k = params->k;
-  const size_t N = (size_t)ops[0].n * ops[0].n;
+  const size_t N = op_rows(ops[0]);
   scsf_status first = SCSF_OK;
   std::string first_msg;
   for (int64_t i = 0; i < n_ops; ++i) {
@@ -1036,17 +1101,21 @@ scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double*
                                  void* scratch, size_t scratch_bytes) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !bounds_host || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
-  const size_t N = (size_t)op->n * op->n;
+  const bool csr = op->kind == SCSF_OP_CSR;
+  const size_t N = op_rows(*op);
   Carve c(scratch, scratch_bytes);
-  double* d = c.take<double>(N);
-  double* we = c.take<double>(N);
-  double* wn = c.take<double>(N);
-  double* part = c.take<double>(2 * (size_t)assemble_blocks(op->n));
+  double* d = csr ? nullptr : c.take<double>(N);
+  double* we = csr ? nullptr : c.take<double>(N);
+  double* wn = csr ? nullptr : c.take<double>(N);
+  double* part = c.take<double>(2 * (size_t)assemble_blocks_rows((long long)N));
   double* bnd = c.take<double>(2);
   if (!c.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
-  SCSF_CUDA(ctx, launch_assemble(op->kind, op->n, op->ax, op->ay, op->v, d, we, wn, part, bnd,
-                                 ctx->stream));
+  if (csr)
+    SCSF_CUDA(ctx, launch_csr_bounds((int)N, op->row_ptr, op->col, op->val, part, bnd, ctx->stream));
+  else
+    SCSF_CUDA(ctx, launch_assemble(op->kind, op->n, op->ax, op->ay, op->v, d, we, wn, part, bnd,
+                                   ctx->stream));
   SCSF_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, bnd, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                  ctx->stream));
   SCSF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1062,21 +1131,23 @@ scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const doubl
   if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
   if (ncols < 1 || ldx < ncols || ldy < ncols || degree < 1 || !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad sizes or filter parameters");
+  const bool csr = op->kind == SCSF_OP_CSR;
   const int n = op->n;
-  const size_t N = (size_t)n * n;
+  const size_t N = op_rows(*op);
   Carve cv(scratch, scratch_bytes);
   double* s0 = cv.take<double>(N * ncols);
   double* s1 = cv.take<double>(N * ncols);
-  double* d = cv.take<double>(N);
-  double* we = cv.take<double>(N);
-  double* wn = cv.take<double>(N);
-  double* part = cv.take<double>(2 * (size_t)assemble_blocks(n));
-  double* bnd = cv.take<double>(2);
+  double* d = csr ? nullptr : cv.take<double>(N);
+  double* we = csr ? nullptr : cv.take<double>(N);
+  double* wn = csr ? nullptr : cv.take<double>(N);
+  double* part = csr ? nullptr : cv.take<double>(2 * (size_t)assemble_blocks(n));
+  double* bnd = csr ? nullptr : cv.take<double>(2);
   if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
-  const Stencil A{d, we, wn, n};
+  if (!csr)
+    SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
+  const Stencil A = csr ? with_csr(Stencil{nullptr, nullptr, nullptr, 0}, *op) : Stencil{d, we, wn, n};
   double* bufs[3] = {s0, s1, Y};
   const int lds[3] = {ncols, ncols, ldy};
   int which = 0;
@@ -1091,6 +1162,8 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
                                  float* Y, int ldy, void* scratch, size_t scratch_bytes) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  if (op->kind == SCSF_OP_CSR)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "the FP32 filter takes stencil operators only");
   if (ncols < 4 || ncols % 4 || ldx % 4 || ldx < ncols || ldy != ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
@@ -1153,6 +1226,8 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !X || !Y || !theta || !scratch)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
+  if (op->kind == SCSF_OP_CSR)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "the defect-corrected filter takes stencil operators only");
   if (ncols < 1 || ncols > kMaxBlockWidth || ldx < ncols || ldy < ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 512, ld >= ncols, valid filter parameters");

@@ -21,11 +21,13 @@ namespace {
 
 size_t chain_bytes(const scsf_batch_chain& c) {
   if (!c.ops || c.n_ops < 1) return 0;
+  if (c.ops[0].kind == SCSF_OP_CSR) return scsf_solve_workspace_size_rows(&c.params, c.ops[0].rows);
   return scsf_solve_workspace_size(&c.params, c.ops[0].n);
 }
 
 double chain_cost(const scsf_batch_chain& c) {
-  const double N = (double)c.ops[0].n * c.ops[0].n;
+  const double N = c.ops[0].kind == SCSF_OP_CSR ? (double)c.ops[0].rows
+                                                : (double)c.ops[0].n * c.ops[0].n;
   const double kb = c.params.k * 1.2;
   return (double)c.n_ops * N * kb * (1.0 + kb / 64.0);
 }

@@ -21,12 +21,21 @@ constexpr int kSplitTarget = 304; // CTAs targeted by split-K Gram launches (2 p
 //   (A y)_I = d[I] y_I - we[I] y_{I+n} - we[I-n] y_{I-n} - wn[I] y_{I+1} - wn[I-1] y_{I-1}
 // we[I] is the coupling of node I to its +i neighbour (zero on the last i row),
 // wn[I] the coupling to its +j neighbour (zero on the last j column).
+// A general sparse operator in CSR form (row_ptr [rows + 1], col / val [nnz], symmetric)
+// travels in the same struct: when rp is non-null the kernels apply A from CSR and ignore
+// d / we / wn.
 struct Stencil {
   const double* d;
   const double* we;
   const double* wn;
   int n;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const double* val = nullptr;
+  int rows = 0;
 };
+
+__host__ __device__ inline int stencil_rows(const Stencil& A) { return A.rp ? A.rows : A.n * A.n; }
 
 // FP32 copy of the stencil coefficients (mixed-precision path).
 struct Stencil32 {

@@ -40,6 +40,11 @@ cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, c
 // storing A X. partials: [resid_blocks(n)][2][ncols]; out2: [2][ncols]. With R32
 // non-null the residual block A X - X diag(theta) is also stored there in FP32 (ld ldr).
 int resid_blocks(int n);
+int resid_blocks_rows(long long N);
+int assemble_blocks_rows(long long N);
+// Gershgorin bounds {lo, hi} of a symmetric CSR matrix (partials: assemble_blocks_rows(rows) x 2).
+cudaError_t launch_csr_bounds(int rows, const int* rp, const int* ci, const double* val,
+                              double* partials, double* bounds, cudaStream_t st);
 cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
                                   const double* theta, double* partials, double* out2,
                                   cudaStream_t st, float* R32 = nullptr, int ldr = 0);

@@ -87,6 +87,37 @@ __global__ void bounds_reduce_kernel(const double* __restrict__ partials, int nb
   }
 }
 
+// Gershgorin bounds of a CSR matrix: per row the diagonal entry -/+ the sum of the
+// off-diagonal magnitudes, reduced per CTA into partials [gridDim][2].
+__global__ void csr_bounds_kernel(int rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const double* __restrict__ val, double* __restrict__ partials) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < rows; I += gridDim.x * blockDim.x) {
+    double dI = 0.0, radius = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p) {
+      if (ci[p] == I) dI += val[p];
+      else radius += fabs(val[p]);
+    }
+    lo = fmin(lo, dI - radius);
+    hi = fmax(hi, dI + radius);
+  }
+  __shared__ double slo[kAsmThreads], shi[kAsmThreads];
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = slo[0];
+    partials[gridDim.x + blockIdx.x] = shi[0];
+  }
+}
+
 // (A y)_I for one column: y points at row I of the block (element c).
 struct NodeCoeffs {
   double d, wE, wW, wN, wS;
@@ -121,9 +152,23 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock)
 cheb_step_f64_kernel(Stencil A, const double* __restrict__ cur, int ldc,
                      const double* __restrict__ prev, int ldp, double* __restrict__ out, int ldo,
                      int ncols, double s1, double s2, double s3) {
-  const int N = A.n * A.n;
+  const int N = stencil_rows(A);
   const int I = blockIdx.x * kRowsPerBlock + threadIdx.y;
   if (I >= N) return;
+  if (A.rp) {  // CSR: out = s1 (A cur) + s2 cur + s3 prev, A cur = sum over the row's entries
+    const int p0 = A.rp[I], p1 = A.rp[I + 1];
+    const double* row = cur + (size_t)I * ldc;
+    const double* prow = prev ? prev + (size_t)I * ldp : nullptr;
+    double* orow = out + (size_t)I * ldo;
+    for (int c = threadIdx.x; c < ncols; c += 32) {
+      double acc = 0.0;
+      for (int p = p0; p < p1; ++p) acc = fma(A.val[p], cur[(size_t)A.ci[p] * ldc + c], acc);
+      double r = fma(s1, acc, s2 * row[c]);
+      if (prow) r = fma(s3, prow[c], r);
+      orow[c] = r;
+    }
+    return;
+  }
   const NodeCoeffs k = load_coeffs(A, I);
   const double diag = fma(s1, k.d, s2);
   const double* row = cur + (size_t)I * ldc;
@@ -141,20 +186,27 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock)
 residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncols,
                       const double* __restrict__ theta, double* __restrict__ partials,
                       float* __restrict__ R32, int ldr) {
-  const int N = A.n * A.n;
+  const int N = stencil_rows(A);
   const int c0 = blockIdx.y * kSmallBlockWidth;  // this CTA's column slice
   double rr[kMaxColChunks], aa[kMaxColChunks];
 #pragma unroll
   for (int q = 0; q < kMaxColChunks; ++q) rr[q] = aa[q] = 0.0;
   for (int I = blockIdx.x * kRowsPerBlock + threadIdx.y; I < N; I += gridDim.x * kRowsPerBlock) {
-    const NodeCoeffs k = load_coeffs(A, I);
+    const NodeCoeffs k = A.rp ? NodeCoeffs{} : load_coeffs(A, I);
     const double* row = X + (size_t)I * ldx;
 #pragma unroll
     for (int q = 0; q < kMaxColChunks; ++q) {
       const int c = c0 + threadIdx.x + 32 * q;
       if (c < ncols) {
         const double x = row[c];
-        const double ax = fma(k.d, x, -offdiag_sum(k, A.n, row, (size_t)ldx, c));
+        double ax;
+        if (A.rp) {
+          ax = 0.0;
+          for (int p = A.rp[I]; p < A.rp[I + 1]; ++p)
+            ax = fma(A.val[p], X[(size_t)A.ci[p] * ldx + c], ax);
+        } else {
+          ax = fma(k.d, x, -offdiag_sum(k, A.n, row, (size_t)ldx, c));
+        }
         const double r = fma(-theta[c], x, ax);
         if (R32) R32[(size_t)I * ldr + c] = (float)r;
         rr[q] = fma(r, r, rr[q]);
@@ -196,10 +248,21 @@ __global__ void column_partials_reduce_kernel(const double* __restrict__ partial
 
 }  // namespace
 
-int assemble_blocks(int n) {
-  const long long N = (long long)n * n;
+int assemble_blocks_rows(long long N) {
   long long b = (N + kAsmThreads - 1) / kAsmThreads;
   return (int)(b < 304 ? b : 304);
+}
+
+int assemble_blocks(int n) { return assemble_blocks_rows((long long)n * n); }
+
+cudaError_t launch_csr_bounds(int rows, const int* rp, const int* ci, const double* val,
+                              double* partials, double* bounds, cudaStream_t st) {
+  const int nb = assemble_blocks_rows(rows);
+  csr_bounds_kernel<<<nb, kAsmThreads, 0, st>>>(rows, rp, ci, val, partials);
+  note_launch();
+  bounds_reduce_kernel<<<1, 256, 0, st>>>(partials, nb, bounds);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(int kind, int n, const double* ax, const double* ay, const double* v,
@@ -216,7 +279,7 @@ cudaError_t launch_assemble(int kind, int n, const double* ax, const double* ay,
 cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, const double* prev,
                                  int ldp, double* out, int ldo, int ncols, double s1, double s2,
                                  double s3, cudaStream_t st) {
-  const int N = A.n * A.n;
+  const int N = stencil_rows(A);
   dim3 block(32, kRowsPerBlock);
   dim3 grid((N + kRowsPerBlock - 1) / kRowsPerBlock);
   cheb_step_f64_kernel<<<grid, block, 0, st>>>(A, cur, ldc, (s3 != 0.0) ? prev : nullptr, ldp, out,
@@ -225,17 +288,18 @@ cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, c
   return cudaGetLastError();
 }
 
-int resid_blocks(int n) {
-  const long long N = (long long)n * n;
+int resid_blocks_rows(long long N) {
   long long b = (N + kRowsPerBlock - 1) / kRowsPerBlock;
   return (int)(b < 304 ? b : 304);
 }
+
+int resid_blocks(int n) { return resid_blocks_rows((long long)n * n); }
 
 cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, int ncols,
                                   const double* theta, double* partials, double* out2,
                                   cudaStream_t st, float* R32, int ldr) {
   if (ncols > kMaxBlockWidth || (R32 && ldr < ncols)) return cudaErrorInvalidValue;
-  const int nb = resid_blocks(A.n);
+  const int nb = resid_blocks_rows(stencil_rows(A));
   const dim3 grid(nb, (ncols + kSmallBlockWidth - 1) / kSmallBlockWidth);
   residual_norms_kernel<<<grid, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta,
                                                                   partials, R32, ldr);

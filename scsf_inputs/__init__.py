@@ -32,6 +32,12 @@ Face coefficients are the field evaluated at face midpoints:
 * ``ay[i, g]`` = a((i+1) h, (g + 1/2) h), g = 0..n
 
 The sort's parameter matrix P (Alg. 2) is the field at the n x n nodes.
+
+General sparse operators (the solver's CSR operator kind) have no grid: there
+the matrix itself is the input. ``knn_graph_chain`` stands in for operators on
+unstructured meshes: a weighted k-nearest-neighbour graph Laplacian on a random
+point cloud (irregular row lengths, 7 to 14 entries a row) plus a quadratic
+potential whose centre moves along the chain.
 """
 from __future__ import annotations
 
@@ -44,7 +50,7 @@ __all__ = [
     "DivAGradOp", "LapPlusVOp", "mode_coefficients", "cosine_field",
     "div_a_grad_chain", "lap_plus_v_chain", "constant_div_a_grad",
     "separable_div_a_grad", "gaussian_block", "batched_chain_specs",
-    "WORKLOADS",
+    "SparseOp", "knn_graph_chain", "WORKLOADS",
 ]
 
 
@@ -164,6 +170,59 @@ def separable_div_a_grad(n: int, seed: int, M: int = 8) -> DivAGradOp:
     ay = np.repeat(np.exp(s * gx_nodes)[:, None], n + 1, axis=1)
     P = np.repeat(np.exp(s * gx_nodes)[:, None], n, axis=1)
     return DivAGradOp(n, ax, ay, P)
+
+
+@dataclass
+class SparseOp:
+    """A symmetric sparse matrix in CSR form (rows sorted, columns ascending in each row)."""
+    rows: int
+    row_ptr: np.ndarray  # [rows + 1] int32
+    col: np.ndarray      # [nnz] int32
+    val: np.ndarray      # [nnz] float64
+
+    @property
+    def N(self) -> int:
+        return self.rows
+
+
+def knn_graph_chain(N: int, n_ops: int, seed: int, neighbours: int = 6,
+                    amplitude: float = 10.0) -> List[SparseOp]:
+    """n_ops operators L + diag(V_t) on one random point cloud.
+
+    N points uniform in the unit square; each is joined to its `neighbours` nearest
+    points, the edge set is symmetrised and every edge gets a weight uniform in
+    [0.5, 1.5). L = D - W is the weighted graph Laplacian and
+    V_t(x, y) = amplitude ((x - c_x)^2 + (y - c_y)^2) with the centre
+    c = (0.5 + 0.2 cos(2 pi t / 64), 0.5 + 0.2 sin(2 pi t / 64)) for problem t (a slow
+    walk, so consecutive problems are close).
+    """
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    pts = rng.random((N, 2))
+    _, nb = cKDTree(pts).query(pts, k=neighbours + 1)
+    i = np.repeat(np.arange(N), neighbours)
+    j = nb[:, 1:].reshape(-1)
+    edges = np.unique(np.stack([np.minimum(i, j), np.maximum(i, j)], axis=1), axis=0)
+    w = 0.5 + rng.random(len(edges))
+    r = np.concatenate([edges[:, 0], edges[:, 1]])
+    c = np.concatenate([edges[:, 1], edges[:, 0]])
+    ww = np.concatenate([w, w])
+    deg = np.bincount(r, weights=ww, minlength=N)
+    out = []
+    for t in range(n_ops):
+        ang = 2.0 * np.pi * t / 64.0
+        cx, cy = 0.5 + 0.2 * np.cos(ang), 0.5 + 0.2 * np.sin(ang)
+        V = amplitude * ((pts[:, 0] - cx) ** 2 + (pts[:, 1] - cy) ** 2)
+        rows = np.concatenate([r, np.arange(N)])
+        cols = np.concatenate([c, np.arange(N)])
+        vals = np.concatenate([-ww, deg + V])
+        order = np.lexsort((cols, rows))
+        rows, cols, vals = rows[order], cols[order], vals[order]
+        row_ptr = np.zeros(N + 1, dtype=np.int64)
+        np.cumsum(np.bincount(rows, minlength=N), out=row_ptr[1:])
+        out.append(SparseOp(N, row_ptr.astype(np.int32), cols.astype(np.int32),
+                            vals.astype(np.float64)))
+    return out
 
 
 def gaussian_block(N: int, k: int, seed: int) -> np.ndarray:

@@ -60,3 +60,17 @@ def test_not_converged_flag():
     op = si.div_a_grad_chain(16, 1, seed=6)[0]
     r = chfsi.solve_chain([op], k=10, degree=2, tol=1e-14, head_seed=0, max_iter=2)[0]
     assert not r.converged and r.iters == 2
+
+
+def test_chain_on_general_csr_matches_dense_definition():
+    """Alg. 3 takes any symmetric matrix: on an irregular graph Laplacian plus potential
+    (no grid) the oracle chain reaches the dense eigenpairs."""
+    ops = si.knn_graph_chain(403, 3, seed=3)
+    res = chfsi.solve_chain(ops, k=10, degree=12, tol=1e-9, head_seed=2)
+    for op, r in zip(ops, res):
+        A = operators.assemble(op)
+        w, V = dense.smallest_eigenpairs(A, 10)
+        assert r.converged
+        assert compare.max_rel_eig_error(w, r.evals) < 1e-10
+        assert np.max(r.resid) <= 1e-9
+        assert compare.orthonormality_error(r.evecs) < 1e-12

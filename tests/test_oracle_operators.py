@@ -1,6 +1,7 @@
 """Pins for oracle.operators / oracle.sturm / oracle.inertia / oracle.dense (CPU only)."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import scsf_inputs as si
 from oracle import dense, inertia, operators, sturm
@@ -179,3 +180,32 @@ def test_cyclic_jacobi_matches_closed_form_and_library():
     S = S + S.T
     wj, _ = dense.cyclic_jacobi(S)
     np.testing.assert_allclose(wj, np.linalg.eigvalsh(S), rtol=1e-12, atol=1e-13)
+
+
+def test_knn_graph_csr_is_laplacian_plus_potential():
+    """The CSR input family: symmetric, sorted CSR; the Laplacian part annihilates constants
+    (A 1 = V exactly, up to rounding), so the smallest eigenvalue lies in [min V, max V]
+    (Rayleigh quotient of the constant vector and L >= 0); Gershgorin encloses the spectrum."""
+    ops = si.knn_graph_chain(301, 2, seed=7)
+    for op in ops:
+        A = operators.assemble(op)
+        assert A.shape == (301, 301) and op.row_ptr[0] == 0 and op.row_ptr[-1] == len(op.val)
+        assert abs(A - A.T).max() == 0.0
+        for r in range(op.rows):  # columns ascending within each row
+            seg = op.col[op.row_ptr[r]:op.row_ptr[r + 1]]
+            assert np.all(np.diff(seg) > 0)
+        lens = np.diff(op.row_ptr)
+        assert lens.min() >= 7 and lens.max() > lens.min()  # irregular rows
+        off = A - sp.diags(A.diagonal())
+        assert np.all(off.data <= 0)  # nonpositive off-diagonal weights
+        V = A @ np.ones(op.rows)
+        assert np.all(V >= 0)
+        w = np.linalg.eigvalsh(A.toarray())
+        assert V.min() - 1e-12 <= w[0] <= V.max() + 1e-12
+        assert w[0] <= V.mean() + 1e-12  # Rayleigh quotient of the constant vector
+        lo, hi = operators.gershgorin_bounds(A)
+        assert lo <= w[0] + 1e-12 and w[-1] <= hi + 1e-12
+    # the potential's centre moves along the chain: the two problems differ only on the diagonal
+    A0, A1 = (operators.assemble(o) for o in ops)
+    D = (A0 - A1).tocoo()
+    assert np.all(D.row[D.data != 0] == D.col[D.data != 0])
