@@ -121,8 +121,23 @@ scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops
  *   form's FP32 and defect-corrected filters are stencil kernels), on chains made
  *   by scsf_chain_create_rows; scsf_cheb_filter and scsf_assemble_bounds take it,
  *   scsf_cheb_filter_f32 / _dc return SCSF_ERR_INVALID_ARG.
- * Unused pointers may be NULL; rows / row_ptr / col / val are read only for SCSF_OP_CSR. */
-typedef enum { SCSF_OP_DIV_A_GRAD = 0, SCSF_OP_LAP_PLUS_V = 1, SCSF_OP_CSR = 2 } scsf_op_kind;
+ * SCSF_OP_PLATE: thin-plate vibration div(grad(D lap u)) = lambda rho u (App. D.2 item 4)
+ *   on the n x n grid, simply supported (u = 0 and D lap u = 0 on the boundary):
+ *   K = L diag(D) L with L = -Lap_h (the 5-point Dirichlet Laplacian), M = diag(rho).
+ *   plate_d, plate_rho: [n][n] FP64 at the nodes, rho > 0. The solver works on the
+ *   symmetric standard form C = M^{-1/2} K M^{-1/2} (13-point, assembled on the device into
+ *   the chain's workspace): evals are the generalized eigenvalues, resid the relative
+ *   residuals of C, and evecs the M-orthonormal modes u = M^{-1/2} v (u^T M u = 1), signed
+ *   as below. SCSF_FP64 only (stencil chains of side n); scsf_cheb_filter and
+ *   scsf_assemble_bounds apply / bound C.
+ * Unused pointers may be NULL; rows / row_ptr / col / val are read only for SCSF_OP_CSR,
+ * plate_d / plate_rho only for SCSF_OP_PLATE. */
+typedef enum {
+  SCSF_OP_DIV_A_GRAD = 0,
+  SCSF_OP_LAP_PLUS_V = 1,
+  SCSF_OP_CSR = 2,
+  SCSF_OP_PLATE = 3
+} scsf_op_kind;
 
 typedef struct {
   int kind;          /* scsf_op_kind                           */
@@ -134,6 +149,8 @@ typedef struct {
   const int32_t* row_ptr;  /* SCSF_OP_CSR                              */
   const int32_t* col;      /* SCSF_OP_CSR                              */
   const double* val;       /* SCSF_OP_CSR                              */
+  const double* plate_d;   /* SCSF_OP_PLATE: D   [n][n]                */
+  const double* plate_rho; /* SCSF_OP_PLATE: rho [n][n]                */
 } scsf_operator;
 
 /* SCSF_FP64: Alg. 3 as written, every step in FP64.
@@ -331,8 +348,10 @@ scsf_status scsf_proposal_prolong(scsf_ctx* ctx, const float* block, int batch, 
  * scsf_cheb_filter: Y = C_m(Abar) X / C_m(t_lambda) by the scaled recurrence of
  *   Alg. 1 (Abar = (A - cI)/e, t_lambda = (lambda - c)/e) for the operator `op`.
  *   X, Y: [N][ncols] FP64 with leading dimensions ldx, ldy (>= ncols);
- *   scratch: device, >= 2 * N * ncols * 8 bytes. X and Y must not overlap.
- * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}).
+ *   scratch: device, >= 8 (2 N ncols + 3 N + 4096) + 8192 bytes, plus 4 (14 N + 1) + 104 N
+ *   for SCSF_OP_PLATE. X and Y must not overlap.
+ * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}); scratch as for
+ *   scsf_cheb_filter with ncols = 0.
  * scsf_small_eigh: all eigenpairs of a symmetric k x k FP64 matrix S
  *   (row-major, k <= scsf_max_block_width()): evals [k] ascending, Z [k][k]
  *   with eigenvector j in column j. scratch >= scsf_small_eigh_scratch(k). */

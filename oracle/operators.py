@@ -54,8 +54,35 @@ def assemble_lap_plus_v(n: int, V: np.ndarray) -> sp.csr_matrix:
     return (A + sp.diags(V.reshape(-1))).tocsr()
 
 
+def laplacian(n: int) -> sp.csr_matrix:
+    """-Lap_h: the 5-point Dirichlet Laplacian (a == 1 in the conservative form)."""
+    return assemble_div_a_grad(n, np.ones((n + 1, n)), np.ones((n, n + 1)))
+
+
+def assemble_plate_stiffness(n: int, D: np.ndarray) -> sp.csr_matrix:
+    """K for div(grad(D lap u)) (App. D.2 item 4): K = L diag(D) L with L = -Lap_h.
+
+    Reading of the boundary condition: the paper states only "Dirichlet"; a fourth-order
+    operator needs two conditions, taken as u = 0 and D lap u = 0 on the boundary (the
+    simply supported plate). Both come from composing two Dirichlet Laplacians: the inner
+    one sees u = 0 outside, the outer one sees D lap u = 0 outside. K is symmetric
+    positive definite with a 13-point stencil."""
+    L = laplacian(n)
+    return (L @ sp.diags(D.reshape(-1)) @ L).tocsr()
+
+
+def assemble_plate(n: int, D: np.ndarray, rho: np.ndarray) -> sp.csr_matrix:
+    """The generalized problem K u = lambda M u, M = diag(rho), in symmetric standard form
+    C = M^{-1/2} K M^{-1/2}: C v = lambda v with u = M^{-1/2} v."""
+    s = sp.diags(1.0 / np.sqrt(rho.reshape(-1)))
+    return (s @ assemble_plate_stiffness(n, D) @ s).tocsr()
+
+
 def assemble(op) -> sp.csr_matrix:
-    """Dispatch on the workload type (duck-typed: .ax/.ay, .V, or CSR arrays taken as given)."""
+    """Dispatch on the workload type (duck-typed: .ax/.ay, .V, .D/.rho (standard form of the
+    plate problem), or CSR arrays taken as given)."""
+    if hasattr(op, "rho"):
+        return assemble_plate(op.n, op.D, op.rho)
     if hasattr(op, "row_ptr"):
         return sp.csr_matrix((op.val, op.col, op.row_ptr), shape=(op.rows, op.rows))
     if hasattr(op, "ax"):

@@ -31,7 +31,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "libscsf.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NO_MEMORY = range(7)
-DIV_A_GRAD, LAP_PLUS_V, CSR = 0, 1, 2
+DIV_A_GRAD, LAP_PLUS_V, CSR, PLATE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
 EXPORTED_SYMBOLS = [
@@ -59,7 +59,8 @@ class ScsfError(RuntimeError):
 class _COperator(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("ax", ctypes.c_void_p),
                 ("ay", ctypes.c_void_p), ("v", ctypes.c_void_p), ("rows", ctypes.c_int64),
-                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("plate_d", ctypes.c_void_p), ("plate_rho", ctypes.c_void_p)]
 
 
 class _CParams(ctypes.Structure):
@@ -208,7 +209,8 @@ def block_width(k: int, nex: int = -1) -> int:
 @dataclass
 class Operator:
     """One discretised operator on the n x n interior grid (device FP64 tensors), or a
-    general symmetric matrix in CSR form (kind CSR; n = 0, N = rows)."""
+    general symmetric matrix in CSR form (kind CSR; n = 0, N = rows). Kind PLATE is the
+    thin-plate problem div(grad(D lap u)) = lambda rho u (D, rho [n, n] at the nodes)."""
     kind: int
     n: int
     ax: Optional[torch.Tensor] = None   # [n+1, n]
@@ -218,6 +220,8 @@ class Operator:
     row_ptr: Optional[torch.Tensor] = None  # [rows + 1] int32
     col: Optional[torch.Tensor] = None      # [nnz] int32
     val: Optional[torch.Tensor] = None      # [nnz] FP64
+    D: Optional[torch.Tensor] = None        # [n, n] (PLATE)
+    rho: Optional[torch.Tensor] = None      # [n, n] (PLATE)
 
     @staticmethod
     def csr(row_ptr, col, val, device="cuda") -> "Operator":
@@ -236,6 +240,10 @@ class Operator:
         """Uploads an ``scsf_inputs`` operator (numpy) to the device."""
         if hasattr(op, "row_ptr"):
             return Operator.csr(op.row_ptr, op.col, op.val, device)
+        if hasattr(op, "rho"):
+            return Operator(PLATE, op.n,
+                            D=torch.as_tensor(op.D, dtype=torch.float64, device=device).contiguous(),
+                            rho=torch.as_tensor(op.rho, dtype=torch.float64, device=device).contiguous())
         if hasattr(op, "ax"):
             return Operator(DIV_A_GRAD, op.n,
                             ax=torch.as_tensor(op.ax, dtype=torch.float64, device=device).contiguous(),
@@ -253,6 +261,11 @@ class Operator:
             _check(self.v, "v")
             if tuple(self.v.shape) != (self.n, self.n):
                 raise ValueError("v must be [n, n]")
+        elif self.kind == PLATE:
+            _check(self.D, "D")
+            _check(self.rho, "rho", device=self.D.device)
+            if tuple(self.D.shape) != (self.n, self.n) or tuple(self.rho.shape) != (self.n, self.n):
+                raise ValueError("D and rho must be [n, n]")
         elif self.kind == CSR:
             _check(self.val, "val")
             _check(self.row_ptr, "row_ptr", dtype=torch.int32, device=self.val.device)
@@ -262,11 +275,12 @@ class Operator:
         else:
             raise ValueError(f"unknown operator kind {self.kind}")
         return _COperator(self.kind, self.n, _ptr(self.ax), _ptr(self.ay), _ptr(self.v),
-                          self.rows, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val))
+                          self.rows, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val),
+                          _ptr(self.D), _ptr(self.rho))
 
     @property
     def device(self):
-        return {DIV_A_GRAD: self.ax, LAP_PLUS_V: self.v, CSR: self.val}[self.kind].device
+        return {DIV_A_GRAD: self.ax, LAP_PLUS_V: self.v, CSR: self.val, PLATE: self.D}[self.kind].device
 
 
 @dataclass
@@ -531,6 +545,11 @@ def solve_batched(chains, concurrency: int = 8, want_vectors: bool = False,
             for i, (e, r, v, stt) in enumerate(outs)]
 
 
+def _plate_scratch(op: Operator) -> int:
+    """Extra building-block scratch for the thin-plate operator's 13-slot CSR form."""
+    return 4 * (14 * op.N + 1) + 104 * op.N + 1024 if op.kind == PLATE else 0
+
+
 def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float, e: float,
                 ctx: Optional[Context] = None) -> torch.Tensor:
     """Alg. 1: C_m(Abar) X / C_m(t_lambda) for X [N, ncols] FP64."""
@@ -540,7 +559,7 @@ def cheb_filter(op: Operator, X: torch.Tensor, degree: int, lam: float, c: float
     if N != op.N:
         raise ValueError("X must have N rows")
     Y = torch.empty_like(X)
-    ws = _workspace(8 * (2 * N * ncols + 3 * N + 2 * 2048) + 8192, X.device)
+    ws = _workspace(8 * (2 * N * ncols + 3 * N + 2 * 2048) + 8192 + _plate_scratch(op), X.device)
     cop = op._c()
     cx.check(library().scsf_cheb_filter(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, ncols,
                                         degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
@@ -606,7 +625,7 @@ def assemble_bounds(op: Operator, ctx: Optional[Context] = None):
     """Gershgorin bounds (lo, hi) of the assembled operator."""
     cx = _ctx(ctx, op.device)
     N = op.N
-    ws = _workspace(8 * (3 * N + 2 * 2048) + 8192, op.device)
+    ws = _workspace(8 * (3 * N + 2 * 2048) + 8192 + _plate_scratch(op), op.device)
     out = (ctypes.c_double * 2)()
     cop = op._c()
     cx.check(library().scsf_assemble_bounds(cx.handle, ctypes.byref(cop), out, ws.data_ptr(),

@@ -94,6 +94,7 @@ bool op_ok(const scsf_operator* op) {
   if (op->kind == SCSF_OP_CSR)
     return op->rows >= 1 && op->rows <= kMaxCsrRows && op->row_ptr && op->col && op->val;
   if (op->n < 2) return false;
+  if (op->kind == SCSF_OP_PLATE) return op->plate_d && op->plate_rho;
   if (op->kind == SCSF_OP_DIV_A_GRAD) return op->ax && op->ay;
   if (op->kind == SCSF_OP_LAP_PLUS_V) return op->v != nullptr;
   return false;
@@ -131,10 +132,13 @@ struct ChainBufs {
   float* coef32;  // [kMaxGraphSteps][3] scalars of the captured FP32 filter
   float* ytab;  // [degree][kb] scalar filter values at the Ritz values
   double* ym;   // [2][kb] recurrence state; y_m in the second row
+  // FP64 stencil chains: the thin-plate operator assembled as CSR (13 slots a row)
+  int *prp, *pci;
+  double* pval;
 };
 
 template <typename Cv>
-void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, ChainBufs& b) {
+void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, ChainBufs& b) {
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
   const int T = (kb + kGemmTile - 1) / kGemmTile;
@@ -160,6 +164,13 @@ void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, ChainBufs& b) 
   b.chol_wide = (kb > kSmallBlockWidth) ? c.template take<char>(chol_wide_scratch_bytes(kb)) : nullptr;
   b.status = c.template take<int>(4);
   b.cols = c.template take<int>(kb);
+  b.prp = b.pci = nullptr;
+  b.pval = nullptr;
+  if (plate) {
+    b.prp = c.template take<int>(N + 1);
+    b.pci = c.template take<int>(13 * N);
+    b.pval = c.template take<double>(13 * N);
+  }
   b.V32 = b.d32 = b.we32 = b.wn32 = b.partials32 = nullptr;
   b.B32[0] = b.B32[1] = b.B32[2] = nullptr;
   b.ytab = nullptr;
@@ -583,7 +594,8 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, (size_t)n_max * n_max, kb, params->precision == SCSF_MIXED, params->degree, b);
+  const bool mixed = params->precision == SCSF_MIXED;
+  carve_chain(c, (size_t)n_max * n_max, kb, mixed, params->degree, !mixed, b);
   return c.used;
 }
 
@@ -593,7 +605,7 @@ size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, (size_t)rows, kb, false, params->degree, b);
+  carve_chain(c, (size_t)rows, kb, false, params->degree, false, b);
   return c.used;
 }
 
@@ -632,7 +644,8 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
   ch->N = (int)N;
   ch->kb = kb;
   Carve c(workspace, workspace_bytes);
-  carve_chain(c, (size_t)N, kb, params->precision == SCSF_MIXED, params->degree, ch->b);
+  const bool mixed = params->precision == SCSF_MIXED;
+  carve_chain(c, (size_t)N, kb, mixed, params->degree, n > 0 && !mixed, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -687,17 +700,30 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
                 csr ? "CSR operator on a stencil chain" : "stencil operator on a CSR chain");
   if (csr ? op->rows != ch->N : op->n != ch->n)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "operator size differs from the chain's");
+  const bool plate = op->kind == SCSF_OP_PLATE;
+  if (plate && ch->p.precision != SCSF_FP64)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "the thin-plate operator takes SCSF_FP64 only (the mixed form's filters are 5-point)");
   if (!evals || !resid) return fail(ctx, SCSF_ERR_INVALID_ARG, "null output pointer");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   const int n = ch->n, N = ch->N, kb = ch->kb, k = ch->p.k, m = ch->p.degree;
   ChainBufs& b = ch->b;
-  const Stencil A = csr ? with_csr(stencil_of(b, n), *op) : stencil_of(b, n);
+  Stencil A = csr ? with_csr(stencil_of(b, n), *op) : stencil_of(b, n);
+  if (plate) {
+    A.rp = b.prp;
+    A.ci = b.pci;
+    A.val = b.pval;
+    A.rows = N;
+  }
   double* h = ctx->pinned;
 
   // operator coefficients and Gershgorin bounds
-  if (csr)
+  if (csr) {
     SCSF_CUDA(ctx, launch_csr_bounds(N, op->row_ptr, op->col, op->val, b.asm_partials, b.bounds, st));
-  else
+  } else if (plate) {
+    SCSF_CUDA(ctx, launch_plate_csr(n, op->plate_d, op->plate_rho, b.prp, b.pci, b.pval, st));
+    SCSF_CUDA(ctx, launch_csr_bounds(N, b.prp, b.pci, b.pval, b.asm_partials, b.bounds, st));
+  } else
     SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, b.d, b.we, b.wn,
                                    b.asm_partials, b.bounds, st));
   SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1035,6 +1061,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, cudaMemcpyAsync(b.cols, h + 2 * kMaxBlockWidth, k * sizeof(int),
                                    cudaMemcpyHostToDevice, st));
     SCSF_CUDA(ctx, launch_gather_cols(N, k, b.V, kb, b.cols, evecs, k, st));
+    if (plate)  // modes of K u = lambda M u: u = M^{-1/2} v
+      SCSF_CUDA(ctx, launch_scale_rows_rsqrt(N, k, evecs, k, op->plate_rho, st));
     SCSF_CUDA(ctx, launch_normalize_signs(N, k, evecs, k, st));
   }
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));  // staging buffer is reused by the next call
@@ -1101,7 +1129,7 @@ scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double*
                                  void* scratch, size_t scratch_bytes) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !bounds_host || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
-  const bool csr = op->kind == SCSF_OP_CSR;
+  const bool csr = op->kind == SCSF_OP_CSR, plate = op->kind == SCSF_OP_PLATE;
   const size_t N = op_rows(*op);
   Carve c(scratch, scratch_bytes);
   double* d = csr ? nullptr : c.take<double>(N);
@@ -1109,11 +1137,17 @@ scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double*
   double* wn = csr ? nullptr : c.take<double>(N);
   double* part = c.take<double>(2 * (size_t)assemble_blocks_rows((long long)N));
   double* bnd = c.take<double>(2);
+  int* prp = plate ? c.take<int>(N + 1) : nullptr;
+  int* pci = plate ? c.take<int>(13 * N) : nullptr;
+  double* pval = plate ? c.take<double>(13 * N) : nullptr;
   if (!c.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
-  if (csr)
+  if (csr) {
     SCSF_CUDA(ctx, launch_csr_bounds((int)N, op->row_ptr, op->col, op->val, part, bnd, ctx->stream));
-  else
+  } else if (plate) {
+    SCSF_CUDA(ctx, launch_plate_csr(op->n, op->plate_d, op->plate_rho, prp, pci, pval, ctx->stream));
+    SCSF_CUDA(ctx, launch_csr_bounds((int)N, prp, pci, pval, part, bnd, ctx->stream));
+  } else
     SCSF_CUDA(ctx, launch_assemble(op->kind, op->n, op->ax, op->ay, op->v, d, we, wn, part, bnd,
                                    ctx->stream));
   SCSF_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, bnd, 2 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1131,23 +1165,34 @@ scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const doubl
   if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
   if (ncols < 1 || ldx < ncols || ldy < ncols || degree < 1 || !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad sizes or filter parameters");
-  const bool csr = op->kind == SCSF_OP_CSR;
+  const bool csr = op->kind == SCSF_OP_CSR, plate = op->kind == SCSF_OP_PLATE;
+  const bool stencil = !csr && !plate;
   const int n = op->n;
   const size_t N = op_rows(*op);
   Carve cv(scratch, scratch_bytes);
   double* s0 = cv.take<double>(N * ncols);
   double* s1 = cv.take<double>(N * ncols);
-  double* d = csr ? nullptr : cv.take<double>(N);
-  double* we = csr ? nullptr : cv.take<double>(N);
-  double* wn = csr ? nullptr : cv.take<double>(N);
-  double* part = csr ? nullptr : cv.take<double>(2 * (size_t)assemble_blocks(n));
-  double* bnd = csr ? nullptr : cv.take<double>(2);
+  double* d = stencil ? cv.take<double>(N) : nullptr;
+  double* we = stencil ? cv.take<double>(N) : nullptr;
+  double* wn = stencil ? cv.take<double>(N) : nullptr;
+  double* part = stencil ? cv.take<double>(2 * (size_t)assemble_blocks(n)) : nullptr;
+  double* bnd = stencil ? cv.take<double>(2) : nullptr;
+  int* prp = plate ? cv.take<int>(N + 1) : nullptr;
+  int* pci = plate ? cv.take<int>(13 * N) : nullptr;
+  double* pval = plate ? cv.take<double>(13 * N) : nullptr;
   if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  if (!csr)
+  if (stencil)
     SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
-  const Stencil A = csr ? with_csr(Stencil{nullptr, nullptr, nullptr, 0}, *op) : Stencil{d, we, wn, n};
+  if (plate) SCSF_CUDA(ctx, launch_plate_csr(n, op->plate_d, op->plate_rho, prp, pci, pval, st));
+  Stencil A = csr ? with_csr(Stencil{nullptr, nullptr, nullptr, 0}, *op) : Stencil{d, we, wn, n};
+  if (plate) {
+    A.rp = prp;
+    A.ci = pci;
+    A.val = pval;
+    A.rows = (int)N;
+  }
   double* bufs[3] = {s0, s1, Y};
   const int lds[3] = {ncols, ncols, ldy};
   int which = 0;
@@ -1162,8 +1207,8 @@ scsf_status scsf_cheb_filter_f32(scsf_ctx* ctx, const scsf_operator* op, const f
                                  float* Y, int ldy, void* scratch, size_t scratch_bytes) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !X || !Y || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
-  if (op->kind == SCSF_OP_CSR)
-    return fail(ctx, SCSF_ERR_INVALID_ARG, "the FP32 filter takes stencil operators only");
+  if (op->kind == SCSF_OP_CSR || op->kind == SCSF_OP_PLATE)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "the FP32 filter takes 5-point stencil operators only");
   if (ncols < 4 || ncols % 4 || ldx % 4 || ldx < ncols || ldy != ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
@@ -1226,8 +1271,9 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !X || !Y || !theta || !scratch)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
-  if (op->kind == SCSF_OP_CSR)
-    return fail(ctx, SCSF_ERR_INVALID_ARG, "the defect-corrected filter takes stencil operators only");
+  if (op->kind == SCSF_OP_CSR || op->kind == SCSF_OP_PLATE)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "the defect-corrected filter takes 5-point stencil operators only");
   if (ncols < 1 || ncols > kMaxBlockWidth || ldx < ncols || ldy < ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 512, ld >= ncols, valid filter parameters");

@@ -280,6 +280,27 @@ normalize_signs_kernel(int rows, double* __restrict__ V, int ldv) {
 }
 }  // namespace
 
+// V[r][c] /= sqrt(w[r]): maps standard-form eigenvectors v of M^{-1/2} K M^{-1/2} to the
+// M-orthonormal solutions u = M^{-1/2} v of K u = lambda M u (M = diag(w)).
+__global__ void scale_rows_rsqrt_kernel(int rows, int ncols, double* __restrict__ V, int ldv,
+                                        const double* __restrict__ w) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)rows * ncols;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ncols), c = (int)(e - (size_t)r * ncols);
+    V[(size_t)r * ldv + c] /= sqrt(w[r]);
+  }
+}
+
+cudaError_t launch_scale_rows_rsqrt(int rows, int ncols, double* V, int ldv, const double* w,
+                                    cudaStream_t st) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  const size_t total = (size_t)rows * ncols;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  scale_rows_rsqrt_kernel<<<blocks, 256, 0, st>>>(rows, ncols, V, ldv, w);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_normalize_signs(int rows, int ncols, double* V, int ldv, cudaStream_t st) {
   if (rows <= 0 || ncols <= 0) return cudaSuccess;
   normalize_signs_kernel<<<ncols, 256, 0, st>>>(rows, V, ldv);

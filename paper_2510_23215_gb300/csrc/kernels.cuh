@@ -42,6 +42,13 @@ cudaError_t launch_cheb_step_f64(const Stencil& A, const double* cur, int ldc, c
 int resid_blocks(int n);
 int resid_blocks_rows(long long N);
 int assemble_blocks_rows(long long N);
+// The thin-plate operator's standard form as a 13-slot-per-row CSR matrix (rp [n^2 + 1],
+// ci / val [13 n^2]); D and rho at the n x n nodes.
+cudaError_t launch_plate_csr(int n, const double* D, const double* rho, int* rp, int* ci,
+                             double* val, cudaStream_t st);
+// V[r][c] /= sqrt(w[r]) for r < rows, c < ncols.
+cudaError_t launch_scale_rows_rsqrt(int rows, int ncols, double* V, int ldv, const double* w,
+                                    cudaStream_t st);
 // Gershgorin bounds {lo, hi} of a symmetric CSR matrix (partials: assemble_blocks_rows(rows) x 2).
 cudaError_t launch_csr_bounds(int rows, const int* rp, const int* ci, const double* val,
                               double* partials, double* bounds, cudaStream_t st);

@@ -118,6 +118,52 @@ __global__ void csr_bounds_kernel(int rows, const int* __restrict__ rp, const in
   }
 }
 
+// Thin-plate operator (App. D.2 item 4) in symmetric standard form C = S K S, K = L diag(D) L,
+// S = diag(rho)^(-1/2), L = -Lap_h with Dirichlet rows (u = 0 and D lap u = 0 on the boundary:
+// the simply supported plate). Row I = (i, j) couples the 13 nodes with |di| + |dj| <= 2:
+//   C_IK = s_I s_K / h^4 sum_J l_IJ D_J l_JK,  l = h^2 L (4 on the diagonal, -1 to each
+// interior neighbour), J over I and its interior neighbours. Fixed 13 slots per row
+// (row_ptr[I] = 13 I) in ascending column order; slots outside the grid hold (col I, 0).
+__device__ __forceinline__ double plate_l(int pi, int pj, int qi, int qj) {
+  const int d = abs(pi - qi) + abs(pj - qj);
+  return d == 0 ? 4.0 : (d == 1 ? -1.0 : 0.0);
+}
+
+__global__ void plate_csr_kernel(int n, const double* __restrict__ D, const double* __restrict__ rho,
+                                 int* __restrict__ rp, int* __restrict__ ci,
+                                 double* __restrict__ val) {
+  const int N = n * n;
+  const double h2 = 1.0 / ((double)(n + 1) * (n + 1));
+  const double inv_h4 = 1.0 / (h2 * h2);
+  constexpr int kOff[13][2] = {{-2, 0}, {-1, -1}, {-1, 0}, {-1, 1}, {0, -2}, {0, -1}, {0, 0},
+                               {0, 1},  {0, 2},   {1, -1}, {1, 0},  {1, 1},  {2, 0}};
+  constexpr int kNb[5][2] = {{0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}};
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
+    const int i = I / n, j = I - i * n;
+    const double sI = 1.0 / sqrt(rho[I]);
+    rp[I] = 13 * I;
+    if (I == N - 1) rp[N] = 13 * N;
+    for (int q = 0; q < 13; ++q) {
+      const int ki = i + kOff[q][0], kj = j + kOff[q][1];
+      double v = 0.0;
+      int col = I;
+      if (ki >= 0 && ki < n && kj >= 0 && kj < n) {
+        col = ki * n + kj;
+        double acc = 0.0;
+        for (int t = 0; t < 5; ++t) {
+          const int ji = i + kNb[t][0], jj = j + kNb[t][1];
+          if (ji < 0 || ji >= n || jj < 0 || jj >= n) continue;
+          const double lk = plate_l(ji, jj, ki, kj);
+          if (lk != 0.0) acc += plate_l(i, j, ji, jj) * D[ji * n + jj] * lk;
+        }
+        v = sI * (1.0 / sqrt(rho[col])) * acc * inv_h4;
+      }
+      ci[13 * I + q] = col;
+      val[13 * I + q] = v;
+    }
+  }
+}
+
 // (A y)_I for one column: y points at row I of the block (element c).
 struct NodeCoeffs {
   double d, wE, wW, wN, wS;
@@ -254,6 +300,13 @@ int assemble_blocks_rows(long long N) {
 }
 
 int assemble_blocks(int n) { return assemble_blocks_rows((long long)n * n); }
+
+cudaError_t launch_plate_csr(int n, const double* D, const double* rho, int* rp, int* ci,
+                             double* val, cudaStream_t st) {
+  plate_csr_kernel<<<assemble_blocks(n), kAsmThreads, 0, st>>>(n, D, rho, rp, ci, val);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_csr_bounds(int rows, const int* rp, const int* ci, const double* val,
                               double* partials, double* bounds, cudaStream_t st) {

@@ -6,11 +6,14 @@ A filter of degree m launches m stencil steps; the per-step device time is taken
 * ``128x120``: one chain of the 128 x 128, k = 100 workload (N = 16384, k_b = 120);
   its three blocks fit in L2, so the rate is an effective one;
 * ``256x480``: the 256 x 256, k = 400 block (N = 65536, k_b = 480, 3 x 126 MB in FP32),
-  which streams every step through DRAM.
+  which streams every step through DRAM;
+* ``--kernel plate``: the FP64 step on the thin-plate operator's 13-slot CSR form
+  (e.g. ``100x120``: N = 10^4, k_b = 120; 24 B per node and column plus 156 B per node).
 
     python -m paper_2510_23215_gb300.filter_bench --kernel f32 --shape 256x480
     python -m paper_2510_23215_gb300.filter_bench --kernel dc --shape 128x120 --degree 3 --once
     python -m paper_2510_23215_gb300.filter_bench --kernel rot --shape 128x120
+    python -m paper_2510_23215_gb300.filter_bench --kernel plate --shape 100x120 --once
 
 ``--once`` runs one filter of the given degree and exits (a short command for profilers).
 """
@@ -22,11 +25,11 @@ import json
 import numpy as np
 import torch
 
-from . import Context, Operator, assemble_bounds, cheb_filter_dc, cheb_filter_f32
+from . import Context, Operator, assemble_bounds, cheb_filter, cheb_filter_dc, cheb_filter_f32
 
 # algorithmic bytes per (node, column) per step: read Y_i and Y_{i-1}, write Y_{i+1}
 # (FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
-BYTES_PER_ELEM = {"f32": 12.0, "dc": 16.0}
+BYTES_PER_ELEM = {"f32": 12.0, "dc": 16.0, "plate": 24.0}
 # FP64 ALU rate of GB300 from unit counts and clocks: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -59,6 +62,15 @@ def setup(kernel: str, shape: str, device, seed: int = 0):
     """(runner(degree), elements per step) for the kernel at the shape."""
     import scsf_inputs as si  # seeded operator generators (no method arithmetic)
     n, kb = (int(v) for v in shape.split("x"))
+    if kernel == "plate":
+        op = Operator.from_workload(si.plate_chain(n, 1, seed=6)[0], device)
+        ctx = Context(device.index or 0, torch.cuda.current_stream(device))
+        lo, hi = assemble_bounds(op, ctx)
+        alpha = lo + 0.01 * (hi - lo)
+        c, e = 0.5 * (alpha + hi), 0.5 * (hi - alpha)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(device)
+        return (lambda d: cheb_filter(op, X, d, lo, c, e, ctx=ctx)), n * n * kb
     if n == 256:
         op = Operator.from_workload(si.lap_plus_v_chain(n, 1, seed=2)[0], device)
     else:
@@ -95,14 +107,15 @@ def per_step_us(run, degree: int, device, reps: int = 3) -> float:
 def measure(kernel: str, shape: str, device, degree: int = 20) -> dict:
     run, elems = setup(kernel, shape, device)
     us = per_step_us(run, degree, device)
-    nbytes = BYTES_PER_ELEM[kernel] * elems
+    kb = int(shape.split("x")[1])
+    nbytes = BYTES_PER_ELEM[kernel] * elems + (156.0 * elems / kb if kernel == "plate" else 0.0)
     return {"kernel": kernel, "shape": shape, "avg_us": us, "bytes_per_launch": nbytes,
             "gbs": nbytes / (us * 1e-6) / 1e9}
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--kernel", choices=["f32", "dc", "rot"], default="f32")
+    ap.add_argument("--kernel", choices=["f32", "dc", "rot", "plate"], default="f32")
     ap.add_argument("--shape", default="128x120")
     ap.add_argument("--degree", type=int, default=20)
     ap.add_argument("--once", action="store_true")

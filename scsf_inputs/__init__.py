@@ -21,6 +21,9 @@ other, with the (0, 0) mode included and no decay weighting.
   deviation of about 0.5 and a spans a factor of about 4-6.
 * Laplacian-plus-potential workloads (stand-in for the Helmholtz family,
   App. D.2 item 3): V = 10 f with M = 12.
+* thin-plate vibration workloads (App. D.2 item 4, div(grad(D lap u)) = lambda rho u):
+  flexural rigidity D = exp(0.5 f / M) and density rho = exp(0.5 g / M), M = 8, with
+  f and g drawn one after the other (f's modes first), both at the n x n nodes.
 
 Grid convention (Sec. 2.1, row-major node order): the unit square holds an
 n x n interior grid with spacing h = 1/(n+1); node (i, j) sits at
@@ -50,7 +53,7 @@ __all__ = [
     "DivAGradOp", "LapPlusVOp", "mode_coefficients", "cosine_field",
     "div_a_grad_chain", "lap_plus_v_chain", "constant_div_a_grad",
     "separable_div_a_grad", "gaussian_block", "batched_chain_specs",
-    "SparseOp", "knn_graph_chain", "WORKLOADS",
+    "SparseOp", "knn_graph_chain", "PlateOp", "plate_chain", "constant_plate", "WORKLOADS",
 ]
 
 
@@ -80,6 +83,24 @@ class LapPlusVOp:
     @property
     def P(self) -> np.ndarray:
         return self.V
+
+
+@dataclass
+class PlateOp:
+    """Thin-plate vibration problem on the n x n interior grid: rigidity D and density rho
+    at the nodes."""
+    n: int
+    D: np.ndarray    # [n, n] float64
+    rho: np.ndarray  # [n, n] float64
+
+    @property
+    def N(self) -> int:
+        return self.n * self.n
+
+    @property
+    def P(self) -> np.ndarray:
+        """Sort input: the local ratio D / rho (the eigenvalues scale with it)."""
+        return self.D / self.rho
 
 
 def mode_coefficients(rng: np.random.Generator, M: int) -> np.ndarray:
@@ -138,6 +159,25 @@ def lap_plus_v_chain(n: int, n_ops: int, seed: int, M: int = 12,
         xi = mode_coefficients(rng, M)
         out.append(LapPlusVOp(n, np.ascontiguousarray(amplitude * cosine_field(xi, nodes, nodes))))
     return out
+
+
+def plate_chain(n: int, n_ops: int, seed: int, M: int = 8) -> List[PlateOp]:
+    """n_ops plate problems: D = exp(0.5 f / M), rho = exp(0.5 g / M), f then g drawn per
+    problem."""
+    rng = np.random.default_rng(seed)
+    nodes, _ = _grids(n)
+    out = []
+    for _ in range(n_ops):
+        f = cosine_field(mode_coefficients(rng, M), nodes, nodes)
+        g = cosine_field(mode_coefficients(rng, M), nodes, nodes)
+        out.append(PlateOp(n, np.ascontiguousarray(np.exp(0.5 * f / M)),
+                           np.ascontiguousarray(np.exp(0.5 * g / M))))
+    return out
+
+
+def constant_plate(n: int, D: float = 1.0, rho: float = 1.0) -> PlateOp:
+    """Uniform plate: D and rho constant."""
+    return PlateOp(n, np.full((n, n), D), np.full((n, n), rho))
 
 
 def constant_div_a_grad(n: int, value: float = 1.0) -> DivAGradOp:

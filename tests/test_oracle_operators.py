@@ -209,3 +209,63 @@ def test_knn_graph_csr_is_laplacian_plus_potential():
     A0, A1 = (operators.assemble(o) for o in ops)
     D = (A0 - A1).tocoo()
     assert np.all(D.row[D.data != 0] == D.col[D.data != 0])
+
+
+def test_plate_stencil_is_the_textbook_biharmonic_stencil():
+    """D == 1: an interior row of K is the 13-point biharmonic stencil (20, -8, 2, 1) / h^4;
+    next to a simply supported edge the centre is 19 (ghost value -u_1), at a corner 18.
+    Variable D: K_II = (16 D_I + sum of D over the interior neighbours) / h^4."""
+    n = 9
+    h = 1.0 / (n + 1)
+    K = operators.assemble_plate_stiffness(n, np.ones((n, n))).toarray() * h**4
+    I = lambda i, j: i * n + j
+    c = I(4, 4)
+    assert K[c, c] == pytest.approx(20.0)
+    for di, dj, v in [(1, 0, -8), (0, 1, -8), (-1, 0, -8), (0, -1, -8), (1, 1, 2), (1, -1, 2),
+                      (-1, 1, 2), (-1, -1, 2), (2, 0, 1), (0, 2, 1), (-2, 0, 1), (0, -2, 1)]:
+        assert K[c, I(4 + di, 4 + dj)] == pytest.approx(v)
+    assert np.count_nonzero(np.abs(K[c]) > 1e-12) == 13
+    assert K[I(0, 4), I(0, 4)] == pytest.approx(19.0) and K[I(0, 0), I(0, 0)] == pytest.approx(18.0)
+    assert np.max(np.count_nonzero(np.abs(K) > 1e-12, axis=1)) == 13
+    D = np.random.default_rng(3).uniform(0.5, 2.0, (n, n))
+    Kd = operators.assemble_plate_stiffness(n, D).toarray() * h**4
+    for (i, j) in [(4, 4), (0, 3), (0, 0), (8, 8)]:
+        nb = sum(D[i + di, j + dj] for di, dj in [(1, 0), (-1, 0), (0, 1), (0, -1)]
+                 if 0 <= i + di < n and 0 <= j + dj < n)
+        assert Kd[I(i, j), I(i, j)] == pytest.approx(16 * D[i, j] + nb)
+
+
+def test_uniform_plate_spectrum_closed_form():
+    """D, rho constant: the modes are the Laplacian's sine modes and
+    lambda_ij = (D / rho) (4/h^2 (sin^2(i pi h/2) + sin^2(j pi h/2)))^2."""
+    n, d0, r0 = 14, 2.5, 0.8
+    h = 1.0 / (n + 1)
+    op = si.constant_plate(n, d0, r0)
+    C = operators.assemble(op)
+    i = np.arange(1, n + 1)
+    lam1 = 4.0 / h**2 * np.sin(i * np.pi * h / 2) ** 2
+    ref = np.sort((d0 / r0 * (lam1[:, None] + lam1[None, :]) ** 2).ravel())
+    w = np.linalg.eigvalsh(C.toarray())
+    assert np.max(np.abs(w - ref)) <= 1e-11 * ref[-1]
+    phi = sturm.laplacian_2d_mode(n, 2, 3)
+    lam = d0 / r0 * (lam1[1] + lam1[2]) ** 2
+    assert np.linalg.norm(C @ phi - lam * phi) <= 1e-12 * lam * np.linalg.norm(phi)
+
+
+def test_plate_standard_form_matches_generalized_problem():
+    """The symmetric standard form C = M^{-1/2} K M^{-1/2} has the generalized eigenvalues
+    of (K, M = diag(rho)) (LAPACK's generalized symmetric-definite solver), and
+    u = M^{-1/2} v solves K u = lambda M u with u^T M u = 1."""
+    import scipy.linalg as sla
+    op = si.plate_chain(11, 1, seed=5)[0]
+    K = operators.assemble_plate_stiffness(op.n, op.D).toarray()
+    M = np.diag(op.rho.reshape(-1))
+    wg = sla.eigh(K, M, eigvals_only=True)
+    C = operators.assemble(op).toarray()
+    assert np.max(np.abs(C - C.T)) <= 1e-15 * np.max(np.abs(C))  # symmetric up to rounding
+    w, V = np.linalg.eigh(C)
+    assert np.max(np.abs(w - wg)) <= 1e-12 * wg[-1]
+    assert w[0] > 0  # symmetric positive definite
+    U = V / np.sqrt(op.rho.reshape(-1))[:, None]
+    assert np.max(np.abs(K @ U - (M @ U) * w)) <= 1e-11 * wg[-1]
+    assert np.max(np.abs(U.T @ M @ U - np.eye(len(w)))) <= 1e-12
