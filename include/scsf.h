@@ -352,6 +352,12 @@ scsf_status scsf_proposal_prolong(scsf_ctx* ctx, const float* block, int batch, 
  *   for SCSF_OP_PLATE. X and Y must not overlap.
  * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}); scratch as for
  *   scsf_cheb_filter with ncols = 0.
+ * scsf_cholqr2: Q = X R^{-1} with X = Q R (Alg. 3, orthonormalisation) by Cholesky QR2:
+ *   G = X^T X, R1 from the Cholesky factor of D^-1 G D^-1 (D = diag(G)^(1/2)) taken in
+ *   FP32, Q1 = X R1^{-1}; then the same in FP64 on Q1. Shifted restarts on a failed pivot;
+ *   shifts_host[2] (host, or NULL) receives the restarts per pass. X [rows][ncols] FP64
+ *   (ldx), Q [rows][ncols] (ldq), 1 <= ncols <= min(rows, 512); X and Q must not overlap;
+ *   scratch >= scsf_cholqr2_scratch(rows, ncols). SCSF_ERR_BREAKDOWN if a pass still fails.
  * scsf_small_eigh: all eigenpairs of a symmetric k x k FP64 matrix S
  *   (row-major, k <= scsf_max_block_width()): evals [k] ascending, Z [k][k]
  *   with eigenvector j in column j. scratch >= scsf_small_eigh_scratch(k). */
@@ -360,6 +366,9 @@ scsf_status scsf_cheb_filter(scsf_ctx* ctx, const scsf_operator* op, const doubl
                              double* Y, int ldy, void* scratch, size_t scratch_bytes);
 scsf_status scsf_assemble_bounds(scsf_ctx* ctx, const scsf_operator* op, double* bounds_host,
                                  void* scratch, size_t scratch_bytes);
+size_t scsf_cholqr2_scratch(int rows, int ncols);
+scsf_status scsf_cholqr2(scsf_ctx* ctx, const double* X, int ldx, int rows, int ncols, double* Q,
+                         int ldq, int* shifts_host, void* scratch, size_t scratch_bytes);
 /* scsf_cheb_filter on FP32 blocks (the mixed form's filter): X, Y [N][ncols]
  * FP32 with ncols and ldx multiples of 4 and ldy == ncols; the operator is assembled in FP64
  * and rounded to FP32; scratch >= 2 N ncols 4 + 6 N 8 + 64 KiB bytes. */

@@ -38,7 +38,8 @@ EXPORTED_SYMBOLS = [
     "scsf_create", "scsf_destroy", "scsf_last_error", "scsf_version",
     "scsf_sort_workspace_size", "scsf_sort", "scsf_max_block_width",
     "scsf_solve_workspace_size", "scsf_chain_create", "scsf_chain_seed", "scsf_chain_step",
-    "scsf_solve_workspace_size_rows", "scsf_chain_create_rows",
+    "scsf_solve_workspace_size_rows", "scsf_chain_create_rows", "scsf_cholqr2_scratch",
+    "scsf_cholqr2",
     "scsf_chain_destroy", "scsf_solve", "scsf_cheb_filter", "scsf_assemble_bounds",
     "scsf_small_eigh_scratch", "scsf_small_eigh", "scsf_set_timing", "scsf_launch_count",
     "scsf_sort_noalloc_capacity", "scsf_sort_noalloc", "scsf_cheb_filter_f32",
@@ -121,6 +122,10 @@ def library() -> ctypes.CDLL:
     L.scsf_max_block_width.restype = i32
     L.scsf_solve_workspace_size.argtypes = [ctypes.POINTER(_CParams), i32]
     L.scsf_solve_workspace_size.restype = sz
+    L.scsf_cholqr2_scratch.argtypes = [i32, i32]
+    L.scsf_cholqr2_scratch.restype = sz
+    L.scsf_cholqr2.argtypes = [vp, vp, i32, i32, i32, vp, i32, ctypes.POINTER(i32), vp, sz]
+    L.scsf_cholqr2.restype = ctypes.c_int
     L.scsf_solve_workspace_size_rows.argtypes = [ctypes.POINTER(_CParams), i64]
     L.scsf_solve_workspace_size_rows.restype = sz
     L.scsf_chain_create_rows.argtypes = [vp, ctypes.POINTER(_CParams), i64, vp, sz,
@@ -631,6 +636,26 @@ def assemble_bounds(op: Operator, ctx: Optional[Context] = None):
     cx.check(library().scsf_assemble_bounds(cx.handle, ctypes.byref(cop), out, ws.data_ptr(),
                                             ws.numel()))
     return float(out[0]), float(out[1])
+
+
+def cholqr2(X: torch.Tensor, ctx: Optional[Context] = None):
+    """Cholesky QR2 of X [rows, ncols] FP64 (FP32 first factor, FP64 second). Returns
+    (Q, (shifted restarts of pass 1, of pass 2))."""
+    _check(X, "X")
+    if X.dim() != 2:
+        raise ValueError("X must be [rows, ncols]")
+    rows, ncols = int(X.shape[0]), int(X.shape[1])
+    cx = _ctx(ctx, X.device)
+    L = library()
+    nbytes = L.scsf_cholqr2_scratch(rows, ncols)
+    if nbytes == 0:
+        raise ValueError("need 1 <= ncols <= min(rows, 512)")
+    ws = _workspace(nbytes, X.device)
+    Q = torch.empty_like(X)
+    shifts = (ctypes.c_int * 2)()
+    cx.check(L.scsf_cholqr2(cx.handle, X.data_ptr(), ncols, rows, ncols, Q.data_ptr(), ncols,
+                            shifts, ws.data_ptr(), ws.numel()))
+    return Q, (int(shifts[0]), int(shifts[1]))
 
 
 def small_eigh(S: torch.Tensor, ctx: Optional[Context] = None):

@@ -1313,6 +1313,71 @@ scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows,
   return SCSF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+template <typename Cv>
+void carve_cholqr2(Cv& cv, int rows, int ncols, double** G, double** L, double** Rinv,
+                   double** partials, double** F, void** wide, int** status) {
+  const size_t kk = (size_t)ncols * ncols;
+  *G = cv.template take<double>(kk);
+  *L = cv.template take<double>(kk);
+  *Rinv = cv.template take<double>(kk);
+  *partials = cv.template take<double>(gemm_tn_partials(rows, ncols, ncols, true));
+  *F = cv.template take<double>((size_t)rows * ncols);
+  *wide = (ncols > kSmallBlockWidth) ? (void*)cv.template take<char>(chol_wide_scratch_bytes(ncols))
+                                     : nullptr;
+  *status = cv.template take<int>(2);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t scsf_cholqr2_scratch(int rows, int ncols) {
+  if (rows < 1 || ncols < 1 || ncols > kMaxBlockWidth || ncols > rows) return 0;
+  SizeCarve sc;
+  double *G, *L, *Rinv, *partials, *F;
+  void* wide;
+  int* status;
+  carve_cholqr2(sc, rows, ncols, &G, &L, &Rinv, &partials, &F, &wide, &status);
+  return sc.used;
+}
+
+scsf_status scsf_cholqr2(scsf_ctx* ctx, const double* X, int ldx, int rows, int ncols, double* Q,
+                         int ldq, int* shifts_host, void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!X || !Q || !scratch) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  if (rows < 1 || ncols < 1 || ncols > kMaxBlockWidth || ncols > rows || ldx < ncols || ldq < ncols)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= min(rows, 512), ld >= ncols");
+  Carve cv(scratch, scratch_bytes);
+  double *G, *L, *Rinv, *partials, *F;
+  void* wide;
+  int* status;
+  carve_cholqr2(cv, rows, ncols, &G, &L, &Rinv, &partials, &F, &wide, &status);
+  if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // pass 1 (FP32 factor of the FP64 Gram matrix) into F, pass 2 (FP64) into Q
+  SCSF_CUDA(ctx, launch_gemm_tn(rows, ncols, ncols, X, ldx, X, ldx, G, ncols, true, partials, st));
+  SCSF_CUDA(ctx, launch_chol_rinv(ncols, G, ncols, true, L, Rinv, status, st, wide));
+  SCSF_CUDA(ctx, launch_gemm_nn(rows, ncols, ncols, 1.0, X, ldx, Rinv, ncols, 0.0, F, ncols, true, st));
+  SCSF_CUDA(ctx, launch_gemm_tn(rows, ncols, ncols, F, ncols, F, ncols, G, ncols, true, partials, st));
+  SCSF_CUDA(ctx, launch_chol_rinv(ncols, G, ncols, false, L, Rinv, status + 1, st, wide));
+  SCSF_CUDA(ctx, launch_gemm_nn(rows, ncols, ncols, 1.0, F, ncols, Rinv, ncols, 0.0, Q, ldq, true, st));
+  int* h = reinterpret_cast<int*>(ctx->pinned);
+  SCSF_CUDA(ctx, cudaMemcpyAsync(h, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+  if (shifts_host) {
+    shifts_host[0] = h[0];
+    shifts_host[1] = h[1];
+  }
+  if (h[0] >= 1000 || h[1] >= 1000)
+    return fail(ctx, SCSF_ERR_BREAKDOWN, "Cholesky QR broke down even with a shift");
+  return SCSF_OK;
+}
+
 size_t scsf_small_eigh_scratch(int k) {
   if (k < 1 || k > kMaxBlockWidth) return 0;
   return small_eigh_scratch_bytes(k);

@@ -3,6 +3,12 @@
 // CholQR2 factors two Gram matrices per outer iteration. The first factor only
 // has to make X R^{-1} well conditioned, so it is computed in FP32 (60x the FP64
 // rate on GB300); the second, which fixes the final orthonormality, in FP64.
+// Both factorise the diagonally scaled Gram matrix S = D^-1 G D^-1 and return L = D L_S
+// (G = L L^T), with D_ii the power of two nearest below sqrt(G_ii) (S_ii in [1, 4)). The
+// scaling is exact, so wherever G's entries are in range the factor has the same bits as
+// without it; it keeps the factorisation in range when the columns of X are far below
+// FP32's (a high-degree filter scales them by 1 / C_m(t_lambda)), and it is within a factor
+// of 4 of the optimal diagonal preconditioner for the pivots (van der Sluis).
 // Both factorisations run in one CTA with the matrix in shared memory
 // (right-looking, one column per step, the trailing update on a 32 x 32 thread
 // grid without index division). The inverse R^{-1} = (L^{-1})^T is spread over
@@ -17,9 +23,18 @@ namespace {
 
 __host__ __device__ __forceinline__ int odd_stride(int k) { return (k % 2 == 0) ? k + 1 : k; }
 
-// G = L L^T for k x k symmetric positive definite G (lower triangle read).
-// On a non-positive pivot the factorisation restarts on G + s I (shifted
-// Cholesky QR) with s growing 100x per retry, starting at c_eps k trace(G).
+// Scale of row / column i: 2^floor(e / 2) for G_ii = m 2^e (m in [1, 2)), or 1 for a
+// diagonal that is not positive and finite (the pivot then fails and the shifted restart
+// takes over).
+__device__ __forceinline__ double chol_scale(double g) {
+  if (!(g > 0.0 && g < INFINITY)) return 1.0;
+  const int e = ilogb(g);
+  return ldexp(1.0, (e >= 0) ? e / 2 : -((1 - e) / 2));
+}
+
+// G = L L^T for k x k symmetric positive definite G (lower triangle read), k <= 160,
+// through S = D^-1 G D^-1 (D from chol_scale). On a non-positive pivot the factorisation restarts on S + s I
+// (shifted Cholesky QR) with s growing 100x per retry, starting at c_eps k trace(S).
 // Writes L (lower, FP64, ld k, zeros above) and status = number of shifted
 // restarts, or 1000 if the last attempt still failed. blockDim = (32, 32).
 template <typename T>
@@ -32,10 +47,13 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
   __shared__ T dinv_s;
   __shared__ int bad;
   __shared__ double trace;
+  __shared__ double sc[kSmallBlockWidth];
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  for (int i = t; i < k; i += 1024) sc[i] = chol_scale(G[(size_t)i * ldg + i]);
+  __syncthreads();
   if (t == 0) {
     double tr = 0.0;
-    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]);
+    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]) / (sc[i] * sc[i]);
     trace = tr;
   }
   __syncthreads();
@@ -44,7 +62,7 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
     const double shift = (attempt == 0) ? 0.0 : shift_eps * k * trace * pow(100.0, attempt - 1);
     for (int i = ty; i < k; i += 32)
       for (int j = tx; j <= i; j += 32)
-        S[i * ks + j] = (T)(G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0));
+        S[i * ks + j] = (T)(G[(size_t)i * ldg + j] / (sc[i] * sc[j]) + ((i == j) ? shift : 0.0));
     if (t == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < k; ++j) {
@@ -75,7 +93,8 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
     __syncthreads();
   }
   for (int i = ty; i < k; i += 32)
-    for (int j = tx; j < k; j += 32) L[(size_t)i * k + j] = (j <= i) ? (double)S[i * ks + j] : 0.0;
+    for (int j = tx; j < k; j += 32)
+      L[(size_t)i * k + j] = (j <= i) ? (double)S[i * ks + j] * sc[i] : 0.0;
   if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
 }
 
@@ -141,12 +160,12 @@ trinv_kernel(int k, const double* __restrict__ L, double* __restrict__ Rinv) {
 constexpr int kPanel = 32;
 
 template <typename T>
-__global__ void chol_load_kernel(int k, const double* __restrict__ G, int ldg, double shift,
-                                 T* __restrict__ M) {
+__global__ void chol_load_kernel(int k, const double* __restrict__ G, int ldg,
+                                 const double* __restrict__ sc, double shift, T* __restrict__ M) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)k * k) return;
   const int i = (int)(e / k), j = (int)(e - (long long)i * k);
-  if (j <= i) M[e] = (T)(G[(size_t)i * ldg + j] + ((i == j) ? shift : 0.0));
+  if (j <= i) M[e] = (T)(G[(size_t)i * ldg + j] / (sc[i] * sc[j]) + ((i == j) ? shift : 0.0));
 }
 
 template <typename T>
@@ -223,17 +242,24 @@ chol_trailing_kernel(int k, T* __restrict__ M, int p) {
 }
 
 template <typename T>
-__global__ void chol_store_kernel(int k, const T* __restrict__ M, double* __restrict__ L) {
+__global__ void chol_store_kernel(int k, const T* __restrict__ M, const double* __restrict__ sc,
+                                  double* __restrict__ L) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)k * k) return;
   const int i = (int)(e / k), j = (int)(e - (long long)i * k);
-  L[e] = (j <= i) ? (double)M[e] : 0.0;
+  L[e] = (j <= i) ? (double)M[e] * sc[i] : 0.0;
 }
 
-__global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg, double* out) {
+// Row scales sc[i] (chol_scale of G_ii) and trace(D^-1 G D^-1) into *out.
+__global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg,
+                                  double* __restrict__ sc, double* out) {
   __shared__ double red[256];
   double s = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) s += fabs(G[(size_t)i * ldg + i]);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double g = G[(size_t)i * ldg + i], d = chol_scale(g);
+    sc[i] = d;
+    s += fabs(g) / (d * d);
+  }
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -243,8 +269,8 @@ __global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg, 
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// Factor with the restart rule of chol_kernel (shift c_eps k trace(G) 100^(attempt-1)); the
-// host reads the failure flag after each attempt (wide blocks only).
+// Factor with the scaling and restart rule of chol_kernel (shift c_eps k trace(S)
+// 100^(attempt-1)); the host reads the failure flag after each attempt (wide blocks only).
 template <typename T>
 cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* status, double eps,
                              void* scratch, cudaStream_t st) {
@@ -252,11 +278,12 @@ cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* st
   T* M = cv.take<T>((size_t)k * k);
   int* bad = cv.take<int>(4);
   double* tr = cv.take<double>(1);
+  double* sc = cv.take<double>(k);
   if (!cv.ok) return cudaErrorInvalidValue;
   const size_t psmem = (size_t)k * 33 * sizeof(T);
   cudaError_t e = ensure_dynamic_smem((const void*)chol_panel_kernel<T>, psmem);
   if (e != cudaSuccess) return e;
-  chol_trace_kernel<<<1, 256, 0, st>>>(k, G, ldg, tr);
+  chol_trace_kernel<<<1, 256, 0, st>>>(k, G, ldg, sc, tr);
   note_launch();
   double trace = 0.0;
   if ((e = cudaMemcpyAsync(&trace, tr, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -268,7 +295,7 @@ cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* st
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     const double shift = (attempt == 0) ? 0.0 : eps * k * trace * pow(100.0, attempt - 1);
     if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st)) != cudaSuccess) return e;
-    chol_load_kernel<T><<<eb, 256, 0, st>>>(k, G, ldg, shift, M);
+    chol_load_kernel<T><<<eb, 256, 0, st>>>(k, G, ldg, sc, shift, M);
     note_launch();
     for (int p = 0; p < k; p += kPanel) {
       chol_panel_kernel<T><<<1, 1024, psmem, st>>>(k, M, p, bad);
@@ -284,7 +311,7 @@ cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* st
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     if (h_bad == 0) break;
   }
-  chol_store_kernel<T><<<eb, 256, 0, st>>>(k, M, L);
+  chol_store_kernel<T><<<eb, 256, 0, st>>>(k, M, sc, L);
   note_launch();
   const int code = (h_bad != 0) ? 1000 : attempt;
   if ((e = cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -308,7 +335,7 @@ cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* statu
 }  // namespace
 
 size_t chol_wide_scratch_bytes(int k) {
-  return align256((size_t)k * k * sizeof(double)) + 512;
+  return align256((size_t)k * k * sizeof(double)) + align256((size_t)k * sizeof(double)) + 512;
 }
 
 cudaError_t launch_chol_rinv(int k, const double* G, int ldg, bool fp32, double* L, double* Rinv,

@@ -117,3 +117,28 @@ def test_block_rotate_matches_numpy(rows, k, n):
     Y = host(scsf.block_rotate(torch.as_tensor(X, device=dev), torch.as_tensor(M, device=dev)))
     ref = X @ M
     assert np.max(np.abs(Y - ref)) <= 1e-13 * k * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("rows,k,lo_exp", [(5000, 120, -30), (3001, 200, -30), (700, 7, 0)])
+def test_cholqr2_orthonormal_and_reproduces_x(rows, k, lo_exp):
+    """Cholesky QR2 (Alg. 3, orthonormalisation) on X = Z diag(s) with Z Gaussian and column
+    scales s down to 1e-30 (a Gram entry of 1e-60 is below FP32's range, so the FP32 first
+    factor must work on the scaled Gram matrix): Q^T Q = I, Q R = X with R = Q^T X upper
+    triangular, and Q equal to the library's Householder Q (its columns signed so that R has
+    a positive diagonal; the column scales leave Q unchanged). k = 200 takes the wide path."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(rows + k)
+    Z = rng.standard_normal((rows, k))
+    s = 10.0 ** rng.uniform(lo_exp, 0.0, k)
+    X = Z * s[None, :]
+    Q, shifts = scsf.cholqr2(torch.as_tensor(X, device=dev))
+    Q = host(Q)
+    assert shifts == (0, 0)
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) <= 1e-13
+    R = Q.T @ X
+    assert np.max(np.abs(np.tril(R, -1)) / s[None, :]) <= 1e-12
+    assert np.max(np.abs(Q @ np.triu(R) - X) / s[None, :]) <= 1e-12
+    Qr, Rr = np.linalg.qr(Z)
+    Qr = Qr * np.sign(np.diag(Rr))[None, :]
+    assert np.max(np.abs(Q - Qr)) <= 1e-11
