@@ -3,12 +3,12 @@
 // CholQR2 factors two Gram matrices per outer iteration. The first factor only
 // has to make X R^{-1} well conditioned, so it is computed in FP32 (60x the FP64
 // rate on GB300); the second, which fixes the final orthonormality, in FP64.
-// Both factorise the diagonally scaled Gram matrix S = D^-1 G D^-1 and return L = D L_S
-// (G = L L^T), with D_ii the power of two nearest below sqrt(G_ii) (S_ii in [1, 4)). The
-// scaling is exact, so wherever G's entries are in range the factor has the same bits as
-// without it; it keeps the factorisation in range when the columns of X are far below
-// FP32's (a high-degree filter scales them by 1 / C_m(t_lambda)), and it is within a factor
-// of 4 of the optimal diagonal preconditioner for the pivots (van der Sluis).
+// When a diagonal entry of G lies outside [2^-100, 2^100] -- columns of X far outside FP32's
+// range, as after a high-degree filter that scales them by 1 / C_m(t_lambda) -- both factor
+// the diagonally scaled Gram matrix S = D^-1 G D^-1 instead and return L = D L_S (G = L L^T),
+// D_ii the power of two just below sqrt(G_ii) (S_ii in [1, 4)): exact, and within a factor
+// of 4 of the optimal diagonal preconditioner (van der Sluis). Otherwise D = I and the factor
+// is the plain one.
 // Both factorisations run in one CTA with the matrix in shared memory
 // (right-looking, one column per step, the trailing update on a 32 x 32 thread
 // grid without index division). The inverse R^{-1} = (L^{-1})^T is spread over
@@ -22,6 +22,11 @@ namespace scsf {
 namespace {
 
 __host__ __device__ __forceinline__ int odd_stride(int k) { return (k % 2 == 0) ? k + 1 : k; }
+
+// A positive finite diagonal entry outside [2^-100, 2^100] switches the scaling on.
+__device__ __forceinline__ bool chol_out_of_range(double g) {
+  return g > 0.0 && g < INFINITY && (g < 0x1p-100 || g > 0x1p100);
+}
 
 // Scale of row / column i: 2^floor(e / 2) for G_ii = m 2^e (m in [1, 2)), or 1 for a
 // diagonal that is not positive and finite (the pivot then fails and the shifted restart
@@ -48,8 +53,14 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
   __shared__ int bad;
   __shared__ double trace;
   __shared__ double sc[kSmallBlockWidth];
+  __shared__ int scaled;
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-  for (int i = t; i < k; i += 1024) sc[i] = chol_scale(G[(size_t)i * ldg + i]);
+  if (t == 0) scaled = 0;
+  __syncthreads();
+  for (int i = t; i < k; i += 1024)
+    if (chol_out_of_range(G[(size_t)i * ldg + i])) scaled = 1;
+  __syncthreads();
+  for (int i = t; i < k; i += 1024) sc[i] = scaled ? chol_scale(G[(size_t)i * ldg + i]) : 1.0;
   __syncthreads();
   if (t == 0) {
     double tr = 0.0;
@@ -250,13 +261,20 @@ __global__ void chol_store_kernel(int k, const T* __restrict__ M, const double* 
   L[e] = (j <= i) ? (double)M[e] * sc[i] : 0.0;
 }
 
-// Row scales sc[i] (chol_scale of G_ii) and trace(D^-1 G D^-1) into *out.
+// Row scales sc[i] (chol_scale of G_ii when any diagonal entry is out of range, else 1) and
+// trace(D^-1 G D^-1) into *out. One CTA.
 __global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg,
                                   double* __restrict__ sc, double* out) {
   __shared__ double red[256];
+  __shared__ int scaled;
+  if (threadIdx.x == 0) scaled = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (chol_out_of_range(G[(size_t)i * ldg + i])) scaled = 1;
+  __syncthreads();
   double s = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double g = G[(size_t)i * ldg + i], d = chol_scale(g);
+    const double g = G[(size_t)i * ldg + i], d = scaled ? chol_scale(g) : 1.0;
     sc[i] = d;
     s += fabs(g) / (d * d);
   }
