@@ -253,7 +253,9 @@ size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows);
  *            its largest-magnitude entry, lowest row on ties, is positive) or NULL
  *   stats  : host pointer or NULL
  *   On SCSF_ERR_NOT_CONVERGED the locked pairs come first, the other
- *   eigenvalue slots hold NaN, and the warm start is kept for the next step. */
+ *   eigenvalue slots hold NaN, and the warm start is kept for the next step.
+ *   An operator with a NaN or Inf coefficient (SCSF_OP_PLATE: also rho <= 0) is rejected
+ *   with SCSF_ERR_INVALID_ARG before any iteration (its Gershgorin bounds are not finite). */
 typedef struct scsf_chain scsf_chain;
 scsf_status scsf_chain_create(scsf_ctx* ctx, const scsf_params* params, int n,
                               void* workspace, size_t workspace_bytes, scsf_chain** out);
@@ -350,8 +352,8 @@ scsf_status scsf_proposal_prolong(scsf_ctx* ctx, const float* block, int batch, 
  *   X, Y: [N][ncols] FP64 with leading dimensions ldx, ldy (>= ncols);
  *   scratch: device, >= 8 (2 N ncols + 3 N + 4096) + 8192 bytes, plus 4 (14 N + 1) + 104 N
  *   for SCSF_OP_PLATE. X and Y must not overlap.
- * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}); scratch as for
- *   scsf_cheb_filter with ncols = 0.
+ * scsf_assemble_bounds: Gershgorin bounds of A (host out[2] = {lo, hi}; NaN or Inf when a
+ *   coefficient is not finite); scratch as for scsf_cheb_filter with ncols = 0.
  * scsf_cholqr2: Q = X R^{-1} with X = Q R (Alg. 3, orthonormalisation) by Cholesky QR2:
  *   G = X^T X, R1 from the Cholesky factor of D^-1 G D^-1 (D = diag(G)^(1/2)) taken in
  *   FP32, Q1 = X R1^{-1}; then the same in FP64 on Q1. Shifted restarts on a failed pivot;

@@ -729,6 +729,10 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));
   const double lo = h[0], hi = h[1];
+  // the bounds kernels keep a NaN, and an infinite coefficient makes hi infinite
+  if (!std::isfinite(lo) || !std::isfinite(hi))
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "operator has non-finite coefficients (NaN or Inf; for the plate, rho <= 0)");
   const double beta = hi;
   double lam, alpha;
   if (!ch->has_block) {  // head of the chain: random block (Sec. 3.2)

@@ -9,6 +9,16 @@
 namespace scsf {
 namespace {
 
+// min / max that keep a NaN (fmin / fmax drop one), so a non-finite operator coefficient
+// reaches the Gershgorin bounds, where the chain rejects the operator.
+__device__ __forceinline__ double nan_min(double a, double b) {
+  return (isnan(a) || isnan(b)) ? a + b : fmin(a, b);
+}
+__device__ __forceinline__ double nan_max(double a, double b) {
+  return (isnan(a) || isnan(b)) ? a + b : fmax(a, b);
+}
+
+
 constexpr int kAsmThreads = 256;
 constexpr int kRowsPerBlock = 8;   // nodes per CTA in the stencil kernels (blockDim.y)
 constexpr int kMaxColChunks = kSmallBlockWidth / 32;  // per column slice (blockIdx.y)
@@ -43,8 +53,8 @@ __global__ void assemble_kernel(int kind, int n, const double* __restrict__ ax,
     we[I] = cE;
     wn[I] = cN;
     const double radius = cE + cW + cN + cS;
-    lo = fmin(lo, dI - radius);
-    hi = fmax(hi, dI + radius);
+    lo = nan_min(lo, dI - radius);
+    hi = nan_max(hi, dI + radius);
   }
   __shared__ double slo[kAsmThreads], shi[kAsmThreads];
   slo[threadIdx.x] = lo;
@@ -52,8 +62,8 @@ __global__ void assemble_kernel(int kind, int n, const double* __restrict__ ax,
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
-      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      slo[threadIdx.x] = nan_min(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = nan_max(shi[threadIdx.x], shi[threadIdx.x + s]);
     }
     __syncthreads();
   }
@@ -68,16 +78,16 @@ __global__ void bounds_reduce_kernel(const double* __restrict__ partials, int nb
   __shared__ double slo[256], shi[256];
   double lo = INFINITY, hi = -INFINITY;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    lo = fmin(lo, partials[b]);
-    hi = fmax(hi, partials[nb + b]);
+    lo = nan_min(lo, partials[b]);
+    hi = nan_max(hi, partials[nb + b]);
   }
   slo[threadIdx.x] = lo;
   shi[threadIdx.x] = hi;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
-      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      slo[threadIdx.x] = nan_min(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = nan_max(shi[threadIdx.x], shi[threadIdx.x + s]);
     }
     __syncthreads();
   }
@@ -98,8 +108,8 @@ __global__ void csr_bounds_kernel(int rows, const int* __restrict__ rp, const in
       if (ci[p] == I) dI += val[p];
       else radius += fabs(val[p]);
     }
-    lo = fmin(lo, dI - radius);
-    hi = fmax(hi, dI + radius);
+    lo = nan_min(lo, dI - radius);
+    hi = nan_max(hi, dI + radius);
   }
   __shared__ double slo[kAsmThreads], shi[kAsmThreads];
   slo[threadIdx.x] = lo;
@@ -107,8 +117,8 @@ __global__ void csr_bounds_kernel(int rows, const int* __restrict__ rp, const in
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
-      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      slo[threadIdx.x] = nan_min(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = nan_max(shi[threadIdx.x], shi[threadIdx.x + s]);
     }
     __syncthreads();
   }

@@ -188,3 +188,26 @@ def test_eigenvector_sign_convention():
         idx = np.argmax(np.abs(V), axis=0)  # first maximum: lowest row on ties
         assert np.all(V[idx, np.arange(V.shape[1])] > 0)
         _check_result(op, ev[j], rs[j], V, 10)
+
+
+def test_non_finite_operator_coefficients_are_rejected():
+    """A NaN or Inf coefficient (or a plate density <= 0) reaches the Gershgorin bounds, and
+    the chain rejects the operator before iterating: SCSF_ERR_INVALID_ARG, in both forms."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    div = si.div_a_grad_chain(24, 1, seed=41)[0]
+    div.ax[3, 4] = np.nan
+    lapv = si.lap_plus_v_chain(24, 1, seed=42)[0]
+    lapv.V[0, 0] = np.inf
+    plate = si.plate_chain(24, 1, seed=43)[0]
+    plate.rho[2, 2] = -1.0
+    csr = si.knn_graph_chain(500, 1, seed=44)[0]
+    csr.val[5] = np.nan
+    cases = [(div, scsf.MIXED), (div, scsf.FP64), (lapv, scsf.FP64), (plate, scsf.FP64),
+             (csr, scsf.FP64)]
+    for op, prec in cases:
+        with pytest.raises(scsf.ScsfError) as err:
+            scsf.solve(to_dev([op], dev), scsf.Params(k=8, nex=4, degree=8, precision=prec))
+        assert err.value.status == scsf.ERR_INVALID_ARG
+    lo, hi = scsf.assemble_bounds(to_dev([div], dev)[0])
+    assert np.isnan(lo) or np.isnan(hi)
