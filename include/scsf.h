@@ -124,7 +124,8 @@ scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops
  * SCSF_OP_PLATE: thin-plate vibration div(grad(D lap u)) = lambda rho u (App. D.2 item 4)
  *   on the n x n grid, simply supported (u = 0 and D lap u = 0 on the boundary):
  *   K = L diag(D) L with L = -Lap_h (the 5-point Dirichlet Laplacian), M = diag(rho).
- *   plate_d, plate_rho: [n][n] FP64 at the nodes, rho > 0. The solver works on the
+ *   plate_d, plate_rho: [n][n] FP64 at the nodes, rho > 0; 2 <= n <= 12851 (13 n^2 CSR
+ *   slots indexed in int32). The solver works on the
  *   symmetric standard form C = M^{-1/2} K M^{-1/2} (13-point, assembled on the device into
  *   the chain's workspace): evals are the generalized eigenvalues, resid the relative
  *   residuals of C, and evecs the M-orthonormal modes u = M^{-1/2} v (u^T M u = 1), signed

@@ -94,7 +94,8 @@ bool op_ok(const scsf_operator* op) {
   if (op->kind == SCSF_OP_CSR)
     return op->rows >= 1 && op->rows <= kMaxCsrRows && op->row_ptr && op->col && op->val;
   if (op->n < 2) return false;
-  if (op->kind == SCSF_OP_PLATE) return op->plate_d && op->plate_rho;
+  if (op->kind == SCSF_OP_PLATE)  // 13 CSR slots a row, indexed in int32
+    return op->plate_d && op->plate_rho && 13LL * op->n * op->n < 0x7fffffffLL;
   if (op->kind == SCSF_OP_DIV_A_GRAD) return op->ax && op->ay;
   if (op->kind == SCSF_OP_LAP_PLUS_V) return op->v != nullptr;
   return false;
