@@ -142,7 +142,7 @@ typedef enum {
 
 typedef struct {
   int kind;          /* scsf_op_kind                           */
-  int n;             /* interior grid side, N = n*n (stencils) */
+  int n;             /* interior grid side, N = n*n (stencils), 2 <= n <= 46340 */
   const double* ax;
   const double* ay;
   const double* v;

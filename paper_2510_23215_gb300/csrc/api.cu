@@ -93,7 +93,7 @@ bool op_ok(const scsf_operator* op) {
   if (!op) return false;
   if (op->kind == SCSF_OP_CSR)
     return op->rows >= 1 && op->rows <= kMaxCsrRows && op->row_ptr && op->col && op->val;
-  if (op->n < 2) return false;
+  if (op->n < 2 || op->n > 46340) return false;  // N = n^2 is indexed in int32
   if (op->kind == SCSF_OP_PLATE)  // 13 CSR slots a row, indexed in int32
     return op->plate_d && op->plate_rho && 13LL * op->n * op->n < 0x7fffffffLL;
   if (op->kind == SCSF_OP_DIV_A_GRAD) return op->ax && op->ay;
@@ -625,6 +625,7 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "need 1 <= k and k + nex <= " + std::to_string(kMaxBlockWidth));
   if (N < kb) return fail(ctx, SCSF_ERR_INVALID_ARG, "operator too small for the block width");
+  if (N > 0x7fffffffLL) return fail(ctx, SCSF_ERR_INVALID_ARG, "N = n^2 must stay below 2^31");
   if (params->degree < 1 || !(params->tol > 0.0) || params->max_iter < 1)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need degree >= 1, tol > 0, max_iter >= 1");
   if (params->precision != SCSF_FP64 && params->precision != SCSF_MIXED)
