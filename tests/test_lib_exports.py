@@ -48,6 +48,22 @@ def test_workspace_queries_without_gpu():
     too_big = scsf.Params(k=430)._c()  # k_b = 516 > 512
     assert L.scsf_solve_workspace_size(ctypes.byref(too_big), 128) == 0
     assert L.scsf_sort_workspace_size(200, 8) >= 200 * 8 * 8 * 16
+    # FP64 stencil chains also hold the thin plate's 13-slot CSR form (4 N + 156 N bytes)
+    ws_f64 = L.scsf_solve_workspace_size(ctypes.byref(p), 128)
+    mixed = scsf.Params(k=100, degree=20, precision=scsf.MIXED)._c()
+    assert ws_f64 >= 4 * 128 * 128 * 120 * 8 + 160 * 128 * 128
+    assert L.scsf_solve_workspace_size(ctypes.byref(mixed), 128) > 0
+    # CSR chains: FP64 only, sized by rows, no stencil-side plate buffers
+    rows = L.scsf_solve_workspace_size_rows(ctypes.byref(p), 128 * 128)
+    assert 4 * 128 * 128 * 120 * 8 <= rows < ws_f64
+    assert L.scsf_solve_workspace_size_rows(ctypes.byref(mixed), 128 * 128) == 0
+    assert L.scsf_solve_workspace_size_rows(ctypes.byref(p), 0) == 0
+    assert L.scsf_solve_workspace_size_rows(ctypes.byref(p), 1 << 31) == 0
+    # Cholesky QR2 building block: 1 <= ncols <= min(rows, 512)
+    assert L.scsf_cholqr2_scratch(5000, 120) >= 5000 * 120 * 8 + 3 * 120 * 120 * 8
+    assert L.scsf_cholqr2_scratch(3001, 200) > L.scsf_cholqr2_scratch(3001, 160)
+    assert L.scsf_cholqr2_scratch(100, 101) == 0
+    assert L.scsf_cholqr2_scratch(1000, 513) == 0
 
 
 def test_context_creation_fails_loudly_without_gpu():
