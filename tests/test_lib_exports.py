@@ -73,3 +73,28 @@ def test_context_creation_fails_loudly_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         scsf.Context(0)
+
+
+def test_operator_descriptors_refuse_host_tensors_and_bad_shapes():
+    """Every operator kind's descriptor is built from CUDA tensors only (no CPU path), and
+    the binding checks shapes and dtypes before any call."""
+    import torch
+    import paper_2510_23215_gb300 as scsf
+    import scsf_inputs as si
+    csr = scsf.Operator.csr([0, 1, 2], [0, 1], [1.0, 2.0], device="cpu")
+    assert csr.N == 2 and csr.row_ptr.dtype == torch.int32
+    with pytest.raises(ValueError, match="CUDA"):
+        csr._c()
+    plate = scsf.Operator.from_workload(si.constant_plate(4), "cpu")
+    assert plate.kind == scsf.PLATE and plate.N == 16
+    with pytest.raises(ValueError, match="CUDA"):
+        plate._c()
+    stencil = scsf.Operator.from_workload(si.constant_div_a_grad(4), "cpu")
+    with pytest.raises(ValueError, match="CUDA"):
+        stencil._c()
+    bad = scsf.Operator(scsf.PLATE, 4, D=torch.zeros((4, 4), dtype=torch.float32),
+                        rho=torch.ones((4, 4), dtype=torch.float64))
+    with pytest.raises(TypeError):
+        bad._c()
+    with pytest.raises(ValueError):
+        scsf.Operator(99, 4)._c()
