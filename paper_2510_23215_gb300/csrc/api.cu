@@ -1,8 +1,8 @@
 // C ABI of the SCSF library: contexts, the sort entry point, and the chain
-// driver that runs Chebyshev filtered subspace iteration (Alg. 3) on each
+// loop that runs Chebyshev filtered subspace iteration (Alg. 3) on each
 // problem of a sorted sequence, warm-started from the previous problem.
 //
-// The driver is host code issuing stream-ordered kernels; the only device ->
+// The loop is host code issuing stream-ordered kernels; the only device ->
 // host traffic per outer iteration is the Ritz values and residual norms of
 // the active block (2-3 k_b doubles), which decide locking and termination.
 #include <algorithm>

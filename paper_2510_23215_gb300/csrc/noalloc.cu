@@ -3,7 +3,7 @@
 // Some callers cannot call cudaMalloc (or any allocating routine) at the point
 // where they need the sort: for example code running inside a host framework
 // that owns every byte of device memory through its own fixed-budget pool, or
-// a latency-critical loop that must not enter the driver's allocator. For them
+// a latency-critical loop that must not enter the CUDA allocator. For them
 // this entry point keeps its scratch (the truncated-DFT features and the
 // visited flags) in a file-scope device array instead of a caller workspace.
 // The array is reserved on every GPU that loads the library and stays there
