@@ -164,6 +164,19 @@ typedef struct {
  * Both forms: 1 <= k_b = k + nex <= scsf_max_block_width() (512) and k_b <= N. */
 typedef enum { SCSF_FP64 = 0, SCSF_MIXED = 1 } scsf_precision;
 
+/* How the tall block products of Alg. 3 are computed: the Gram matrices X^T X of the
+ * Cholesky QR (orthonormalisation step), the Rayleigh-Ritz matrix Q^T (A Q), the rotation
+ * X = Q Z and the triangular solve X R^{-1}, plus the deflation products against locked
+ * columns. The paper forms them in FP64 on CPU cores.
+ * SCSF_PRODUCT_TENSOR (default): on the tcgen05 tensor cores from BF16 digit planes with
+ *   exact FP32 accumulation (the error-free splitting of Ozaki, Ogita and Oishi; 8 base-128
+ *   digits per operand for FP64-phase products, an error of about 2^-55 of |a_i| |b_j| per
+ *   term, on a par with FP64 arithmetic; 4 digits for the mixed form's FP32 phase).
+ *   Results do not depend on the summation order (integer sums, one final rounding).
+ * SCSF_PRODUCT_FP64: FP64 (and, in the FP32 phase, FP32) fused multiply-adds on the CUDA
+ *   cores. */
+typedef enum { SCSF_PRODUCT_TENSOR = 0, SCSF_PRODUCT_FP64 = 1 } scsf_product_method;
+
 typedef struct {
   int k;             /* wanted eigenpairs (L in the paper), >= 1                          */
   int nex;           /* extra block columns; < 0 selects ceil(0.2 k) (App. D.4)            */
@@ -175,6 +188,7 @@ typedef struct {
   int degree_fp32;   /* SCSF_MIXED: Chebyshev degree of the FP32 phase (<= 0: degree)     */
   double switch_tol; /* SCSF_MIXED: leave the FP32 phase once every wanted residual is at
                         or below this (> 0), besides the FP32-floor and stall rules       */
+  int products;      /* scsf_product_method of the block products                         */
 } scsf_params;
 
 typedef struct {
@@ -396,6 +410,29 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
  * Y FP64 [rows][n] (ldy), all device, Y must not overlap X or M; 1 <= k, n <= 512. */
 scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,
                               const double* M, int ldm, int n, double* Y, int ldy);
+/* Block products with a selectable method (scsf_product_method; see scsf_params.products).
+ * scsf_block_gram: C = A^T B (Alg. 3: the Gram matrix X^T X of Cholesky QR, the
+ *   Rayleigh-Ritz matrix Q^T (A Q), the coefficients of deflation against locked columns).
+ *   A [rows][m] (lda), B [rows][n] (ldb), C [m][n] (ldc), FP64, device; symmetric != 0
+ *   promises that C is symmetric (m == n; A == B, or B = S A for a symmetric S): only
+ *   the upper half is formed and mirrored.
+ * scsf_block_rotate_ex: Y = alpha X M + beta Y (Alg. 3: the rotation X = Q Z, the
+ *   triangular solve X R^{-1} of Cholesky QR, the deflation update Y - V C).
+ *   X [rows][k] (ldx), M [k][n] (ldm), Y [rows][n] (ldy), FP64, device; Y must not
+ *   overlap X or M.
+ * Both: 1 <= m, n, k <= 512, 1 <= rows < 2^31; slices: digits per operand of the tensor
+ * method (4, 7 or 8; ignored by SCSF_PRODUCT_FP64); scratch: device, 256-byte aligned,
+ * >= scsf_block_product_scratch(rows, max width, slices) bytes. The call synchronises the
+ * context's stream and returns SCSF_ERR_TIMEOUT if a bounded wait inside the tensor-core
+ * kernel gave up (Y or C undefined then). */
+size_t scsf_block_product_scratch(int64_t rows, int kmax, int slices);
+scsf_status scsf_block_gram(scsf_ctx* ctx, const double* A, int lda, const double* B, int ldb,
+                            int rows, int m, int n, int symmetric, int method, int slices,
+                            double* C, int ldc, void* scratch, size_t scratch_bytes);
+scsf_status scsf_block_rotate_ex(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,
+                                 const double* M, int ldm, int n, double alpha, double beta,
+                                 int method, int slices, double* Y, int ldy, void* scratch,
+                                 size_t scratch_bytes);
 size_t scsf_small_eigh_scratch(int k);
 scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
                             void* scratch, size_t scratch_bytes);

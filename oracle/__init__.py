@@ -22,9 +22,11 @@ Subspace Filter"):
   pin the rest (App. C and the separable special cases).
 * ``inertia``    - Sylvester inertia count via banded LDL^T.
 * ``compare``    - eigenvalue / eigenspace comparisons used by tests.
+* ``products``   - correctly rounded block products A^T B and X M (the Gram,
+  Rayleigh-Ritz and rotation products of Alg. 3), for the tensor-core products.
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, worked examples and brute force, none of which reuse the function's
 own formula.
 """
-from . import operators, sort, chebyshev, chfsi, dense, sturm, inertia, compare  # noqa: F401
+from . import operators, sort, chebyshev, chfsi, dense, sturm, inertia, compare, products  # noqa: F401

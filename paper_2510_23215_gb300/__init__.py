@@ -25,6 +25,7 @@ __all__ = [
     "ScsfError", "Operator", "Params", "Context", "Chain", "library", "lib_path",
     "sort", "solve", "cheb_filter", "assemble_bounds", "small_eigh", "block_width",
     "FP64", "MIXED", "DIV_A_GRAD", "LAP_PLUS_V", "EXPORTED_SYMBOLS", "launch_count",
+    "PRODUCT_TENSOR", "PRODUCT_FP64", "block_gram", "block_rotate",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,6 +34,7 @@ lib_path = os.path.join(_HERE, "libscsf.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NO_MEMORY = range(7)
 DIV_A_GRAD, LAP_PLUS_V, CSR, PLATE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
+PRODUCT_TENSOR, PRODUCT_FP64 = 0, 1
 
 EXPORTED_SYMBOLS = [
     "scsf_create", "scsf_destroy", "scsf_last_error", "scsf_version",
@@ -48,6 +50,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_forward", "scsf_proposal_train_step", "scsf_proposal_target_scratch",
     "scsf_proposal_targets", "scsf_proposal_prolong",
     "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist", "scsf_block_rotate",
+    "scsf_block_product_scratch", "scsf_block_gram", "scsf_block_rotate_ex",
 ]
 
 
@@ -68,7 +71,7 @@ class _CParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nex", ctypes.c_int), ("degree", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int),
-                ("switch_tol", ctypes.c_double)]
+                ("switch_tol", ctypes.c_double), ("products", ctypes.c_int)]
 
 
 class _CStats(ctypes.Structure):
@@ -178,6 +181,13 @@ def library() -> ctypes.CDLL:
     L.scsf_sort_noalloc_capacity.restype = sz
     L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
     L.scsf_sort_noalloc.restype = ctypes.c_int
+    L.scsf_block_product_scratch.argtypes = [i64, i32, i32]
+    L.scsf_block_product_scratch.restype = sz
+    L.scsf_block_gram.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, vp, sz]
+    L.scsf_block_gram.restype = ctypes.c_int
+    L.scsf_block_rotate_ex.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, dbl, dbl, i32, i32, vp,
+                                       i32, vp, sz]
+    L.scsf_block_rotate_ex.restype = ctypes.c_int
     for name in EXPORTED_SYMBOLS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int or name in (
@@ -299,10 +309,12 @@ class Params:
     seed: int = 0
     degree_fp32: int = 0   # MIXED: degree of the FP32 phase (0: same as degree)
     switch_tol: float = 0.0  # MIXED: leave the FP32 phase at this wanted residual (0: off)
+    products: int = PRODUCT_TENSOR  # block products on the tensor cores (or PRODUCT_FP64)
 
     def _c(self) -> _CParams:
         return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
-                        self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32, self.switch_tol)
+                        self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32, self.switch_tol,
+                        self.products)
 
     @property
     def kb(self) -> int:
@@ -487,6 +499,57 @@ class Chain:
             pass
 
 
+def _product_scratch(rows: int, kmax: int, slices: int, device) -> torch.Tensor:
+    nbytes = library().scsf_block_product_scratch(rows, kmax, slices)
+    if nbytes == 0:
+        raise ValueError("unsupported product sizes")
+    return _workspace(nbytes, device)
+
+
+def block_gram(A: torch.Tensor, B: Optional[torch.Tensor] = None, symmetric: bool = False,
+               method: int = PRODUCT_TENSOR, slices: int = 8,
+               ctx: Optional[Context] = None) -> torch.Tensor:
+    """C = A^T B (FP64 [rows, m] and [rows, n] device tensors; B = A when omitted) by
+    scsf_block_gram: on the tensor cores (digit split, `slices` digits) or the FP64 pipe."""
+    B = A if B is None else B
+    _check(A, "A")
+    _check(B, "B", device=A.device)
+    if A.dim() != 2 or B.dim() != 2 or A.shape[0] != B.shape[0]:
+        raise ValueError("A and B must be [rows, m] and [rows, n]")
+    c = _ctx(ctx, A.device)
+    rows, m, n = int(A.shape[0]), int(A.shape[1]), int(B.shape[1])
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    ws = _product_scratch(rows, max(m, n), slices, A.device)
+    c.check(library().scsf_block_gram(c.handle, A.data_ptr(), m, B.data_ptr(), n, rows, m, n,
+                                      1 if symmetric else 0, method, slices, C.data_ptr(), n,
+                                      ws.data_ptr(), ws.numel()))
+    return C
+
+
+def block_rotate(X: torch.Tensor, M: torch.Tensor, Y: Optional[torch.Tensor] = None,
+                 alpha: float = 1.0, beta: float = 0.0, method: int = PRODUCT_TENSOR,
+                 slices: int = 8, ctx: Optional[Context] = None) -> torch.Tensor:
+    """Y = alpha X M + beta Y (FP64 [rows, k], [k, n], [rows, n]) by scsf_block_rotate_ex."""
+    _check(X, "X")
+    _check(M, "M", device=X.device)
+    if X.dim() != 2 or M.dim() != 2 or X.shape[1] != M.shape[0]:
+        raise ValueError("X must be [rows, k] and M [k, n]")
+    rows, k, n = int(X.shape[0]), int(X.shape[1]), int(M.shape[1])
+    if Y is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs Y")
+        Y = torch.empty((rows, n), dtype=torch.float64, device=X.device)
+    _check(Y, "Y", device=X.device)
+    if tuple(Y.shape) != (rows, n):
+        raise ValueError("Y must be [rows, n]")
+    c = _ctx(ctx, X.device)
+    ws = _product_scratch(rows, max(k, n), slices, X.device)
+    c.check(library().scsf_block_rotate_ex(c.handle, X.data_ptr(), k, rows, k, M.data_ptr(), n, n,
+                                           alpha, beta, method, slices, Y.data_ptr(), n,
+                                           ws.data_ptr(), ws.numel()))
+    return Y
+
+
 def solve(ops: List[Operator], params: Params, want_vectors: bool = False,
           ctx: Optional[Context] = None):
     """scsf_solve over ops (already in solve order). Returns (evals, resid, evecs|None, stats)."""
@@ -612,8 +675,8 @@ def cheb_filter_dc(op: Operator, X: torch.Tensor, theta: torch.Tensor, degree: i
     return Y
 
 
-def block_rotate(X: torch.Tensor, M: torch.Tensor, ctx: Optional[Context] = None) -> torch.Tensor:
-    """Y = X M (FP64): the rotation of Alg. 3 as a building block."""
+def block_rotate_fp64(X: torch.Tensor, M: torch.Tensor, ctx: Optional[Context] = None) -> torch.Tensor:
+    """Y = X M on the FP64 pipe (scsf_block_rotate): the rotation of Alg. 3 as a building block."""
     _check(X, "X")
     _check(M, "M")
     if X.dim() != 2 or M.dim() != 2 or X.shape[1] != M.shape[0]:

@@ -136,10 +136,14 @@ struct ChainBufs {
   // FP64 stencil chains: the thin-plate operator assembled as CSR (13 slots a row)
   int *prp, *pci;
   double* pval;
+  // tensor-core block products: digit planes, exponents and exact split partials
+  void* oz;
+  size_t oz_bytes;
 };
 
 template <typename Cv>
-void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, ChainBufs& b) {
+void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, bool tensor,
+                 ChainBufs& b) {
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
   const int T = (kb + kGemmTile - 1) / kGemmTile;
@@ -165,6 +169,12 @@ void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, Ch
   b.chol_wide = (kb > kSmallBlockWidth) ? c.template take<char>(chol_wide_scratch_bytes(kb)) : nullptr;
   b.status = c.template take<int>(4);
   b.cols = c.template take<int>(kb);
+  b.oz = nullptr;
+  b.oz_bytes = 0;
+  if (tensor) {
+    b.oz_bytes = oz_scratch_bytes((int)N, kb, kOzSlicesF64);
+    b.oz = c.template take<char>(b.oz_bytes);
+  }
   b.prp = b.pci = nullptr;
   b.pval = nullptr;
   if (plate) {
@@ -596,7 +606,8 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   SizeCarve c;
   ChainBufs b;
   const bool mixed = params->precision == SCSF_MIXED;
-  carve_chain(c, (size_t)n_max * n_max, kb, mixed, params->degree, !mixed, b);
+  carve_chain(c, (size_t)n_max * n_max, kb, mixed, params->degree, !mixed,
+              params->products == SCSF_PRODUCT_TENSOR, b);
   return c.used;
 }
 
@@ -606,7 +617,8 @@ size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows) {
   if (kb < 1 || kb > kMaxBlockWidth) return 0;
   SizeCarve c;
   ChainBufs b;
-  carve_chain(c, (size_t)rows, kb, false, params->degree, false, b);
+  carve_chain(c, (size_t)rows, kb, false, params->degree, false,
+              params->products == SCSF_PRODUCT_TENSOR, b);
   return c.used;
 }
 
@@ -630,6 +642,9 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need degree >= 1, tol > 0, max_iter >= 1");
   if (params->precision != SCSF_FP64 && params->precision != SCSF_MIXED)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "precision must be SCSF_FP64 or SCSF_MIXED");
+  if (params->products != SCSF_PRODUCT_TENSOR && params->products != SCSF_PRODUCT_FP64)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "products must be SCSF_PRODUCT_TENSOR or SCSF_PRODUCT_FP64");
   if (params->precision == SCSF_MIXED && n == 0)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "SCSF_MIXED needs a stencil operator (its FP32 filters are stencil kernels)");
@@ -647,7 +662,8 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
   ch->kb = kb;
   Carve c(workspace, workspace_bytes);
   const bool mixed = params->precision == SCSF_MIXED;
-  carve_chain(c, (size_t)N, kb, mixed, params->degree, n > 0 && !mixed, ch->b);
+  carve_chain(c, (size_t)N, kb, mixed, params->degree, n > 0 && !mixed,
+              params->products == SCSF_PRODUCT_TENSOR, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -784,6 +800,35 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   int dc_steps = 0;
   double dc_elems = 0.0, t_filter_dc = 0.0;
 
+  // the tall block products (rows = N): tensor-core digit-split products or CUDA-core FMAs
+  const bool tc = ch->p.products == SCSF_PRODUCT_TENSOR;
+  int* oz_err = b.status + 2;  // set by a tensor-core product whose bounded wait gave up
+  if (tc) SCSF_CUDA(ctx, cudaMemsetAsync(oz_err, 0, sizeof(int), st));
+  auto tn64 = [&](int m_, int n_, const double* A_, int lda_, const double* B_, int ldb_,
+                  double* C_, int ldc_, bool sym_) -> cudaError_t {
+    return tc ? launch_gemm_tn_oz(N, m_, n_, A_, lda_, B_, ldb_, C_, ldc_, sym_, kOzSlicesF64,
+                                  b.oz, b.oz_bytes, oz_err, st)
+              : launch_gemm_tn(N, m_, n_, A_, lda_, B_, ldb_, C_, ldc_, sym_, b.gemm_partials, st);
+  };
+  auto nn64 = [&](int k_, int n_, double al, const double* A_, int lda_, const double* M_,
+                  int ldm_, double be, double* C_, int ldc_, bool upper_) -> cudaError_t {
+    return tc ? launch_gemm_nn_oz(N, k_, n_, al, A_, lda_, M_, ldm_, be, C_, ldc_, kOzSlicesF64,
+                                  b.oz, b.oz_bytes, oz_err, st)
+              : launch_gemm_nn(N, k_, n_, al, A_, lda_, M_, ldm_, be, C_, ldc_, upper_, st);
+  };
+  auto tn32 = [&](int m_, int n_, const float* A_, int lda_, const float* B_, int ldb_,
+                  double* C_, int ldc_, bool sym_) -> cudaError_t {
+    return tc ? launch_gemm_tn_oz_f32(N, m_, n_, A_, lda_, B_, ldb_, C_, ldc_, sym_, b.oz,
+                                      b.oz_bytes, oz_err, st)
+              : launch_gemm_tn_f32(N, m_, n_, A_, lda_, B_, ldb_, C_, ldc_, sym_, b.partials32, st);
+  };
+  auto nn32 = [&](int k_, int n_, float al, const float* A_, int lda_, const double* M_, int ldm_,
+                  float be, float* C_, int ldc_, bool upper_) -> cudaError_t {
+    return tc ? launch_gemm_nn_oz_f32(N, k_, n_, al, A_, lda_, M_, ldm_, be, C_, ldc_, b.oz,
+                                      b.oz_bytes, oz_err, st)
+              : launch_gemm_nn_f32(N, k_, n_, al, A_, lda_, M_, ldm_, be, C_, ldc_, upper_, st);
+  };
+
   // FP32 phase of the mixed form: the whole block iterates in FP32 (filter, Cholesky
   // QR, Rayleigh-Ritz, rotation) without locking, until the wanted residuals stop
   // improving, i.e. the subspace has converged to FP32 accuracy. FP32 storage floors
@@ -812,27 +857,35 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       float* F1 = b.B32[(which + 1) % 3];
       float* F2 = b.B32[(which + 2) % 3];
       for (int pass = 0; pass < 2; ++pass) {
-        SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, Y, kb, b.G, kb, true, b.partials32, st));
+        SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, Y, kb, b.G, kb, true));
         SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + pass, st,
                                         b.chol_wide));
-        SCSF_CUDA(ctx, launch_gemm_nn_f32(N, kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true, st));
+        SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true));
         std::swap(Y, F1);
       }
       SCSF_CUDA(ctx, mark(2));
       SCSF_CUDA(ctx, launch_cheb_step_f32(A32, Y, kb, nullptr, 0, F2, kb, kb, 1.f, 0.f, 0.f, st));
       // Q^T (A Q) is symmetric (A is): only its upper tiles are formed, then mirrored
-      SCSF_CUDA(ctx, launch_gemm_tn_f32(N, kb, kb, Y, kb, F2, kb, b.H, kb, true, b.partials32, st));
+      SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, F2, kb, b.H, kb, true));
       SCSF_CUDA(ctx, mark(3));
       SCSF_CUDA(ctx, launch_small_eigh_f32(kb, b.H, kb, b.theta, b.Z, kb, b.eigh_scratch, st));
       SCSF_CUDA(ctx, mark(4));
-      SCSF_CUDA(ctx, launch_gemm_nn_f32(N, kb, kb, 1.f, Y, kb, b.Z, kb, 0.f, b.V32, kb, false, st));
+      SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Z, kb, 0.f, b.V32, kb, false));
       SCSF_CUDA(ctx, mark(5));
       SCSF_CUDA(ctx, launch_residual_norms_f32(A32, b.V32, kb, kb, b.theta, b.res_partials, b.res2, st));
       SCSF_CUDA(ctx, mark(6));
       SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, kb * sizeof(double), cudaMemcpyDeviceToHost, st));
       SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * kb * sizeof(double),
                                      cudaMemcpyDeviceToHost, st));
+      SCSF_CUDA(ctx, cudaMemcpyAsync(h + 3 * kMaxBlockWidth, b.status, 3 * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
       SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+      {
+        int st3[3];
+        std::memcpy(st3, h + 3 * kMaxBlockWidth, sizeof(st3));
+        if (tc && st3[2] != 0)
+          return fail(ctx, SCSF_ERR_TIMEOUT, "a tensor-core block product gave up waiting");
+      }
       if (timing) {
         float ms = 0.f;
         SCSF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
@@ -919,30 +972,30 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       // the defect-corrected filter already took the first pass (in FP32, on Z)
       const int passes = dc ? 1 : 2;
       for (int pass = 0; pass < passes; ++pass) {
-        SCSF_CUDA(ctx, launch_gemm_tn(N, nl, ka, b.V, kb, Y, kb, b.C, ka, false, b.gemm_partials, st));
-        SCSF_CUDA(ctx, launch_gemm_nn(N, nl, ka, -1.0, b.V, kb, b.C, ka, 1.0, Y, kb, false, st));
+        SCSF_CUDA(ctx, tn64(nl, ka, b.V, kb, Y, kb, b.C, ka, false));
+        SCSF_CUDA(ctx, nn64(nl, ka, -1.0, b.V, kb, b.C, ka, 1.0, Y, kb, false));
       }
       flops += 4.0 * passes * N * nl * ka;
     }
     if (!mixed) {
       for (int pass = 0; pass < 2; ++pass) {
-        SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+        SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, Y, kb, b.G, ka, true));
         // the first factor only has to precondition, so it is taken in FP32
         SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, pass == 0 && fp32_first, b.C, b.Rinv,
                                         b.status + pass, st, b.chol_wide));
-        SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
+        SCSF_CUDA(ctx, nn64(ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true));
         std::swap(Y, F1);
         flops += 2.0 * N * ka * ka;
       }
       SCSF_CUDA(ctx, mark(2));
       // Rayleigh quotient G = Q^T A Q on the active columns
       SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, true, b.gemm_partials, st));
+      SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, F2, kb, b.H, ka, true));
       SCSF_CUDA(ctx, mark(3));
       // reduced eigenproblem and rotation back
       SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
       SCSF_CUDA(ctx, mark(4));
-      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false, st));
+      SCSF_CUDA(ctx, nn64(ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false));
       SCSF_CUDA(ctx, mark(5));
     } else {
       // Mixed form: the same Cholesky QR2, Rayleigh-Ritz and rotation with two FP64 block
@@ -952,22 +1005,21 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       // as with Q = Q1 R2^{-1}.
       if (fp32_first) {
         SCSF_CUDA(ctx, launch_block_f64_to_f32(N, ka, Y, kb, b.B32[0], kb, st));
-        SCSF_CUDA(ctx, launch_gemm_tn_f32(N, ka, ka, b.B32[0], kb, b.B32[0], kb, b.G, ka, true,
-                                          b.partials32, st));
+        SCSF_CUDA(ctx, tn32(ka, ka, b.B32[0], kb, b.B32[0], kb, b.G, ka, true));
       } else {
-        SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+        SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, Y, kb, b.G, ka, true));
       }
       SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, fp32_first, b.C, b.Rinv, b.status, st,
                                       b.chol_wide));
-      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true, st));
+      SCSF_CUDA(ctx, nn64(ka, ka, 1.0, Y, kb, b.Rinv, ka, 0.0, F1, kb, true));
       std::swap(Y, F1);  // Y = Q1
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, Y, kb, b.G, ka, true, b.gemm_partials, st));
+      SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, Y, kb, b.G, ka, true));
       SCSF_CUDA(ctx, launch_chol_rinv(ka, b.G, ka, false, b.C, b.Rinv, b.status + 1, st,
                                       b.chol_wide));
       flops += 1.5 * N * ka * ka;
       SCSF_CUDA(ctx, mark(2));
       SCSF_CUDA(ctx, launch_cheb_step_f64(A, Y, kb, nullptr, 0, F2, kb, ka, 1.0, 0.0, 0.0, st));
-      SCSF_CUDA(ctx, launch_gemm_tn(N, ka, ka, Y, kb, F2, kb, b.H, ka, true, b.gemm_partials, st));
+      SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, F2, kb, b.H, ka, true));
       // H = R2^{-T} (H1 R2^{-1}) with T = H1 R2^{-1} in b.G
       SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.H, ka, b.Rinv, ka, 0.0, b.G, ka, true, st));
       SCSF_CUDA(ctx, launch_gemm_tn(ka, ka, ka, b.Rinv, ka, b.G, ka, b.H, ka, false, b.gemm_partials,
@@ -977,7 +1029,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       SCSF_CUDA(ctx, mark(4));
       // X = Q1 M, M = R2^{-1} Z in b.C
       SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.Rinv, ka, b.Z, ka, 0.0, b.C, ka, false, st));
-      SCSF_CUDA(ctx, launch_gemm_nn(N, ka, ka, 1.0, Y, kb, b.C, ka, 0.0, b.V + nl, kb, false, st));
+      SCSF_CUDA(ctx, nn64(ka, ka, 1.0, Y, kb, b.C, ka, 0.0, b.V + nl, kb, false));
       SCSF_CUDA(ctx, mark(5));
     }
     rot_launches += 1;
@@ -990,7 +1042,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.theta, ka * sizeof(double), cudaMemcpyDeviceToHost, st));
     SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * ka * sizeof(double),
                                    cudaMemcpyDeviceToHost, st));
-    SCSF_CUDA(ctx, cudaMemcpyAsync(h + 3 * kMaxBlockWidth, b.status, 2 * sizeof(int),
+    SCSF_CUDA(ctx, cudaMemcpyAsync(h + 3 * kMaxBlockWidth, b.status, 3 * sizeof(int),
                                    cudaMemcpyDeviceToHost, st));
     SCSF_CUDA(ctx, cudaStreamSynchronize(st));
     if (timing) {
@@ -1001,8 +1053,10 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
         else tms[i] += ms;
       }
     }
-    int chol_status[2];
+    int chol_status[3];
     std::memcpy(chol_status, h + 3 * kMaxBlockWidth, sizeof(chol_status));
+    if (tc && chol_status[2] != 0)
+      return fail(ctx, SCSF_ERR_TIMEOUT, "a tensor-core block product gave up waiting");
     // an FP32 first factor that needed a shift preconditions too weakly for one FP64 pass
     // to reach FP64 orthogonality: take the first factor in FP64 for the rest of this problem
     if (fp32_first && chol_status[0] > 0) fp32_first = false;
@@ -1317,6 +1371,101 @@ scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows,
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   SCSF_CUDA(ctx, launch_gemm_nn(rows, k, n, 1.0, X, ldx, M, ldm, 0.0, Y, ldy, false, ctx->stream));
   return SCSF_OK;
+}
+
+size_t scsf_block_product_scratch(int64_t rows, int kmax, int slices) {
+  if (rows < 1 || rows > 0x7fffffffLL || kmax < 1 || kmax > kMaxBlockWidth) return 0;
+  if (slices != 4 && slices != 7 && slices != 8) return 0;
+  const size_t fp64 = gemm_tn_partials((int)rows, kmax, kmax, false) * sizeof(double);
+  return 256 + std::max(fp64, oz_scratch_bytes((int)rows, kmax, slices));
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validates a product call and carves its error flag; returns SCSF_OK or the failure.
+scsf_status product_setup(scsf_ctx* ctx, int64_t rows, int w1, int w2, int method, int slices,
+                          void* scratch, size_t scratch_bytes, int** err, void** rest,
+                          size_t* rest_bytes) {
+  if (rows < 1 || rows > 0x7fffffffLL || w1 < 1 || w2 < 1 || w1 > kMaxBlockWidth ||
+      w2 > kMaxBlockWidth)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= rows < 2^31 and widths in [1, 512]");
+  if (method != SCSF_PRODUCT_TENSOR && method != SCSF_PRODUCT_FP64)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "method must be SCSF_PRODUCT_TENSOR or SCSF_PRODUCT_FP64");
+  if (method == SCSF_PRODUCT_TENSOR && slices != 4 && slices != 7 && slices != 8)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "slices must be 4, 7 or 8");
+  if (!scratch || reinterpret_cast<uintptr_t>(scratch) % 256 != 0)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "scratch must be a 256-byte aligned device buffer");
+  if (scratch_bytes < scsf_block_product_scratch(rows, std::max(w1, w2),
+                                                 method == SCSF_PRODUCT_TENSOR ? slices : 7))
+    return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch smaller than scsf_block_product_scratch()");
+  *err = static_cast<int*>(scratch);
+  *rest = static_cast<char*>(scratch) + 256;
+  *rest_bytes = scratch_bytes - 256;
+  return SCSF_OK;
+}
+
+scsf_status product_finish(scsf_ctx* ctx, int* err) {
+  int* h = reinterpret_cast<int*>(ctx->pinned);
+  SCSF_CUDA(ctx, cudaMemcpyAsync(h, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SCSF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[0] != 0) return fail(ctx, SCSF_ERR_TIMEOUT, "a tensor-core product gave up waiting");
+  return SCSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+scsf_status scsf_block_gram(scsf_ctx* ctx, const double* A, int lda, const double* B, int ldb,
+                            int rows, int m, int n, int symmetric, int method, int slices,
+                            double* C, int ldc, void* scratch, size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!A || !B || !C) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  int* err;
+  void* rest;
+  size_t rest_bytes;
+  scsf_status s = product_setup(ctx, rows, m, n, method, slices, scratch, scratch_bytes, &err,
+                                &rest, &rest_bytes);
+  if (s != SCSF_OK) return s;
+  if (lda < m || ldb < n || ldc < n || (symmetric && m != n))
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need lda >= m, ldb >= n, ldc >= n (symmetric: m == n)");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  SCSF_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  if (method == SCSF_PRODUCT_TENSOR)
+    SCSF_CUDA(ctx, launch_gemm_tn_oz(rows, m, n, A, lda, B, ldb, C, ldc, symmetric != 0, slices,
+                                     rest, rest_bytes, err, st));
+  else
+    SCSF_CUDA(ctx, launch_gemm_tn(rows, m, n, A, lda, B, ldb, C, ldc, symmetric != 0,
+                                  static_cast<double*>(rest), st));
+  return product_finish(ctx, err);
+}
+
+scsf_status scsf_block_rotate_ex(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,
+                                 const double* M, int ldm, int n, double alpha, double beta,
+                                 int method, int slices, double* Y, int ldy, void* scratch,
+                                 size_t scratch_bytes) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!X || !M || !Y) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  int* err;
+  void* rest;
+  size_t rest_bytes;
+  scsf_status s = product_setup(ctx, rows, k, n, method, slices, scratch, scratch_bytes, &err,
+                                &rest, &rest_bytes);
+  if (s != SCSF_OK) return s;
+  if (ldx < k || ldm < n || ldy < n)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "need ldx >= k, ldm >= n, ldy >= n");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  SCSF_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  if (method == SCSF_PRODUCT_TENSOR)
+    SCSF_CUDA(ctx, launch_gemm_nn_oz(rows, k, n, alpha, X, ldx, M, ldm, beta, Y, ldy, slices, rest,
+                                     rest_bytes, err, st));
+  else
+    SCSF_CUDA(ctx, launch_gemm_nn(rows, k, n, alpha, X, ldx, M, ldm, beta, Y, ldy, false, st));
+  return product_finish(ctx, err);
 }
 
 }  // extern "C"

@@ -158,6 +158,32 @@ cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float*
                                const double* M, int ldm, float beta, float* C, int ldc, bool upper,
                                cudaStream_t st);
 
+// ---- tensor-core split products (ozaki.cu) ----------------------------------
+// FP64-accurate A^T B and A M on tcgen05 tensor cores: operands cut into `slices` base-128
+// digit planes (BF16), exact FP32 accumulation per 64-row chunk, integer level sums, one
+// rounding to FP64 at the end. slices 8 for FP64-class products (7: ~10x the error), kOzSlicesF32 for
+// the FP32 phase. scratch: device, >= oz_scratch_bytes(rows, kmax, slices) for products
+// with rows rows and m, n, k <= kmax; 256-byte aligned. err: device int set to 1 when a
+// bounded wait inside the kernel gave up (results then undefined).
+constexpr int kOzSlicesF64 = 8;
+constexpr int kOzSlicesF32 = 4;
+size_t oz_scratch_bytes(int rows, int kmax, int slices);
+// C[m x n] = A^T B over rows rows (symmetric: A == B, only the upper tiles, mirrored)
+cudaError_t launch_gemm_tn_oz(int rows, int m, int n, const double* A, int lda, const double* B,
+                              int ldb, double* C, int ldc, bool symmetric, int slices,
+                              void* scratch, size_t scratch_bytes, int* err, cudaStream_t st);
+cudaError_t launch_gemm_tn_oz_f32(int rows, int m, int n, const float* A, int lda, const float* B,
+                                  int ldb, double* C, int ldc, bool symmetric, void* scratch,
+                                  size_t scratch_bytes, int* err, cudaStream_t st);
+// C[rows x n] = alpha A[rows x k] M[k x n] + beta C (C must not overlap A or M)
+cudaError_t launch_gemm_nn_oz(int rows, int k, int n, double alpha, const double* A, int lda,
+                              const double* M, int ldm, double beta, double* C, int ldc,
+                              int slices, void* scratch, size_t scratch_bytes, int* err,
+                              cudaStream_t st);
+cudaError_t launch_gemm_nn_oz_f32(int rows, int k, int n, float alpha, const float* A, int lda,
+                                  const double* M, int ldm, float beta, float* C, int ldc,
+                                  void* scratch, size_t scratch_bytes, int* err, cudaStream_t st);
+
 // ---- random head block (rng.cu) -----------------------------------------
 cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64_t seed,
                                  cudaStream_t st);

@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 def measure_rotation(shape: str, device, reps: int = 20) -> dict:
     """Y = X M with X FP64 [N, k_b] and M [k_b, k_b] (the rotation X = Q Z of Alg. 3), timed
     alone: CUDA events around `reps` launches."""
-    from . import block_rotate
+    from . import block_rotate_fp64 as block_rotate
     n, kb = (int(v) for v in shape.split("x"))
     g = torch.Generator(device="cpu").manual_seed(1)
     X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(device)

@@ -114,7 +114,7 @@ def test_block_rotate_matches_numpy(rows, k, n):
     rng = np.random.default_rng(rows + k)
     X = rng.standard_normal((rows, k))
     M = rng.standard_normal((k, n))
-    Y = host(scsf.block_rotate(torch.as_tensor(X, device=dev), torch.as_tensor(M, device=dev)))
+    Y = host(scsf.block_rotate_fp64(torch.as_tensor(X, device=dev), torch.as_tensor(M, device=dev)))
     ref = X @ M
     assert np.max(np.abs(Y - ref)) <= 1e-13 * k * np.max(np.abs(ref))
 
