@@ -9,9 +9,9 @@
 // D_ii the power of two just below sqrt(G_ii) (S_ii in [1, 4)): exact, and within a factor
 // of 4 of the optimal diagonal preconditioner (van der Sluis). Otherwise D = I and the factor
 // is the plain one.
-// Both factorisations run in one CTA with the matrix in shared memory
-// (right-looking, one column per step, the trailing update on a 32 x 32 thread
-// grid without index division). The inverse R^{-1} = (L^{-1})^T is spread over
+// Both factorisations run in one CTA with the matrix in shared memory (right-looking,
+// blocked in 32-column panels: the diagonal block by one warp, the rows below it one
+// thread each, the rank-32 trailing update on a 32 x 32 thread grid). The inverse R^{-1} = (L^{-1})^T is spread over
 // k single-warp CTAs: one warp forward-substitutes one column of L^{-1}, in FP32 for
 // the first pass and FP64 for the second.
 #include <algorithm>
@@ -38,21 +38,28 @@ __device__ __forceinline__ double chol_scale(double g) {
 }
 
 // G = L L^T for k x k symmetric positive definite G (lower triangle read), k <= 160,
-// through S = D^-1 G D^-1 (D from chol_scale). On a non-positive pivot the factorisation restarts on S + s I
-// (shifted Cholesky QR) with s growing 100x per retry, starting at c_eps k trace(S).
-// Writes L (lower, FP64, ld k, zeros above) and status = number of shifted
-// restarts, or 1000 if the last attempt still failed. blockDim = (32, 32).
+// through S = D^-1 G D^-1 (D from chol_scale). On a non-positive pivot the factorisation
+// restarts on S + s I (shifted Cholesky QR) with s growing 100x per retry, starting at
+// c_eps k trace(S). Writes L (lower, FP64, ld k, zeros above) and status = number of
+// shifted restarts, or 1000 if the last attempt still failed.
+// Blocked in 32-column panels with the matrix in shared memory, three barriers a panel:
+// warp 0 factors the panel's diagonal block (warp-synchronous, one column a step), one
+// thread per row below it solves its panel row against the diagonal block, and all
+// threads apply the panel's rank-32 update to the trailing lower triangle.
+// blockDim = (32, 32).
 template <typename T>
 __global__ void __launch_bounds__(1024)
-chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L,
-            int* __restrict__ status, double shift_eps) {
+chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L,
+                    int* __restrict__ status, double shift_eps) {
   extern __shared__ unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);  // k x ks
   const int ks = odd_stride(k);
-  __shared__ T dinv_s;
+  constexpr int PW = 32;
+  __shared__ T dinv[PW];
   __shared__ int bad;
   __shared__ double trace;
-  __shared__ double sc[kSmallBlockWidth];
+  __shared__ double sc[kSmallBlockWidth], isc[kSmallBlockWidth];
+  __shared__ double red[32];
   __shared__ int scaled;
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
   if (t == 0) scaled = 0;
@@ -60,11 +67,21 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
   for (int i = t; i < k; i += 1024)
     if (chol_out_of_range(G[(size_t)i * ldg + i])) scaled = 1;
   __syncthreads();
-  for (int i = t; i < k; i += 1024) sc[i] = scaled ? chol_scale(G[(size_t)i * ldg + i]) : 1.0;
+  // scales are powers of two: their reciprocals are exact, so S = G isc_i isc_j is exact
+  double part = 0.0;
+  for (int i = t; i < k; i += 1024) {
+    const double g = G[(size_t)i * ldg + i];
+    const double d = scaled ? chol_scale(g) : 1.0;
+    sc[i] = d;
+    isc[i] = 1.0 / d;
+    part += fabs(g) * isc[i] * isc[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (tx == 0) red[ty] = part;
   __syncthreads();
   if (t == 0) {
     double tr = 0.0;
-    for (int i = 0; i < k; ++i) tr += fabs(G[(size_t)i * ldg + i]) / (sc[i] * sc[i]);
+    for (int w = 0; w < 32; ++w) tr += red[w];
     trace = tr;
   }
   __syncthreads();
@@ -72,31 +89,59 @@ chol_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L
   for (; attempt < 4; ++attempt) {
     const double shift = (attempt == 0) ? 0.0 : shift_eps * k * trace * pow(100.0, attempt - 1);
     for (int i = ty; i < k; i += 32)
-      for (int j = tx; j <= i; j += 32)
-        S[i * ks + j] = (T)(G[(size_t)i * ldg + j] / (sc[i] * sc[j]) + ((i == j) ? shift : 0.0));
+      for (int j = tx; j <= i; j += 32) {
+        const double g = G[(size_t)i * ldg + j];
+        S[i * ks + j] = (T)((scaled ? g * isc[i] * isc[j] : g) + ((i == j) ? shift : 0.0));
+      }
     if (t == 0) bad = 0;
     __syncthreads();
-    for (int j = 0; j < k; ++j) {
-      if (t == 0) {
-        const T p = S[j * ks + j];
-        if (!(p > T(0))) {
-          if (bad == 0) bad = j + 1;
-          S[j * ks + j] = T(1);
-          dinv_s = T(1);
-        } else {
-          const T l = sqrt(p);
-          S[j * ks + j] = l;
-          dinv_s = T(1) / l;
+    for (int p = 0; p < k; p += PW) {
+      const int w = min(PW, k - p);
+      if (ty == 0) {  // diagonal block, lane = row within the panel
+        const int lane = tx;
+        for (int j = 0; j < w; ++j) {
+          T piv = S[(p + j) * ks + p + j];
+          if (!(piv > T(0))) {
+            if (lane == 0 && bad == 0) bad = p + j + 1;
+            piv = T(1);
+          }
+          const T l = sqrt(piv), inv = T(1) / l;
+          __syncwarp();
+          if (lane == j) {
+            S[(p + j) * ks + p + j] = l;
+            dinv[j] = inv;
+          }
+          if (lane > j && lane < w) S[(p + lane) * ks + p + j] *= inv;
+          __syncwarp();
+          if (lane > j && lane < w) {
+            const T lrj = S[(p + lane) * ks + p + j];
+            for (int c = j + 1; c <= lane; ++c) S[(p + lane) * ks + p + c] -= lrj * S[(p + c) * ks + p + j];
+          }
+          __syncwarp();
         }
       }
       __syncthreads();
-      const T inv = dinv_s;
-      for (int i = j + 1 + t; i < k; i += 1024) S[i * ks + j] *= inv;
+      // rows below the panel: L21 = A21 L11^{-T}, forward substitution along each row
+      for (int r = p + w + t; r < k; r += 1024) {
+        T* row = S + r * ks + p;
+        for (int j = 0; j < w; ++j) {
+          T v = row[j];
+          const T* lj = S + (p + j) * ks + p;
+          for (int c = 0; c < j; ++c) v -= row[c] * lj[c];
+          row[j] = v * dinv[j];
+        }
+      }
       __syncthreads();
-      // trailing lower triangle: S[i][c] -= L[i][j] L[c][j], j < c <= i
-      for (int i = j + 1 + ty; i < k; i += 32) {
-        const T lij = S[i * ks + j];
-        for (int c = j + 1 + tx; c <= i; c += 32) S[i * ks + c] -= lij * S[c * ks + j];
+      // trailing lower triangle: S[r][c] -= sum_q L[r][p + q] L[c][p + q]
+      const int q0 = p + w;
+      for (int r = q0 + ty; r < k; r += 32) {
+        const T* lr = S + r * ks + p;
+        for (int c = q0 + tx; c <= r; c += 32) {
+          const T* lc = S + c * ks + p;
+          T acc = T(0);
+          for (int q = 0; q < w; ++q) acc = fma(lr[q], lc[q], acc);
+          S[r * ks + c] -= acc;
+        }
       }
       __syncthreads();
     }
@@ -287,7 +332,7 @@ __global__ void chol_trace_kernel(int k, const double* __restrict__ G, int ldg,
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// Factor with the scaling and restart rule of chol_kernel (shift c_eps k trace(S)
+// Factor with the scaling and restart rule of chol_blocked_kernel (shift c_eps k trace(S)
 // 100^(attempt-1)); the host reads the failure flag after each attempt (wide blocks only).
 template <typename T>
 cudaError_t launch_chol_wide(int k, const double* G, int ldg, double* L, int* status, double eps,
@@ -343,9 +388,9 @@ template <typename T>
 cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* status, double eps,
                           cudaStream_t st) {
   const size_t smem = (size_t)k * odd_stride(k) * sizeof(T);
-  cudaError_t e = ensure_dynamic_smem((const void*)chol_kernel<T>, smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)chol_blocked_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  chol_kernel<T><<<1, dim3(32, 32), smem, st>>>(k, G, ldg, L, status, eps);
+  chol_blocked_kernel<T><<<1, dim3(32, 32), smem, st>>>(k, G, ldg, L, status, eps);
   note_launch();
   return cudaGetLastError();
 }

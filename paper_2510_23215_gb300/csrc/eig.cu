@@ -1,21 +1,29 @@
 // Reduced symmetric eigensolve G W = W Lambda (Alg. 3, reduced eigensolve) for k <= 512
 // (shared-memory kernels up to k = 160, global-memory variants above).
 //
-// GB300 runs FP32 about 60x faster than FP64, so the decomposition is found
-// in FP32 and then refined to FP64 accuracy:
-//   1. parallel cyclic Jacobi in FP32, one CTA, both k x k matrices in shared
+// GB300 runs FP32 about 60x faster than FP64, and one SM runs FP64 at about 2 FMA/clk, so
+// the decomposition is found cheaply and then refined to FP64 accuracy on all SMs:
+//   0. a probe (one CTA, FP32) decides whether G is already nearly diagonal: every pair
+//      whose diagonal entries differ by more than the cluster floor has |g_ij| below
+//      1e-2 of that difference. In a warm-started chain this holds for every Rayleigh-Ritz
+//      matrix after the first of a problem (the block is already close to the Ritz
+//      vectors), and then the start is the identity;
+//   1. otherwise parallel cyclic Jacobi in FP32, one CTA, both k x k matrices in shared
 //      memory with an odd row stride (column accesses are bank-conflict free),
 //      round-robin (circle method) pair ordering: the k/2 disjoint rotations of a
 //      round are applied as one similarity transform, thread by thread over 2 x 2
 //      blocks, two barriers per round;
-//   2. two Ogita-Aishima refinement steps in FP64 (X' = X (I + E) with
+//   2. Ogita-Aishima refinement steps in FP64 (X' = X (I + E) with
 //      R = I - X^T X, S = X^T G X, lambda_i = s_ii/(1 - r_ii), E_ij =
 //      (s_ij + lambda_j r_ij)/(lambda_j - lambda_i), or r_ij/2 for pairs closer
 //      than delta = max(2(||S - D|| + ||G|| ||R||), 3e-3 ||G||)); each step squares
-//      the error. X^T [G X | X] is one split-K product over all SMs;
-//   3. exact FP64 Jacobi rotations for the pairs left coupled in step 2 (close
-//      pairs, where the first-order update does not converge from FP32 accuracy);
-//      only entries above 1e-13 ||G|| rotate, so a resolved matrix costs one scan;
+//      the error. X^T [G X | X] is one split-K product over all SMs, the element-wise
+//      update runs on many CTAs after a one-CTA norm pass;
+//   3. the pairs the refinement left coupled (eigenvalues closer than delta) form runs of
+//      consecutive eigenvalues; each run (cluster) is diagonalised exactly by one warp
+//      (cyclic FP64 Jacobi on its small block) and its columns of X rotated along. Runs
+//      longer than kClusterMax fall back to exact FP64 round-robin Jacobi sweeps over
+//      the whole matrix;
 //   4. ascending sort of the pairs.
 #include <algorithm>
 
@@ -24,10 +32,16 @@
 namespace scsf {
 namespace {
 
-// Refinement steps: the FP32 Jacobi result of a wide matrix carries more accumulated
-// rounding (k - 1 rounds per sweep), so it gets two more quadratic steps.
-constexpr int kOaSteps = 2;
+// Refinement steps (each squares the error): from the probe's start (couplings below 1e-2
+// of the gaps, or FP32 Jacobi accuracy) three reach FP64, two the FP32 phase's accuracy;
+// the FP32 Jacobi result of a wide matrix carries more accumulated rounding (k - 1 rounds
+// per sweep), so it gets one more.
+constexpr int kOaSteps = 3;
+constexpr int kOaStepsF32 = 2;
 constexpr int kOaStepsWide = 4;
+constexpr float kNearDiag = 1e-2f;  // probe: largest |g_ij| / |g_jj - g_ii| of separated pairs
+constexpr int kClusterMax = 16;     // longest run one warp diagonalises
+constexpr int kClusterWarps = 8;    // warps that take runs (static shared memory: 35 KB)
 constexpr int kJacobiSweeps = 30;
 constexpr double kClusterFloor = 3e-3;  // relative gap below which pairs go to FP64 Jacobi
 constexpr double kCleanupTol = 1e-13;   // |P_pq| / ||G|| below which a pair counts as resolved
@@ -185,9 +199,15 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
 template <bool kWide>
 __global__ void __launch_bounds__(1024)
 jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, int ldz,
-                  double* __restrict__ lam, int max_sweeps, float* __restrict__ wide) {
+                  double* __restrict__ lam, int max_sweeps, float* __restrict__ wide,
+                  const int* __restrict__ start) {
+  // the leading block [0, t0) is already nearly diagonal (probe): Jacobi on [t0, k) only,
+  // the identity on the rest
+  const int t0 = start ? min(max(*start, 0), k) : 0;
+  const int kf = k;
+  k = kf - t0;
   extern __shared__ float smf[];
-  const int ks = odd_stride(k);
+  const int ks = odd_stride(k > 0 ? k : 1);
   float* A = kWide ? wide : smf;                      // k x ks
   float* V = kWide ? wide + k * ks : smf + k * ks;    // k x ks
   __shared__ float red[64];
@@ -195,9 +215,16 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
   __shared__ int s_pl[kMaxBlockWidth + 2];
   __shared__ int s_nrot;
   const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < kf * kf; e += nt) {
+    const int i = e / kf, j = e - i * kf;
+    if (i < t0 || j < t0) Z[(size_t)i * ldz + j] = (i == j) ? 1.0 : 0.0;
+  }
+  if (lam)
+    for (int i = t; i < t0; i += nt) lam[i] = S[(size_t)i * kf + i];
+  if (k <= 0) return;
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    A[i * ks + j] = (float)S[e];
+    A[i * ks + j] = (float)S[(size_t)(t0 + i) * kf + t0 + j];
     V[i * ks + j] = (i == j) ? 1.0f : 0.0f;
   }
   __syncthreads();
@@ -230,33 +257,36 @@ jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, i
   }
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    Z[(size_t)i * ldz + j] = (double)V[i * ks + j];
+    Z[(size_t)(t0 + i) * ldz + t0 + j] = (double)V[i * ks + j];
   }
   if (lam)
-    for (int i = t; i < k; i += nt) lam[i] = (double)A[i * ks + i];
+    for (int i = t; i < k; i += nt) lam[t0 + i] = (double)A[i * ks + i];
 }
 
-// Element-wise part of one Ogita-Aishima step (single CTA). PQ = Z^T [S Z | Z]
-// (k x 2k): P = left half, Q = right half. Writes Eplus = I + E (k x k) and lam.
+// Norm pass of one Ogita-Aishima step (one CTA): lambda_i = s_ii / (1 - r_ii) and the
+// cluster threshold delta, from PQ = Z^T [S Z | Z] (k x 2k; P = left half, Q = right half).
+// state[0] = delta.
 __global__ void __launch_bounds__(1024)
-oa_update_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Eplus,
-                 double* __restrict__ lam, double cluster_floor) {
-  __shared__ double s_lam[kMaxBlockWidth];
+oa_norms_kernel(int k, const double* __restrict__ PQ, double* __restrict__ lam,
+                double* __restrict__ state, double cluster_floor) {
   __shared__ double red[3][32];
-  __shared__ double delta;
   const int t = threadIdx.x, nt = blockDim.x;
   const int ld = 2 * k;
-  for (int i = t; i < k; i += nt) s_lam[i] = PQ[i * ld + i] / PQ[i * ld + k + i];  // s_ii/(1-r_ii)
-  __syncthreads();
-  double off2 = 0.0, r2 = 0.0, nrm = 0.0;
+  // the norms only set the cluster threshold: FP32 sums (one SM's FP64 pipe is narrow)
+  float off2 = 0.f, r2 = 0.f;
+  double nrm = 0.0;
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    const double r = ((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j];
-    const double sd = PQ[i * ld + j] - ((i == j) ? s_lam[i] : 0.0);
-    off2 = fma(sd, sd, off2);
-    r2 = fma(r, r, r2);
+    const float r = (float)(((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j]);
+    const float sd = (i == j) ? 0.f : (float)PQ[i * ld + j];
+    off2 = fmaf(sd, sd, off2);
+    r2 = fmaf(r, r, r2);
   }
-  for (int i = t; i < k; i += nt) nrm = fmax(nrm, fabs(s_lam[i]));
+  for (int i = t; i < k; i += nt) {
+    const double li = PQ[i * ld + i] / PQ[i * ld + k + i];  // s_ii / (1 - r_ii)
+    lam[i] = li;
+    nrm = fmax(nrm, fabs(li));
+  }
   for (int o = 16; o > 0; o >>= 1) {
     off2 += __shfl_xor_sync(0xffffffffu, off2, o);
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
@@ -275,20 +305,198 @@ oa_update_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Eplu
       b += red[1][w];
       c = fmax(c, red[2][w]);
     }
-    // pairs closer than cluster_floor * ||S|| are left to the FP64 Jacobi pass:
-    // the first-order update only converges when the error is below gap/||S||
-    delta = fmax(2.0 * (sqrt(a) + c * sqrt(b)), cluster_floor * c);
+    // pairs closer than cluster_floor * ||S|| are left to the cluster pass: the
+    // first-order update only converges when the error is below gap/||S||
+    state[0] = fmax(2.0 * (sqrt(a) + c * sqrt(b)), cluster_floor * c);
   }
+}
+
+// Element-wise part of the step on many CTAs: Eplus = I + E.
+__global__ void oa_apply_kernel(int k, const double* __restrict__ PQ, const double* __restrict__ lam,
+                                const double* __restrict__ state, double* __restrict__ Eplus) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  const int ld = 2 * k;
+  const int i = e / k, j = e - i * k;
+  const double r = ((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j];
+  const double li = lam[i], lj = lam[j];
+  const double gap = lj - li;
+  const double v = (i != j && fabs(gap) > state[0]) ? (PQ[i * ld + j] + lj * r) / gap : 0.5 * r;
+  Eplus[e] = v + ((i == j) ? 1.0 : 0.0);
+}
+
+// Probe (one CTA, FP32): the pairs of S whose diagonal entries differ by more than
+// floor * max|s_ii| are "separated"; a separated pair with |s_ij| > kNearDiag |s_jj - s_ii| is
+// "far". start[0] = the smallest index of any far pair (k when there is none): the FP32
+// Jacobi then only has to diagonalise the trailing block [start, k), and the refinement
+// converges from there. In a warm-started chain the far pairs, if any, are the couplings
+// among the top (guard) columns, which converge last.
+__global__ void __launch_bounds__(1024)
+eig_probe_kernel(int k, const double* __restrict__ S, double floor, int* __restrict__ start) {
+  __shared__ float red[32];
+  __shared__ int first;
+  const int t = threadIdx.x, nt = blockDim.x;
+  float nrm = 0.f;
+  for (int i = t; i < k; i += nt) nrm = fmaxf(nrm, fabsf((float)S[(size_t)i * k + i]));
+  for (int o = 16; o > 0; o >>= 1) nrm = fmaxf(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+  if ((t & 31) == 0) red[t >> 5] = nrm;
+  if (t == 0) first = k;
   __syncthreads();
-  const double dl = delta;
+  float m = 0.f;
+  for (int w = 0; w < (nt + 31) / 32; ++w) m = fmaxf(m, red[w]);
+  const float dl = (float)floor * m;
+  int local = k;
   for (int e = t; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    const double r = ((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j];
-    const double gap = s_lam[j] - s_lam[i];
-    const double v = (i != j && fabs(gap) > dl) ? (PQ[i * ld + j] + s_lam[j] * r) / gap : 0.5 * r;
-    Eplus[e] = v + ((i == j) ? 1.0 : 0.0);
+    if (j <= i) continue;
+    const float gap = fabsf((float)S[(size_t)j * k + j] - (float)S[(size_t)i * k + i]);
+    const float sij = fabsf((float)S[e]);
+    if ((gap > dl && sij > kNearDiag * gap) || !(sij == sij)) local = min(local, i);
   }
-  for (int i = t; i < k; i += nt) lam[i] = s_lam[i];
+  if (local < k) atomicMin(&first, local);
+  __syncthreads();
+  if (t == 0) start[0] = first;
+}
+
+// Exact diagonalisation of the clusters the refinement left coupled (one CTA). P = Z^T S Z
+// is the left half of PQ. Pairs with |P_ij| > tol (tol = kCleanupTol max|P_ii|) join the run
+// of consecutive eigenvalues between them (positions in ascending order of diag(P)); each
+// run of length 2..kClusterMax is diagonalised by one warp (cyclic FP64 Jacobi on its small
+// block to below tol) and its columns of Z (ld ldz) rotated along. lam = diag(P) updated.
+// A run longer than kClusterMax: with fallback non-null, fallback[0] = 1 and nothing changes
+// (exact round-robin sweeps take over); with fallback null such runs keep their columns of Z
+// (the FP32 phase, whose start vectors already resolve them to FP32 accuracy).
+__global__ void __launch_bounds__(1024)
+cluster_jacobi_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Z, int ldz,
+                      double* __restrict__ lam, int* __restrict__ fallback) {
+  __shared__ int pos[kMaxBlockWidth], idx[kMaxBlockWidth], reach[kMaxBlockWidth];
+  __shared__ int run_start[kMaxBlockWidth], nruns, too_long;
+  __shared__ double nrm;
+  __shared__ double blk[kClusterWarps][kClusterMax][kClusterMax + 1];
+  __shared__ double W[kClusterWarps][kClusterMax][kClusterMax + 1];
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5;
+  const int ld = 2 * k;
+  __shared__ double mred[32];
+  double m = 0.0;
+  for (int i = t; i < k; i += nt) m = fmax(m, fabs(PQ[i * ld + i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) mred[warp] = m;
+  __syncthreads();
+  if (t == 0) {
+    double mm = 0.0;
+    for (int w = 0; w < nt / 32; ++w) mm = fmax(mm, mred[w]);
+    nrm = mm;
+    nruns = 0;
+    too_long = 0;
+  }
+  // ascending positions of the diagonal (ties by index)
+  for (int i = t; i < k; i += nt) {
+    const double li = PQ[i * ld + i];
+    int r = 0;
+    for (int j = 0; j < k; ++j) {
+      const double lj = PQ[j * ld + j];
+      r += (lj < li || (lj == li && j < i)) ? 1 : 0;
+    }
+    pos[i] = r;
+    idx[r] = i;
+    reach[r] = r;
+  }
+  __syncthreads();
+  const double tol = kCleanupTol * nrm;
+  for (int e = t; e < k * k; e += nt) {
+    const int i = e / k, j = e - i * k;
+    if (j <= i) continue;
+    const double pij = 0.5 * (PQ[i * ld + j] + PQ[j * ld + i]);
+    if (fabs(pij) > tol) {
+      const int a = min(pos[i], pos[j]), b = max(pos[i], pos[j]);
+      atomicMax(&reach[a], b);
+    }
+  }
+  __syncthreads();
+  if (t == 0) {  // runs: maximal intervals joined by some coupled pair
+    int r = 0;
+    while (r < k) {
+      int end = reach[r];
+      int q = r;
+      while (q < end) {
+        ++q;
+        end = max(end, reach[q]);
+      }
+      if (end > r) {
+        if (end - r + 1 > kClusterMax) too_long = 1;
+        run_start[nruns++] = r;
+      }
+      reach[r] = end;  // end of the run starting at r
+      r = end + 1;
+    }
+  }
+  __syncthreads();
+  if (too_long && fallback) {
+    if (t == 0) fallback[0] = 1;
+    return;
+  }
+  for (int i = t; i < k; i += nt) lam[i] = PQ[i * ld + i];
+  __syncthreads();
+  if (warp >= kClusterWarps) return;
+  for (int c = warp; c < nruns; c += kClusterWarps) {
+    const int r0 = run_start[c], n = reach[r0] - r0 + 1;
+    if (n > kClusterMax) continue;
+    double(*A)[kClusterMax + 1] = blk[warp];
+    double(*V)[kClusterMax + 1] = W[warp];
+    for (int e = lane; e < n * n; e += 32) {
+      const int a = e / n, b = e - a * n;
+      const int ia = idx[r0 + a], ib = idx[r0 + b];
+      A[a][b] = 0.5 * (PQ[ia * ld + ib] + PQ[ib * ld + ia]);
+      V[a][b] = (a == b) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      double off = 0.0;
+      for (int e = lane; e < n * n; e += 32) {
+        const int a = e / n, b = e - a * n;
+        if (a != b) off = fmax(off, fabs(A[a][b]));
+      }
+      for (int o = 16; o > 0; o >>= 1) off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+      if (off <= 0.1 * tol) break;
+      for (int p = 0; p < n - 1; ++p)
+        for (int q = p + 1; q < n; ++q) {
+          const double apq = A[p][q];
+          double cs = 1.0, sn = 0.0;
+          if (fabs(apq) > 0.1 * tol) jacobi_angle(A[p][p], A[q][q], apq, cs, sn);
+          __syncwarp();
+          if (sn != 0.0) {
+            // A' = J^T A J on rows / columns p, q; V' = V J
+            if (lane < n) {
+              const double ap = A[p][lane], aq = A[q][lane];
+              A[p][lane] = cs * ap - sn * aq;
+              A[q][lane] = sn * ap + cs * aq;
+            }
+            __syncwarp();
+            if (lane < n) {
+              const double ap = A[lane][p], aq = A[lane][q];
+              A[lane][p] = cs * ap - sn * aq;
+              A[lane][q] = sn * ap + cs * aq;
+              const double vp = V[lane][p], vq = V[lane][q];
+              V[lane][p] = cs * vp - sn * vq;
+              V[lane][q] = sn * vp + cs * vq;
+            }
+            __syncwarp();
+          }
+        }
+    }
+    for (int a = lane; a < n; a += 32) lam[idx[r0 + a]] = A[a][a];
+    // Z[:, run] = Z[:, run] V, row by row
+    for (int row = lane; row < k; row += 32) {
+      double z[kClusterMax];
+      for (int a = 0; a < n; ++a) z[a] = Z[(size_t)row * ldz + idx[r0 + a]];
+      for (int b = 0; b < n; ++b) {
+        double v = 0.0;
+        for (int a = 0; a < n; ++a) v = fma(z[a], V[a][b], v);
+        Z[(size_t)row * ldz + idx[r0 + b]] = v;
+      }
+    }
+    __syncwarp();
+  }
 }
 
 // Exact FP64 Jacobi on P = Z^T S Z (left half of PQ, symmetrised on load) for
@@ -297,7 +505,9 @@ oa_update_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Eplu
 template <bool kWide>
 __global__ void __launch_bounds__(1024)
 jacobi_f64_cleanup_kernel(int k, const double* __restrict__ PQ, double* __restrict__ Z, int ldz,
-                          double* __restrict__ lam, int max_sweeps, double* __restrict__ wide) {
+                          double* __restrict__ lam, int max_sweeps, double* __restrict__ wide,
+                          const int* __restrict__ only_if) {
+  if (only_if && !*only_if) return;  // the cluster pass resolved every coupled pair
   extern __shared__ double smd[];
   const int ks = odd_stride(k);
   double* P = kWide ? wide : smd;  // k x ks
@@ -373,7 +583,8 @@ sort_pairs_kernel(int k, const double* __restrict__ lam, const double* __restric
 
 // Scratch: S (k x k); two k x 2k panels [T | Z]; PQ (k x 2k); Eplus (k x k); lam; partials.
 struct EighScratch {
-  double *S, *TZ0, *TZ1, *PQ, *E, *lam, *partials;
+  double *S, *TZ0, *TZ1, *PQ, *E, *lam, *partials, *state;
+  int* flags;  // [0] near-diagonal (probe), [1] cluster pass fell back
   float* wide32;   // k > kSmallBlockWidth: the FP32 Jacobi matrices (2 k ks)
   double* wide64;  // k > kSmallBlockWidth: the FP64 clean-up matrix (k ks)
 };
@@ -389,6 +600,8 @@ EighScratch carve_eigh(C& c, int k) {
   s.E = c.template take<double>(kk);
   s.lam = c.template take<double>(k);
   s.partials = c.template take<double>(gemm_tn_partials(k, k, 2 * k, false));
+  s.state = c.template take<double>(4);
+  s.flags = c.template take<int>(4);
   s.wide32 = nullptr;
   s.wide64 = nullptr;
   if (k > kSmallBlockWidth) {
@@ -413,31 +626,74 @@ cudaError_t set_smem(const void* fn, size_t bytes) {
 
 
 cudaError_t run_jacobi_f32(int k, const double* S, double* Z, int ldz, double* lam,
-                           const EighScratch& w, cudaStream_t st) {
+                           const EighScratch& w, cudaStream_t st, const int* near) {
   cudaError_t e;
   if (k <= kSmallBlockWidth) {
     const size_t smem32 = 2 * (size_t)k * odd_stride(k) * sizeof(float);
     if ((e = set_smem((const void*)jacobi_f32_kernel<false>, smem32)) != cudaSuccess) return e;
-    jacobi_f32_kernel<false><<<1, 1024, smem32, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, nullptr);
+    jacobi_f32_kernel<false><<<1, 1024, smem32, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, nullptr,
+                                                       near);
   } else {
-    jacobi_f32_kernel<true><<<1, 1024, 0, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, w.wide32);
+    jacobi_f32_kernel<true><<<1, 1024, 0, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, w.wide32, near);
   }
   note_launch();
   return cudaGetLastError();
 }
 
+// Cluster pass; with `exact`, runs too long for it fall back to round-robin FP64 sweeps.
 cudaError_t run_cleanup_f64(int k, const double* PQ, double* Z, int ldz, double* lam,
-                            const EighScratch& w, cudaStream_t st) {
+                            const EighScratch& w, cudaStream_t st, bool exact) {
   cudaError_t e;
+  if ((e = cudaMemsetAsync(w.flags + 1, 0, sizeof(int), st)) != cudaSuccess) return e;
+  cluster_jacobi_kernel<<<1, 1024, 0, st>>>(k, PQ, Z, ldz, lam, exact ? w.flags + 1 : nullptr);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!exact) return cudaSuccess;
   if (k <= kSmallBlockWidth) {
     const size_t smem64 = (size_t)k * odd_stride(k) * sizeof(double);
     if ((e = set_smem((const void*)jacobi_f64_cleanup_kernel<false>, smem64)) != cudaSuccess) return e;
-    jacobi_f64_cleanup_kernel<false><<<1, 1024, smem64, st>>>(k, PQ, Z, ldz, lam, 6, nullptr);
+    jacobi_f64_cleanup_kernel<false><<<1, 1024, smem64, st>>>(k, PQ, Z, ldz, lam, 6, nullptr,
+                                                               w.flags + 1);
   } else {
-    jacobi_f64_cleanup_kernel<true><<<1, 1024, 0, st>>>(k, PQ, Z, ldz, lam, 10, w.wide64);
+    jacobi_f64_cleanup_kernel<true><<<1, 1024, 0, st>>>(k, PQ, Z, ldz, lam, 10, w.wide64,
+                                                        w.flags + 1);
   }
   note_launch();
   return cudaGetLastError();
+}
+
+// Start (probe, then FP32 Jacobi unless nearly diagonal) and `steps` refinement steps on the
+// symmetrised w.S; the eigenvectors end in the right half of the returned panel (ld 2k),
+// PQ = Z^T [S Z | Z] of the final Z in w.PQ.
+cudaError_t eigh_refined(int k, const EighScratch& w, int steps, double** TZout, cudaStream_t st) {
+  cudaError_t e;
+  const int ld2 = 2 * k;
+  eig_probe_kernel<<<1, 1024, 0, st>>>(k, w.S, kClusterFloor, w.flags);
+  note_launch();
+  double* TZ = w.TZ0;
+  double* TZn = w.TZ1;
+  if ((e = run_jacobi_f32(k, w.S, TZ + k, ld2, nullptr, w, st, w.flags)) != cudaSuccess) return e;
+  for (int step = 0; step <= steps; ++step) {
+    // T = S Z into the left half; PQ = Z^T [T | Z]
+    if ((e = launch_gemm_nn(k, k, k, 1.0, w.S, k, TZ + k, ld2, 0.0, TZ, ld2, false, st)) != cudaSuccess)
+      return e;
+    if ((e = launch_gemm_tn(k, k, 2 * k, TZ + k, ld2, TZ, ld2, w.PQ, ld2, false, w.partials, st)) !=
+        cudaSuccess)
+      return e;
+    if (step == steps) break;
+    oa_norms_kernel<<<1, 1024, 0, st>>>(k, w.PQ, w.lam, w.state, kClusterFloor);
+    note_launch();
+    oa_apply_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, w.PQ, w.lam, w.state, w.E);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Z' = Z (I + E) into the next panel's right half
+    if ((e = launch_gemm_nn(k, k, k, 1.0, TZ + k, ld2, w.E, k, 0.0, TZn + k, ld2, false, st)) !=
+        cudaSuccess)
+      return e;
+    std::swap(TZ, TZn);
+  }
+  *TZout = TZ;
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -457,30 +713,11 @@ cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, do
   const int ld2 = 2 * k;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, S, lds, w.S);
   note_launch();
-  // Z lives in the right half of a [T | Z] panel (ld 2k)
-  double* TZ = w.TZ0;
-  double* TZn = w.TZ1;
-  if ((e = run_jacobi_f32(k, w.S, TZ + k, ld2, nullptr, w, st)) != cudaSuccess) return e;
+  double* TZ = nullptr;
   const int oa_steps = (k > kSmallBlockWidth) ? kOaStepsWide : kOaSteps;
-  for (int step = 0; step <= oa_steps; ++step) {
-    // T = S Z into the left half; PQ = Z^T [T | Z]
-    if ((e = launch_gemm_nn(k, k, k, 1.0, w.S, k, TZ + k, ld2, 0.0, TZ, ld2, false, st)) != cudaSuccess)
-      return e;
-    if ((e = launch_gemm_tn(k, k, 2 * k, TZ + k, ld2, TZ, ld2, w.PQ, ld2, false, w.partials, st)) !=
-        cudaSuccess)
-      return e;
-    if (step == oa_steps) break;
-    oa_update_kernel<<<1, 1024, 0, st>>>(k, w.PQ, w.E, w.lam, kClusterFloor);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // Z' = Z (I + E) into the next panel's right half
-    if ((e = launch_gemm_nn(k, k, k, 1.0, TZ + k, ld2, w.E, k, 0.0, TZn + k, ld2, false, st)) !=
-        cudaSuccess)
-      return e;
-    std::swap(TZ, TZn);
-  }
+  if ((e = eigh_refined(k, w, oa_steps, &TZ, st)) != cudaSuccess) return e;
   // exact FP64 rotations for the pairs the refinement treated as clusters
-  if ((e = run_cleanup_f64(k, w.PQ, TZ + k, ld2, w.lam, w, st)) != cudaSuccess) return e;
+  if ((e = run_cleanup_f64(k, w.PQ, TZ + k, ld2, w.lam, w, st, true)) != cudaSuccess) return e;
   sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, TZ + k, ld2, evals, Zout, ldz);
   note_launch();
   return cudaGetLastError();
@@ -499,8 +736,11 @@ cudaError_t launch_small_eigh_f32(int k, const double* S, int lds, double* evals
   cudaError_t e;
   symmetrize_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, S, lds, w.S);
   note_launch();
-  if ((e = run_jacobi_f32(k, w.S, w.TZ0, k, w.lam, w, st)) != cudaSuccess) return e;
-  sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, w.TZ0, k, evals, Zout, ldz);
+  // FP32-phase accuracy (about 1e-7): two refinement steps from the probe's start
+  double* TZ = nullptr;
+  if ((e = eigh_refined(k, w, kOaStepsF32, &TZ, st)) != cudaSuccess) return e;
+  if ((e = run_cleanup_f64(k, w.PQ, TZ + k, 2 * k, w.lam, w, st, false)) != cudaSuccess) return e;
+  sort_pairs_kernel<<<1, 1024, 0, st>>>(k, w.lam, TZ + k, 2 * k, evals, Zout, ldz);
   note_launch();
   return cudaGetLastError();
 }
