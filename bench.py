@@ -3,10 +3,11 @@ Chebyshev filtered subspace iteration) on GB300, at relative residual <= 1e-8.
 
 One step = the whole path over one batch: sort 200 synthetic -div(a grad u)
 operators on a 128 x 128 grid (p0 = 8), then solve them in sorted order, each problem
-warm-started from its predecessor, for the k = 100 smallest eigenpairs (tol 1e-8). The timed form is the
-mixed one (FP32 phase, then FP64 phase with the defect-corrected filter; filter degrees
-100 and 100), with the sorted sequence cut into 8 chains solved concurrently; the plain
-FP64 form at the workload degree 20, one sequential chain, is timed beside it.
+warm-started from its predecessor, for the k = 100 smallest eigenpairs (tol 1e-8). The timed
+form is the mixed one (FP32 phase, then FP64 phase with the defect-corrected filter; block
+products on the tensor cores), with the sorted sequence cut into 8 chains solved
+concurrently. Beside it: the plain FP64 form at its own best degree and the same 8 chains
+(the tuned comparison), and the paper's form as written (degree 20, one sequential chain).
 Each rank runs its own batch (weak scaling, no data-path collective).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -38,8 +39,9 @@ L2_FLUSH_BYTES = 512 << 20
 # algorithmic bytes per (node, column) per filter step: read Y_i and Y_{i-1}, write Y_{i+1}
 # (FP64: 24 B, FP32: 12 B); the defect-corrected step also reads the residual block (16 B)
 BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 16.0}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
-# current kernels (profiles/cheb_step_*.md); kernels not captured at a shape are absent
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one earlier ncu capture of each
+# kernel at the named shape (copied, not measured in this run); absent where not captured
+TRAFFIC_SOURCE = "one ncu capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum)"
 TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6,
                       "gemm_nn_rotation": 15.85e6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
@@ -180,13 +182,13 @@ def run_ours(args):
     h_resid = torch.empty((n_ops, k), dtype=torch.float64).pin_memory()
     st = torch.cuda.current_stream(dev)
 
-    def step(fields, ax, ay, precision, chunks=1):
+    def step(fields, ax, ay, precision, chunks=1, degree=None):
         if precision == scsf.MIXED:  # the chosen form tunes its filter degrees
             params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32,
                                  tol=w["tol"], seed=7 + rank, precision=precision,
                                  switch_tol=args.switch_tol)
-        else:                        # the plain form keeps the workload's degree
-            params = scsf.Params(k=k, degree=w["degree"], tol=w["tol"], seed=7 + rank,
+        else:                        # the plain form: its own degree (default: the workload's)
+            params = scsf.Params(k=k, degree=degree or w["degree"], tol=w["tol"], seed=7 + rank,
                                  precision=precision)
         perm = scsf.sort(fields, p0=w["p0"], start=0, ctx=ctx).cpu().tolist()
         dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i]) for i in perm]
@@ -207,12 +209,14 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
-    def timed(precision, steps, warmup, sample_clocks=False, chunks=1, phase_timing=False):
+    def timed(precision, steps, warmup, sample_clocks=False, chunks=1, phase_timing=False,
+              degree=None):
         for _ in range(warmup):
-            step(d_fields, d_ax, d_ay, precision, chunks)
+            step(d_fields, d_ax, d_ay, precision, chunks, degree)
         barrier()
         ctx.set_timing(phase_timing)
         times, all_stats, good = [], [], 0
+        last_ev, max_res = None, 0.0
         launches0 = scsf.launch_count()
         clk = ClockSampler(local) if sample_clocks else None
         if clk:
@@ -222,17 +226,19 @@ def run_ours(args):
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            ev, rs, stats = step(d_fields, d_ax, d_ay, precision, chunks)
+            ev, rs, stats = step(d_fields, d_ax, d_ay, precision, chunks, degree)
             e1.record(st)
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
             all_stats.extend(stats)
             good += int((rs <= w["tol"]).sum().item())
+            max_res = max(max_res, float(rs.max().item()))
+            last_ev = ev
         if clk:
             clk.__exit__(None, None, None)
         ctx.set_timing(False)
-        return {"ms": sum(times), "stats": all_stats, "pairs": good,
-                "launches": scsf.launch_count() - launches0,
+        return {"ms": sum(times), "stats": all_stats, "pairs": good, "max_resid": max_res,
+                "last_ev": last_ev, "launches": scsf.launch_count() - launches0,
                 "clocks": clk.summary() if clk else None}
 
     def reduce_max_sum(ms, pairs):
@@ -268,13 +274,25 @@ def run_ours(args):
     e2e_ms, e2e_pairs = reduce_max_sum(e2e_ms, e2e_pairs)
     e2e_value = e2e_pairs / (e2e_ms * 1e-3)
 
-    other = None
+    other, paper_form = None, None
     if not args.no_plain and chosen != "fp64":
-        plain = timed(forms["fp64"], args.plain_steps, 1, phase_timing=False)
+        # the tuned comparison: plain FP64 at its best degree, same chains in flight
+        plain = timed(forms["fp64"], args.plain_steps, 1, chunks=args.plain_chunks,
+                      degree=args.plain_degree)
         p_ms, p_pairs = reduce_max_sum(plain["ms"], plain["pairs"])
-        other = {"form": "plain FP64, one sequential chain", "value": p_pairs / (p_ms * 1e-3),
-                 "ms_per_step": p_ms / args.plain_steps, "steps": args.plain_steps, "warmup": 1,
+        other = {"form": f"plain FP64 (Alg. 3 in FP64), degree {args.plain_degree}, "
+                         f"{args.plain_chunks} concurrent chains",
+                 "value": p_pairs / (p_ms * 1e-3), "ms_per_step": p_ms / args.plain_steps,
+                 "steps": args.plain_steps, "warmup": 1, "degree": args.plain_degree,
+                 "chunks": args.plain_chunks,
                  "iters_per_op_mean": float(np.mean([s["iters"] for s in plain["stats"]]))}
+        if not args.no_paper_form:
+            # the paper's form as written: workload degree, one sequential chain (context)
+            pf = timed(forms["fp64"], 1, 0, chunks=1)
+            f_ms, f_pairs = reduce_max_sum(pf["ms"], pf["pairs"])
+            paper_form = {"form": f"plain FP64, degree {w['degree']}, one sequential chain",
+                          "value": f_pairs / (f_ms * 1e-3), "ms_per_step": f_ms, "steps": 1,
+                          "iters_per_op_mean": float(np.mean([s["iters"] for s in pf["stats"]]))}
 
     all_stats = instrumented["stats"]
     # per-phase device time of the instrumented step: CUDA events on each chain's own stream,
@@ -312,7 +330,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "gemm_nn_kernel (FP64 block rotation X = Q M)",
                 "achieved": rot["tflops"], "peak": rot["peak_tflops"], "unit": "TFLOP/s",
                 "frac": rot["tflops"] / rot["peak_tflops"],
-                "traffic": TRAFFIC_PER_LAUNCH.get("gemm_nn_rotation"),
+                "traffic": TRAFFIC_PER_LAUNCH.get("gemm_nn_rotation"), "traffic_source": TRAFFIC_SOURCE,
                 "flops_per_launch": rot["flops_per_launch"], "avg_us_alone": rot["avg_us"],
                 "peak_source": ("FP64 ALU rate from unit counts and clocks: 152 SMs x 2 FMA/clk x "
                                 "2 flop x 2.07 GHz (MEASURED_PEAKS.json has no FP64 figure)"),
@@ -345,9 +363,17 @@ def run_ours(args):
                     key=lambda p: phase_ms[p])
     roofline["dominant_phase"] = dom_phase
 
-    cpu = None
+    cpu, err_vs_oracle = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ops, args.cpu_sample_ops)
+        # the oracle's eigenvalues of the sampled problems (the first problems of the sorted
+        # sequence, i.e. of the first chain) against the GPU's from the last timed step
+        got = main["last_ev"].detach().cpu().numpy()
+        errs = [float(np.max(np.abs(got[i] - ref) / np.abs(ref)))
+                for i, ref in enumerate(cpu.pop("evals"))]
+        err_vs_oracle = {"problems": len(errs), "max_rel_eig_err": max(errs),
+                         "oracle": "CPU FP64 ChFSI (Householder QR) of the same problems",
+                         "max_resid_all_pairs": main["max_resid"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -378,6 +404,9 @@ def run_ours(args):
         "ms_instrumented_step": instrumented["ms"],
         "plain_fp64": other,
         "speedup_vs_plain_fp64": (value / other["value"]) if other else None,
+        "plain_fp64_paper_form": paper_form,
+        "speedup_vs_paper_form": (value / paper_form["value"]) if paper_form else None,
+        "err_vs_oracle": err_vs_oracle,
         "roofline": roofline,
         "roofline_filter": roofline_filter,
         "roofline_filter_dram": roofline_dram,
@@ -413,7 +442,8 @@ def cpu_baseline(ops, sample_ops: int):
     return {"value": pairs / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"sort of all {len(ops)} problems (prorated) + chain solve of the first "
                       f"{sample_ops} sorted problem(s); numpy/LAPACK default thread pool",
-            "seconds": t_sort + t_solve, "iters": [r.iters for r in res]}
+            "seconds": t_sort + t_solve, "iters": [r.iters for r in res],
+            "evals": [r.evals for r in res]}
 
 
 def run_reference(args):
@@ -425,6 +455,7 @@ def run_reference(args):
     cb = None
     for _ in range(max(1, args.steps)):
         cb = cpu_baseline(ops, args.cpu_sample_ops)
+        cb.pop("evals")
         vals.append(cb["value"])
         secs.append(cb["seconds"])
     value = float(np.mean(vals))
@@ -455,8 +486,14 @@ def main():
     ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed",
                     help="headline form (default: the mixed form; plain FP64 is timed beside it)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
-    ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--degree-fp32", type=int, default=100, help="mixed form: FP32-phase degree")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--plain-degree", type=int, default=100,
+                    help="plain FP64 comparison: filter degree (its best on this workload)")
+    ap.add_argument("--plain-chunks", type=int, default=8,
+                    help="plain FP64 comparison: concurrent chains")
+    ap.add_argument("--no-paper-form", action="store_true",
+                    help="skip the paper's form (degree 20, one sequential chain)")
+    ap.add_argument("--degree-fp32", type=int, default=60, help="mixed form: FP32-phase degree")
     ap.add_argument("--degree-fp64", type=int, default=100, help="mixed form: FP64-phase degree")
     ap.add_argument("--switch-tol", type=float, default=0.0,
                     help="mixed form: wanted residual at which the FP32 phase hands over (0: off)")
