@@ -8,11 +8,10 @@
 //      1e-2 of that difference. In a warm-started chain this holds for every Rayleigh-Ritz
 //      matrix after the first of a problem (the block is already close to the Ritz
 //      vectors), and then the start is the identity;
-//   1. otherwise parallel cyclic Jacobi in FP32, one CTA, both k x k matrices in shared
-//      memory with an odd row stride (column accesses are bank-conflict free),
-//      round-robin (circle method) pair ordering: the k/2 disjoint rotations of a
-//      round are applied as one similarity transform, thread by thread over 2 x 2
-//      blocks, two barriers per round;
+//   1. otherwise an FP32 eigenbasis of the trailing block that holds the strongly coupled
+//      pairs (the probe returns its first index; the leading block keeps the identity):
+//      Householder tridiagonalisation in one CTA, then eigenvalues by multisection, vectors
+//      by inverse iteration and the back-transformation on many warps (trd.cuh);
 //   2. Ogita-Aishima refinement steps in FP64 (X' = X (I + E) with
 //      R = I - X^T X, S = X^T G X, lambda_i = s_ii/(1 - r_ii), E_ij =
 //      (s_ij + lambda_j r_ij)/(lambda_j - lambda_i), or r_ij/2 for pairs closer
@@ -23,7 +22,8 @@
 //      consecutive eigenvalues; each run (cluster) is diagonalised exactly by one warp
 //      (cyclic FP64 Jacobi on its small block) and its columns of X rotated along. Runs
 //      longer than kClusterMax fall back to exact FP64 round-robin Jacobi sweeps over
-//      the whole matrix;
+//      the whole matrix (one CTA, circle-method pair order: the k/2 disjoint rotations of
+//      a round applied as one similarity transform over 2 x 2 blocks);
 //   4. ascending sort of the pairs.
 #include <algorithm>
 
@@ -33,16 +33,15 @@ namespace scsf {
 namespace {
 
 // Refinement steps (each squares the error): from the probe's start (couplings below 1e-2
-// of the gaps, or FP32 Jacobi accuracy) three reach FP64, two the FP32 phase's accuracy;
-// the FP32 Jacobi result of a wide matrix carries more accumulated rounding (k - 1 rounds
-// per sweep), so it gets one more.
+// of the gaps, or the FP32 dense start's accuracy) three reach FP64, two the FP32 phase's
+// accuracy; the FP32 dense start of a wide matrix carries more accumulated rounding, so it
+// gets one more.
 constexpr int kOaSteps = 3;
 constexpr int kOaStepsF32 = 2;
 constexpr int kOaStepsWide = 4;
 constexpr float kNearDiag = 1e-2f;  // probe: largest |g_ij| / |g_jj - g_ii| of separated pairs
 constexpr int kClusterMax = 16;     // longest run one warp diagonalises
 constexpr int kClusterWarps = 8;    // warps that take runs (static shared memory: 35 KB)
-constexpr int kJacobiSweeps = 30;
 constexpr double kClusterFloor = 3e-3;  // relative gap below which pairs go to FP64 Jacobi
 constexpr double kCleanupTol = 1e-13;   // |P_pq| / ||G|| below which a pair counts as resolved
 
@@ -172,96 +171,7 @@ __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv,
   __syncthreads();
 }
 
-// Block-wide sums of two values (every thread gets the results).
-template <typename T>
-__device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    red[warp] = a;
-    red[32 + warp] = b;
-  }
-  __syncthreads();
-  a = 0;
-  b = 0;
-  for (int w = 0; w < nwarps; ++w) {
-    a += red[w];
-    b += red[32 + w];
-  }
-}
-
-// kWide: A and V live in global scratch `wide` (blocks wider than kSmallBlockWidth, whose
-// two k x k FP32 matrices exceed shared memory); otherwise in dynamic shared memory.
-template <bool kWide>
-__global__ void __launch_bounds__(1024)
-jacobi_f32_kernel(int k, const double* __restrict__ S, double* __restrict__ Z, int ldz,
-                  double* __restrict__ lam, int max_sweeps, float* __restrict__ wide,
-                  const int* __restrict__ start) {
-  // the leading block [0, t0) is already nearly diagonal (probe): Jacobi on [t0, k) only,
-  // the identity on the rest
-  const int t0 = start ? min(max(*start, 0), k) : 0;
-  const int kf = k;
-  k = kf - t0;
-  extern __shared__ float smf[];
-  const int ks = odd_stride(k > 0 ? k : 1);
-  float* A = kWide ? wide : smf;                      // k x ks
-  float* V = kWide ? wide + k * ks : smf + k * ks;    // k x ks
-  __shared__ float red[64];
-  __shared__ float s_al[kMaxBlockWidth + 1], s_be[kMaxBlockWidth + 1];
-  __shared__ int s_pl[kMaxBlockWidth + 2];
-  __shared__ int s_nrot;
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int e = t; e < kf * kf; e += nt) {
-    const int i = e / kf, j = e - i * kf;
-    if (i < t0 || j < t0) Z[(size_t)i * ldz + j] = (i == j) ? 1.0 : 0.0;
-  }
-  if (lam)
-    for (int i = t; i < t0; i += nt) lam[i] = S[(size_t)i * kf + i];
-  if (k <= 0) return;
-  for (int e = t; e < k * k; e += nt) {
-    const int i = e / k, j = e - i * k;
-    A[i * ks + j] = (float)S[(size_t)(t0 + i) * kf + t0 + j];
-    V[i * ks + j] = (i == j) ? 1.0f : 0.0f;
-  }
-  __syncthreads();
-  const int kp = (k + 1) & ~1;  // index k is a dummy player when k is odd
-  float prev_off = INFINITY;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    float off = 0.f, all = 0.f;
-    for (int e = t; e < k * k; e += nt) {
-      const int i = e / k, j = e - i * k;
-      const float a = A[i * ks + j];
-      all += a * a;
-      if (i != j) off += a * a;
-    }
-    block_sum2(off, all, red);
-    // converged to FP32 resolution, or stalled at the rounding floor (Jacobi converges
-    // linearly at first, so a stall only counts once the off-diagonal part is tiny).
-    // The refinement's cluster threshold scales with this residue, so it must be small.
-    if (off <= 1e-13f * all || (off < 1e-10f * all && off > 0.5f * prev_off)) break;
-    prev_off = off;
-    if (t == 0) s_nrot = 0;
-    __syncthreads();
-    for (int round = 0; round < kp - 1; ++round)
-      // threshold Jacobi: entries already at FP32 rounding level relative to their
-      // diagonal pair are left alone, so late sweeps rotate (and move) little
-      jacobi_round_blocks<float>(A, ks, V, ks, k, kp, round, [](float apq, float app, float aqq) {
-        return fabsf(apq) > 3e-8f * (fabsf(app) + fabsf(aqq)) && apq != 0.f;
-      }, s_al, s_be, s_pl, &s_nrot);
-    // a sweep without a single rotation above the threshold leaves nothing to do
-    if (s_nrot == 0) break;
-  }
-  for (int e = t; e < k * k; e += nt) {
-    const int i = e / k, j = e - i * k;
-    Z[(size_t)(t0 + i) * ldz + t0 + j] = (double)V[i * ks + j];
-  }
-  if (lam)
-    for (int i = t; i < k; i += nt) lam[t0 + i] = (double)A[i * ks + i];
-}
+#include "trd.cuh"
 
 // Norm pass of one Ogita-Aishima step (one CTA): lambda_i = s_ii / (1 - r_ii) and the
 // cluster threshold delta, from PQ = Z^T [S Z | Z] (k x 2k; P = left half, Q = right half).
@@ -585,7 +495,9 @@ sort_pairs_kernel(int k, const double* __restrict__ lam, const double* __restric
 struct EighScratch {
   double *S, *TZ0, *TZ1, *PQ, *E, *lam, *partials, *state;
   int* flags;  // [0] near-diagonal (probe), [1] cluster pass fell back
-  float* wide32;   // k > kSmallBlockWidth: the FP32 Jacobi matrices (2 k ks)
+  float *Hv, *dd, *ee, *lamt, *V32;  // tridiagonal start: reflectors, T, eigenpairs of T
+  int* skip;
+  float* trdA;     // k > kSmallBlockWidth: the FP32 block being reduced (k (k + 1))
   double* wide64;  // k > kSmallBlockWidth: the FP64 clean-up matrix (k ks)
 };
 
@@ -602,10 +514,16 @@ EighScratch carve_eigh(C& c, int k) {
   s.partials = c.template take<double>(gemm_tn_partials(k, k, 2 * k, false));
   s.state = c.template take<double>(4);
   s.flags = c.template take<int>(4);
-  s.wide32 = nullptr;
+  s.Hv = c.template take<float>(kk);
+  s.V32 = c.template take<float>(kk);
+  s.dd = c.template take<float>(k);
+  s.ee = c.template take<float>(k);
+  s.lamt = c.template take<float>(k);
+  s.skip = c.template take<int>(k);
+  s.trdA = nullptr;
   s.wide64 = nullptr;
   if (k > kSmallBlockWidth) {
-    s.wide32 = c.template take<float>(2 * (size_t)k * odd_stride(k));
+    s.trdA = c.template take<float>((size_t)k * (k + 1));
     s.wide64 = c.template take<double>((size_t)k * odd_stride(k));
   }
   return s;
@@ -625,17 +543,28 @@ cudaError_t set_smem(const void* fn, size_t bytes) {
 }
 
 
-cudaError_t run_jacobi_f32(int k, const double* S, double* Z, int ldz, double* lam,
-                           const EighScratch& w, cudaStream_t st, const int* near) {
+// Dense start on the trailing block the probe selected (Householder tridiagonalisation,
+// multisection, inverse iteration, back-transformation); the leading block gets the identity.
+cudaError_t run_trd(int k, const double* S, double* Z, int ldz, double* lam, const EighScratch& w,
+                    cudaStream_t st, const int* start) {
   cudaError_t e;
   if (k <= kSmallBlockWidth) {
-    const size_t smem32 = 2 * (size_t)k * odd_stride(k) * sizeof(float);
-    if ((e = set_smem((const void*)jacobi_f32_kernel<false>, smem32)) != cudaSuccess) return e;
-    jacobi_f32_kernel<false><<<1, 1024, smem32, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, nullptr,
-                                                       near);
+    const size_t smem = (size_t)k * (k + 1) * sizeof(float);
+    if ((e = set_smem((const void*)trd_reduce_kernel<false>, smem)) != cudaSuccess) return e;
+    trd_reduce_kernel<false><<<1, 1024, smem, st>>>(k, S, start, Z, ldz, lam, nullptr, w.Hv, w.dd,
+                                                     w.ee, w.skip);
   } else {
-    jacobi_f32_kernel<true><<<1, 1024, 0, st>>>(k, S, Z, ldz, lam, kJacobiSweeps, w.wide32, near);
+    trd_reduce_kernel<true><<<1, 1024, 0, st>>>(k, S, start, Z, ldz, lam, w.trdA, w.Hv, w.dd, w.ee,
+                                                w.skip);
   }
+  note_launch();
+  trd_eigval_kernel<<<(k + 7) / 8, 256, 0, st>>>(k, start, w.dd, w.ee, w.lamt);
+  note_launch();
+  const size_t vsmem = (size_t)kTrdWarpsPerBlock * 7 * k * sizeof(float);
+  trd_eigvec_kernel<<<(k + kTrdWarpsPerBlock - 1) / kTrdWarpsPerBlock, 32 * kTrdWarpsPerBlock,
+                      vsmem, st>>>(k, start, w.dd, w.ee, w.lamt, w.V32);
+  note_launch();
+  trd_back_kernel<<<(k + 7) / 8, 256, 0, st>>>(k, start, w.Hv, w.skip, w.V32, w.lamt, Z, ldz, lam);
   note_launch();
   return cudaGetLastError();
 }
@@ -662,7 +591,7 @@ cudaError_t run_cleanup_f64(int k, const double* PQ, double* Z, int ldz, double*
   return cudaGetLastError();
 }
 
-// Start (probe, then FP32 Jacobi unless nearly diagonal) and `steps` refinement steps on the
+// Start (probe, then the FP32 dense start on the block it selects) and `steps` refinement steps on the
 // symmetrised w.S; the eigenvectors end in the right half of the returned panel (ld 2k),
 // PQ = Z^T [S Z | Z] of the final Z in w.PQ.
 cudaError_t eigh_refined(int k, const EighScratch& w, int steps, double** TZout, cudaStream_t st) {
@@ -672,7 +601,7 @@ cudaError_t eigh_refined(int k, const EighScratch& w, int steps, double** TZout,
   note_launch();
   double* TZ = w.TZ0;
   double* TZn = w.TZ1;
-  if ((e = run_jacobi_f32(k, w.S, TZ + k, ld2, nullptr, w, st, w.flags)) != cudaSuccess) return e;
+  if ((e = run_trd(k, w.S, TZ + k, ld2, nullptr, w, st, w.flags)) != cudaSuccess) return e;
   for (int step = 0; step <= steps; ++step) {
     // T = S Z into the left half; PQ = Z^T [T | Z]
     if ((e = launch_gemm_nn(k, k, k, 1.0, w.S, k, TZ + k, ld2, 0.0, TZ, ld2, false, st)) != cudaSuccess)
