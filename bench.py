@@ -363,6 +363,11 @@ def run_ours(args):
                     key=lambda p: phase_ms[p])
     roofline["dominant_phase"] = dom_phase
 
+    other_configs = {}
+    if not args.no_k400:
+        other_configs["lapv256_k400"] = leg_lapv256_k400(args, rank, dev, ctx, st, hbm_peak)
+    if not args.no_batched:
+        other_configs["batched_uneven_64x32"] = leg_batched_uneven(args, rank, dev, ctx, st)
     cpu, err_vs_oracle = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ops, args.cpu_sample_ops)
@@ -407,6 +412,7 @@ def run_ours(args):
         "plain_fp64_paper_form": paper_form,
         "speedup_vs_paper_form": (value / paper_form["value"]) if paper_form else None,
         "err_vs_oracle": err_vs_oracle,
+        "other_configs": other_configs,
         "roofline": roofline,
         "roofline_filter": roofline_filter,
         "roofline_filter_dram": roofline_dram,
@@ -421,6 +427,120 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- other configurations
+def _nex_mult4(k: int) -> int:
+    """nex >= ceil(0.2 k) with k + nex a multiple of 4 (the mixed form's float4 block rows)."""
+    nex = -(-k // 5)
+    while (k + nex) % 4:
+        nex += 1
+    return nex
+
+
+def _timed_call(fn, dev, st):
+    import torch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    return out, e0.elapsed_time(e1)
+
+
+def leg_lapv256_k400(args, rank, dev, ctx, st, hbm_peak):
+    """The k = 400 workload: 1000 operators -Lap u + V u on 256 x 256 (V = 10 f, 12 x 12
+    modes), sorted on the GPU; a prefix of the sorted sequence solved in the mixed form as
+    concurrent chains. Every returned pair is checked at the FP64 residual 1e-8."""
+    import torch
+    import paper_2510_23215_gb300 as scsf
+    n, k, n_ops, prefix, chains = 256, 400, 1000, args.k400_prefix, args.k400_chains
+    ops = si.lap_plus_v_chain(n, n_ops, seed=2 + 1000 * rank)
+    fields = torch.as_tensor(np.stack([o.P for o in ops]), device=dev)
+    vs = torch.as_tensor(np.stack([o.V for o in ops]), device=dev)
+    params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32, tol=1e-8,
+                         seed=5 + rank, precision=scsf.MIXED)
+
+    def step(count, n_chains):
+        perm = scsf.sort(fields, p0=8, ctx=ctx).cpu().tolist()[:count]
+        dops = [scsf.Operator(scsf.LAP_PLUS_V, n, v=vs[i]) for i in perm]
+        b = np.linspace(0, count, n_chains + 1).round().astype(int)
+        res = scsf.solve_batched([(dops[x:y], params) for x, y in zip(b[:-1], b[1:]) if y > x],
+                                 concurrency=n_chains, ctx=ctx)
+        rs = torch.cat([r[1] for r in res])
+        return rs, [s_ for r in res for s_ in r[3]], perm
+
+    step(8, 2)  # warm-up: kernels, graphs, tuned launch widths
+    (rs, stats, perm), ms = _timed_call(lambda: step(prefix, chains), dev, st)
+    pairs = int((rs <= 1e-8).sum().item())
+    # in-run FP32 filter rate: one chain over the first problems with per-phase events
+    ctx.set_timing(True)
+    dops = [scsf.Operator(scsf.LAP_PLUS_V, n, v=vs[i]) for i in perm[:3]]
+    _, _, _, st3 = scsf.solve(dops, params, ctx=ctx)
+    ctx.set_timing(False)
+    t32 = sum(x["t_filter32_ms"] for x in st3) * 1e-3
+    by32 = 12.0 * sum(x["filter32_elems"] for x in st3)
+    gbs = by32 / t32 / 1e9 if t32 > 0 else None
+    return {
+        "workload": "lapv256_k400", "metric": METRIC, "unit": UNIT,
+        "value": pairs / (ms * 1e-3), "ms_per_step": ms, "steps": 1, "warmup": 1,
+        "pairs": pairs, "max_resid": float(rs.max().item()),
+        "config": {"grid": f"{n}x{n}", "N": n * n, "k": k, "block_width": scsf.block_width(k),
+                   "n_ops_sorted": n_ops, "solved_prefix": prefix, "chains": chains,
+                   "law": "V = 10 f, f = sum of 12 x 12 cosine modes, N(0,1) coefficients",
+                   "form": "mixed (FP32 phase + FP64 finish), block products on tensor cores",
+                   "degrees": {"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}},
+        "iters_per_op_mean": float(np.mean([x["iters"] for x in stats])),
+        "roofline_filter_in_run": {
+            "bound": "hbm", "kernel": "cheb_step_f32_kernel (per-step FP32 filter, blocks > L2)",
+            "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (gbs / hbm_peak) if gbs else None,
+            "note": "12 B per (node, column) per step over the FP32 filter's CUDA-event time "
+                    "inside one chain's solve of 3 problems"},
+    }
+
+
+def leg_batched_uneven(args, rank, dev, ctx, st):
+    """64 sorted chains of 32 operators each, grid side and k drawn per chain (n in 64..192,
+    k in 32..256), -div(a grad u) law; each chain sorted on the GPU and all chains solved by
+    one batched call (mixed form), every pair checked at 1e-8."""
+    import torch
+    import paper_2510_23215_gb300 as scsf
+    specs = si.batched_chain_specs(args.batched_chains, 32, seed=3 + 1000 * rank)
+    data = []
+    for sp in specs:
+        ops = si.div_a_grad_chain(sp.n, sp.n_ops, sp.seed)
+        data.append((sp, torch.as_tensor(np.stack([o.P for o in ops]), device=dev),
+                     torch.as_tensor(np.stack([o.ax for o in ops]), device=dev),
+                     torch.as_tensor(np.stack([o.ay for o in ops]), device=dev)))
+
+    def step(items):
+        chains = []
+        for sp, f, ax, ay in items:
+            perm = scsf.sort(f, p0=8, ctx=ctx).cpu().tolist()
+            dops = [scsf.Operator(scsf.DIV_A_GRAD, sp.n, ax=ax[i], ay=ay[i]) for i in perm]
+            chains.append((dops, scsf.Params(k=sp.k, nex=_nex_mult4(sp.k), degree=args.degree_fp64,
+                                             degree_fp32=args.degree_fp32, tol=1e-8, seed=sp.seed,
+                                             precision=scsf.MIXED)))
+        res = scsf.solve_batched(chains, concurrency=args.batched_concurrency, ctx=ctx)
+        return res
+
+    step(data[:8])  # warm-up
+    res, ms = _timed_call(lambda: step(data), dev, st)
+    pairs = sum(int((r[1] <= 1e-8).sum().item()) for r in res)
+    want = sum(sp.k * sp.n_ops for sp, *_ in data)
+    return {
+        "workload": "batched_uneven_64x32", "metric": METRIC, "unit": UNIT,
+        "value": pairs / (ms * 1e-3), "ms_per_step": ms, "steps": 1, "warmup": 1,
+        "pairs": pairs, "pairs_wanted": want,
+        "max_resid": max(float(r[1].max().item()) for r in res),
+        "statuses": sorted({int(r[4]) for r in res}),
+        "config": {"chains": len(data), "ops_per_chain": 32, "n_range": [64, 192],
+                   "k_range": [32, 256], "concurrency": args.batched_concurrency,
+                   "form": "mixed, one batched call (worker threads, one stream each)",
+                   "degrees": {"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}},
+    }
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -502,6 +622,13 @@ def main():
     ap.add_argument("--concurrency", type=int, default=0,
                     help="chains in flight at once (0: all chunks; more chunks than slots "
                          "balance uneven chains)")
+    ap.add_argument("--no-k400", action="store_true", help="skip the 256 x 256, k = 400 leg")
+    ap.add_argument("--k400-prefix", type=int, default=64,
+                    help="k = 400 leg: solved prefix of the 1000 sorted problems")
+    ap.add_argument("--k400-chains", type=int, default=4, help="k = 400 leg: concurrent chains")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-chain uneven leg")
+    ap.add_argument("--batched-chains", type=int, default=64)
+    ap.add_argument("--batched-concurrency", type=int, default=8)
     ap.add_argument("--n-ops", type=int, default=None,
                     help="problems per batch (default 200; smaller only for profiler captures)")
     args = ap.parse_args()

@@ -152,6 +152,9 @@ typedef struct {
   const double* val;       /* SCSF_OP_CSR                              */
   const double* plate_d;   /* SCSF_OP_PLATE: D   [n][n]                */
   const double* plate_rho; /* SCSF_OP_PLATE: rho [n][n]                */
+  const double* field;     /* the problem's parameter field P [n][n] at the nodes (the sort
+                              input: a for SCSF_OP_DIV_A_GRAD, V for SCSF_OP_LAP_PLUS_V); read
+                              only by chain heads when params.use_proposal, NULL otherwise */
 } scsf_operator;
 
 /* SCSF_FP64: Alg. 3 as written, every step in FP64.
@@ -189,6 +192,14 @@ typedef struct {
   double switch_tol; /* SCSF_MIXED: leave the FP32 phase once every wanted residual is at
                         or below this (> 0), besides the FP32-floor and stall rules       */
   int products;      /* scsf_product_method of the block products                         */
+  int use_proposal;  /* 1: chain heads start from the learned proposal (see scsf_proposal_*):
+                        64 block columns from the network's coarse subspace prolonged to the
+                        grid, the rest from the seeded Philox block, and filter bounds from
+                        its predicted log(lambda_1), log(lambda_64) with lambda_kb taken as
+                        lambda_64 k_b / 64 (2-D Weyl law). Needs stencil operators with
+                        n a multiple of 32, k_b >= 64 and op->field set at heads           */
+  const float* proposal; /* use_proposal: the network's FP32 parameters (device,
+                        scsf_proposal_param_count() floats), read at every head           */
 } scsf_params;
 
 typedef struct {
@@ -279,6 +290,15 @@ scsf_status scsf_chain_create_rows(scsf_ctx* ctx, const scsf_params* params, int
 scsf_status scsf_chain_seed(scsf_chain* chain, const double* block, const double* ritz_host);
 scsf_status scsf_chain_step(scsf_chain* chain, const scsf_operator* op, double* evals,
                             double* resid, double* evecs, scsf_stats* stats);
+/* The next scsf_chain_step starts as a chain head (Gaussian block, or the learned proposal
+ * with params.use_proposal) instead of from the previous problem's block: for a step whose
+ * sorted predecessor is far away (scsf_far_steps). */
+scsf_status scsf_chain_restart(scsf_chain* chain);
+/* Far steps of a sorted chain (host arrays): dist[n_ops] = the squared feature distances
+ * from scsf_sort_dist (dist[0] = 0 for the head); far[0] = 1, and far[i] = 1 for i >= 1 when
+ * dist[i] is above the `quantile` (0..1) of dist[1..n_ops-1] (linear interpolation between
+ * order statistics), else 0. Those steps are restarted from the learned proposal. */
+scsf_status scsf_far_steps(const double* dist, int64_t n_ops, double quantile, int32_t* far);
 void scsf_chain_destroy(scsf_chain* chain);
 
 /* Solve n_ops problems (same n; or all SCSF_OP_CSR with the same rows) in the given

@@ -51,6 +51,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_targets", "scsf_proposal_prolong",
     "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist", "scsf_block_rotate",
     "scsf_block_product_scratch", "scsf_block_gram", "scsf_block_rotate_ex",
+    "scsf_chain_restart", "scsf_far_steps",
 ]
 
 
@@ -64,14 +65,16 @@ class _COperator(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("ax", ctypes.c_void_p),
                 ("ay", ctypes.c_void_p), ("v", ctypes.c_void_p), ("rows", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
-                ("plate_d", ctypes.c_void_p), ("plate_rho", ctypes.c_void_p)]
+                ("plate_d", ctypes.c_void_p), ("plate_rho", ctypes.c_void_p),
+                ("field", ctypes.c_void_p)]
 
 
 class _CParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nex", ctypes.c_int), ("degree", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int),
-                ("switch_tol", ctypes.c_double), ("products", ctypes.c_int)]
+                ("switch_tol", ctypes.c_double), ("products", ctypes.c_int),
+                ("use_proposal", ctypes.c_int), ("proposal", ctypes.c_void_p)]
 
 
 class _CStats(ctypes.Structure):
@@ -188,6 +191,10 @@ def library() -> ctypes.CDLL:
     L.scsf_block_rotate_ex.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, dbl, dbl, i32, i32, vp,
                                        i32, vp, sz]
     L.scsf_block_rotate_ex.restype = ctypes.c_int
+    L.scsf_chain_restart.argtypes = [vp]
+    L.scsf_chain_restart.restype = ctypes.c_int
+    L.scsf_far_steps.argtypes = [ctypes.POINTER(dbl), i64, dbl, ctypes.POINTER(i32)]
+    L.scsf_far_steps.restype = ctypes.c_int
     for name in EXPORTED_SYMBOLS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int or name in (
@@ -237,6 +244,7 @@ class Operator:
     val: Optional[torch.Tensor] = None      # [nnz] FP64
     D: Optional[torch.Tensor] = None        # [n, n] (PLATE)
     rho: Optional[torch.Tensor] = None      # [n, n] (PLATE)
+    field: Optional[torch.Tensor] = None    # [n, n] parameter field (learned-proposal heads)
 
     @staticmethod
     def csr(row_ptr, col, val, device="cuda") -> "Operator":
@@ -262,9 +270,10 @@ class Operator:
         if hasattr(op, "ax"):
             return Operator(DIV_A_GRAD, op.n,
                             ax=torch.as_tensor(op.ax, dtype=torch.float64, device=device).contiguous(),
-                            ay=torch.as_tensor(op.ay, dtype=torch.float64, device=device).contiguous())
-        return Operator(LAP_PLUS_V, op.n,
-                        v=torch.as_tensor(op.V, dtype=torch.float64, device=device).contiguous())
+                            ay=torch.as_tensor(op.ay, dtype=torch.float64, device=device).contiguous(),
+                            field=torch.as_tensor(op.P, dtype=torch.float64, device=device).contiguous())
+        v = torch.as_tensor(op.V, dtype=torch.float64, device=device).contiguous()
+        return Operator(LAP_PLUS_V, op.n, v=v, field=v)
 
     def _c(self) -> _COperator:
         if self.kind == DIV_A_GRAD:
@@ -289,9 +298,13 @@ class Operator:
                 raise ValueError("row_ptr must have rows + 1 entries and col / val nnz each")
         else:
             raise ValueError(f"unknown operator kind {self.kind}")
+        if self.field is not None:
+            _check(self.field, "field")
+            if tuple(self.field.shape) != (self.n, self.n):
+                raise ValueError("field must be [n, n]")
         return _COperator(self.kind, self.n, _ptr(self.ax), _ptr(self.ay), _ptr(self.v),
                           self.rows, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val),
-                          _ptr(self.D), _ptr(self.rho))
+                          _ptr(self.D), _ptr(self.rho), _ptr(self.field))
 
     @property
     def device(self):
@@ -310,11 +323,14 @@ class Params:
     degree_fp32: int = 0   # MIXED: degree of the FP32 phase (0: same as degree)
     switch_tol: float = 0.0  # MIXED: leave the FP32 phase at this wanted residual (0: off)
     products: int = PRODUCT_TENSOR  # block products on the tensor cores (or PRODUCT_FP64)
+    proposal: Optional["Proposal"] = None  # chain heads start from this learned proposal
 
     def _c(self) -> _CParams:
+        use = self.proposal is not None
         return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
                         self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32, self.switch_tol,
-                        self.products)
+                        self.products, 1 if use else 0,
+                        self.proposal.params.data_ptr() if use else None)
 
     @property
     def kb(self) -> int:
@@ -463,6 +479,10 @@ class Chain:
         arr = (ctypes.c_double * kb)(*[float(x) for x in ritz])
         self.ctx.check(library().scsf_chain_seed(self._h, block.data_ptr(), arr))
 
+    def restart(self):
+        """The next step starts as a chain head (the learned proposal when the params have one)."""
+        self.ctx.check(library().scsf_chain_restart(self._h))
+
     def step(self, op: Operator, want_vectors: bool = True, raise_on_nonconvergence: bool = True,
              history: bool = False):
         """Solves the next problem. With history=True, stats["history"] lists per outer
@@ -497,6 +517,19 @@ class Chain:
             self.close()
         except Exception:
             pass
+
+
+def far_steps(dist, quantile: float = 0.9) -> List[bool]:
+    """scsf_far_steps: the head and every step whose squared feature distance to its sorted
+    predecessor is above the given quantile of the chain's step distances."""
+    d = [float(x) for x in (dist.tolist() if hasattr(dist, "tolist") else dist)]
+    n = len(d)
+    arr = (ctypes.c_double * n)(*d)
+    out = (ctypes.c_int32 * n)()
+    st = library().scsf_far_steps(arr, n, float(quantile), out)
+    if st != OK:
+        raise ScsfError(st, "scsf_far_steps: bad arguments")
+    return [bool(x) for x in out]
 
 
 def _product_scratch(rows: int, kmax: int, slices: int, device) -> torch.Tensor:
@@ -740,7 +773,8 @@ class Proposal:
 
     forward(fields) -> (bounds [B, 2] log(lambda_1), log(lambda_64); block [B, 1024, 64])
     train_step(fields, t_bounds, t_Q, lr) -> (subspace, orthonormality, bounds) loss terms
-    head_block(field, n, kb, seed) -> (FP64 [n*n, kb] start block, Ritz estimates) for Chain.seed
+    Params(..., proposal=this) makes every chain head start from the proposal; the library
+    composes the head block (scsf_params.use_proposal).
     """
 
     COARSE, KY = 32, 64
@@ -808,22 +842,3 @@ class Proposal:
         self.ctx.check(L.scsf_proposal_targets(self.ctx.handle, evecs.data_ptr(), B, n, lde,
                                                Q.data_ptr(), scratch.data_ptr(), scratch.numel()))
         return Q
-
-    def head_block(self, field: torch.Tensor, n: int, kb: int, seed: int = 0):
-        """Start block for a chain head: 64 prolonged proposal columns, the rest Gaussian
-        (seeded), and Ritz estimates spanning [lambda_1, lambda_kb]. The network predicts
-        lambda_1 and lambda_64; lambda_kb is extrapolated by the 2-D Weyl law (the
-        eigenvalue count grows linearly in lambda), lambda_kb ~ lambda_64 kb / 64, so the
-        filter's damped interval starts above the whole block."""
-        bounds, block = self.forward(field.reshape(1, *field.shape).contiguous())
-        fine = torch.empty((n * n, kb), dtype=torch.float64, device=self.ctx.device)
-        if kb > self.KY:
-            g = torch.Generator(device="cpu").manual_seed(seed)
-            fine[:, self.KY:] = torch.randn((n * n, kb - self.KY), generator=g,
-                                            dtype=torch.float64).to(self.ctx.device)
-        self.ctx.check(library().scsf_proposal_prolong(self.ctx.handle, block.data_ptr(), 1, n,
-                                                       fine.data_ptr(), kb))
-        lo, hi = [math.exp(float(x)) for x in bounds[0].cpu()]
-        hi = max(hi * kb / self.KY, hi)
-        ritz = [lo + (hi - lo) * i / (kb - 1) for i in range(kb)]
-        return fine, ritz

@@ -139,11 +139,15 @@ struct ChainBufs {
   // tensor-core block products: digit planes, exponents and exact split partials
   void* oz;
   size_t oz_bytes;
+  // learned proposal at chain heads: network workspace, predicted log-bounds, coarse block
+  void* prop_ws;
+  size_t prop_ws_bytes;
+  float *prop_bounds, *prop_block;
 };
 
 template <typename Cv>
 void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, bool tensor,
-                 ChainBufs& b) {
+                 bool proposal, ChainBufs& b) {
   const size_t blk = N * kb;
   const size_t kk = (size_t)kb * kb;
   const int T = (kb + kGemmTile - 1) / kGemmTile;
@@ -174,6 +178,15 @@ void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, bo
   if (tensor) {
     b.oz_bytes = oz_scratch_bytes((int)N, kb, kOzSlicesF64);
     b.oz = c.template take<char>(b.oz_bytes);
+  }
+  b.prop_ws = nullptr;
+  b.prop_ws_bytes = 0;
+  b.prop_bounds = b.prop_block = nullptr;
+  if (proposal) {
+    b.prop_ws_bytes = scsf_proposal_workspace_size(1);
+    b.prop_ws = c.template take<char>(b.prop_ws_bytes);
+    b.prop_bounds = c.template take<float>(2);
+    b.prop_block = c.template take<float>(1024 * 64);
   }
   b.prp = b.pci = nullptr;
   b.pval = nullptr;
@@ -607,7 +620,7 @@ size_t scsf_solve_workspace_size(const scsf_params* params, int n_max) {
   ChainBufs b;
   const bool mixed = params->precision == SCSF_MIXED;
   carve_chain(c, (size_t)n_max * n_max, kb, mixed, params->degree, !mixed,
-              params->products == SCSF_PRODUCT_TENSOR, b);
+              params->products == SCSF_PRODUCT_TENSOR, params->use_proposal != 0, b);
   return c.used;
 }
 
@@ -618,7 +631,7 @@ size_t scsf_solve_workspace_size_rows(const scsf_params* params, int64_t rows) {
   SizeCarve c;
   ChainBufs b;
   carve_chain(c, (size_t)rows, kb, false, params->degree, false,
-              params->products == SCSF_PRODUCT_TENSOR, b);
+              params->products == SCSF_PRODUCT_TENSOR, false, b);
   return c.used;
 }
 
@@ -645,6 +658,11 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
   if (params->products != SCSF_PRODUCT_TENSOR && params->products != SCSF_PRODUCT_FP64)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "products must be SCSF_PRODUCT_TENSOR or SCSF_PRODUCT_FP64");
+  if (params->use_proposal &&
+      (!params->proposal || n < 32 || n % 32 != 0 || kb < 64))
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "use_proposal needs the network parameters, a stencil chain with n a multiple "
+                "of 32 and k + nex >= 64");
   if (params->precision == SCSF_MIXED && n == 0)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "SCSF_MIXED needs a stencil operator (its FP32 filters are stencil kernels)");
@@ -663,7 +681,7 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
   Carve c(workspace, workspace_bytes);
   const bool mixed = params->precision == SCSF_MIXED;
   carve_chain(c, (size_t)N, kb, mixed, params->degree, n > 0 && !mixed,
-              params->products == SCSF_PRODUCT_TENSOR, ch->b);
+              params->products == SCSF_PRODUCT_TENSOR, params->use_proposal != 0, ch->b);
   if (!c.ok) {
     delete ch;
     return fail(ctx, SCSF_ERR_NO_MEMORY, "solve workspace too small");
@@ -693,6 +711,27 @@ scsf_status scsf_chain_create_rows(scsf_ctx* ctx, const scsf_params* params, int
 }
 
 void scsf_chain_destroy(scsf_chain* chain) { delete chain; }
+
+scsf_status scsf_chain_restart(scsf_chain* ch) {
+  if (!ch) return SCSF_ERR_INVALID_ARG;
+  ch->has_block = false;
+  return SCSF_OK;
+}
+
+scsf_status scsf_far_steps(const double* dist, int64_t n_ops, double quantile, int32_t* far) {
+  if (!dist || !far || n_ops < 1 || !(quantile >= 0.0 && quantile <= 1.0))
+    return SCSF_ERR_INVALID_ARG;
+  far[0] = 1;
+  if (n_ops == 1) return SCSF_OK;
+  std::vector<double> v(dist + 1, dist + n_ops);
+  std::sort(v.begin(), v.end());
+  const double pos = quantile * (double)(v.size() - 1);
+  const size_t lo = (size_t)std::floor(pos);
+  const size_t hi = std::min(lo + 1, v.size() - 1);
+  const double thr = v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+  for (int64_t i = 1; i < n_ops; ++i) far[i] = dist[i] > thr ? 1 : 0;
+  return SCSF_OK;
+}
 
 scsf_status scsf_chain_seed(scsf_chain* ch, const double* block, const double* ritz_host) {
   if (!ch) return SCSF_ERR_INVALID_ARG;
@@ -753,7 +792,24 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
                 "operator has non-finite coefficients (NaN or Inf; for the plate, rho <= 0)");
   const double beta = hi;
   double lam, alpha;
-  if (!ch->has_block) {  // head of the chain: random block (Sec. 3.2)
+  if (!ch->has_block && ch->p.use_proposal) {
+    // head from the learned proposal: the network's coarse subspace prolonged to the grid
+    // in columns 0..63, the seeded Gaussian block in the rest; filter bounds from its
+    // predicted log(lambda_1), log(lambda_64), lambda_kb ~ lambda_64 k_b / 64 (2-D Weyl law)
+    if (!op->field)
+      return fail(ctx, SCSF_ERR_INVALID_ARG, "use_proposal: the head operator has no field");
+    scsf_status ps = scsf_proposal_forward(ctx, ch->p.proposal, op->field, 1, n, b.prop_bounds,
+                                           b.prop_block, b.prop_ws, b.prop_ws_bytes);
+    if (ps != SCSF_OK) return ps;
+    if ((ps = scsf_proposal_prolong(ctx, b.prop_block, 1, n, b.V, kb)) != SCSF_OK) return ps;
+    if (kb > 64) SCSF_CUDA(ctx, launch_philox_normal(b.V + 64, N, kb - 64, kb, ch->p.seed, st));
+    float* hb = reinterpret_cast<float*>(h + 8);
+    SCSF_CUDA(ctx, cudaMemcpyAsync(hb, b.prop_bounds, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+    const double l1 = std::exp((double)hb[0]), l64 = std::exp((double)hb[1]);
+    lam = std::isfinite(l1) ? std::max(l1, lo) : lo;
+    alpha = std::isfinite(l64) ? std::max(l64 * kb / 64.0, l64) : lo + 2.0 * ((double)kb / N) * (hi - lo);
+  } else if (!ch->has_block) {  // head of the chain: random block (Sec. 3.2)
     SCSF_CUDA(ctx, launch_philox_normal(b.V, N, kb, kb, ch->p.seed, st));
     lam = lo;
     alpha = lo + 2.0 * ((double)kb / N) * (hi - lo);

@@ -6,21 +6,23 @@ every operator are pooled to the 32 x 32 coarse grid and orthonormalised (the
 targets); log(lambda_1) and log(lambda_64) are the bound targets. The network is
 trained with Adam on a cosine learning-rate schedule, and evaluated by solving
 held-out operators as chain heads twice: from the seeded Gaussian block (Sec. 3.2)
-and from the proposal block. Both runs must reach the same residual tolerance; the
-difference in filter iterations is the gain.
+and from the proposal (the library composes the head block from the network's output).
+Both runs must reach the same residual tolerance; the difference in filter iterations is
+the gain.
 
     python -m paper_2510_23215_gb300.proposal_train --n 128 --train 5000 --test 500
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import time
 
 import numpy as np
 import torch
 
-from . import Chain, Operator, Params, Proposal, solve_batched, sort
+from . import Chain, Operator, Params, Proposal, far_steps, solve_batched, sort
 
 
 def label(ops, n: int, params: Params, device, chunk: int = 256, chain_len: int = 16,
@@ -54,18 +56,17 @@ def train(prop: Proposal, fields, Q, tb, steps: int, batch: int = 32, lr: float 
     return hist
 
 
-def head_iterations(prop: Proposal, ops, fields, n: int, params: Params, device):
-    """Filter iterations of each operator solved as a chain head from the Gaussian
-    block and from the proposal, with the largest final residual of each."""
+def head_iterations(prop: Proposal, ops, params: Params, device):
+    """Filter iterations of each operator solved as a chain head, once from the Gaussian
+    block (Sec. 3.2) and once from the proposal (the library composes the proposal's head
+    block: scsf_params.use_proposal), with the largest final residual of each."""
     out = {"random": [], "proposal": [], "resid_random": 0.0, "resid_proposal": 0.0}
     for j, o in enumerate(ops):
         op = Operator.from_workload(o, device)
-        ch = Chain(params, n, device=device)
-        _, r1, _, st1 = ch.step(op, want_vectors=False)
-        block, ritz = prop.head_block(fields[j], n, params.kb, seed=j)
-        ch2 = Chain(params, n, device=device)
-        ch2.seed(block, ritz)
-        _, r2, _, st2 = ch2.step(op, want_vectors=False)
+        p_rand = dataclasses.replace(params, seed=1000 + j, proposal=None)
+        p_prop = dataclasses.replace(params, seed=1000 + j, proposal=prop)
+        _, r1, _, st1 = Chain(p_rand, o.n, device=device).step(op, want_vectors=False)
+        _, r2, _, st2 = Chain(p_prop, o.n, device=device).step(op, want_vectors=False)
         out["random"].append(int(st1["iters"]))
         out["proposal"].append(int(st2["iters"]))
         out["resid_random"] = max(out["resid_random"], float(r1.max()))
@@ -75,23 +76,22 @@ def head_iterations(prop: Proposal, ops, fields, n: int, params: Params, device)
 
 def solve_chain_with_proposal(ops, prop: Proposal, params: Params, device, p0: int = 8,
                               quantile: float = 0.9):
-    """Sort the operators (Alg. 2) and solve them in that order as one warm-started chain,
-    seeding the head and every far step -- a step whose squared feature distance to its
-    predecessor is above the given quantile of the chain's step distances -- from the
-    proposal block instead of the predecessor's. Returns (perm, seeded positions,
-    [(evals, resid, stats)] in chain order)."""
+    """Sort the operators (Alg. 2) and solve them in that order as one warm-started chain
+    whose head and far steps -- steps whose squared feature distance to their predecessor
+    is above the given quantile of the chain's step distances (scsf_far_steps) -- restart
+    from the proposal instead of the predecessor's block. Returns (perm, restarted
+    positions, [(evals, resid, stats)] in chain order)."""
     n = ops[0].n
     fields = torch.as_tensor(np.stack([o.P for o in ops]), device=device)
     perm, dist = sort(fields, p0=p0, return_distances=True)
     perm = perm.cpu().tolist()
-    dist = dist.cpu().numpy()
-    thr = float(np.quantile(dist[1:], quantile)) if len(ops) > 1 else float("inf")
-    ch = Chain(params, n, device=device)
+    far = far_steps(dist.cpu(), quantile)
+    ch = Chain(dataclasses.replace(params, proposal=prop), n, device=device)
     seeded, out = [], []
     for pos, j in enumerate(perm):
-        if pos == 0 or dist[pos] > thr:
-            block, ritz = prop.head_block(fields[j], n, params.kb, seed=j)
-            ch.seed(block, ritz)
+        if far[pos]:
+            if pos > 0:
+                ch.restart()
             seeded.append(pos)
         ev, rs, _, st = ch.step(Operator.from_workload(ops[j], device), want_vectors=False)
         out.append((ev, rs, st))
@@ -99,7 +99,10 @@ def solve_chain_with_proposal(ops, prop: Proposal, params: Params, device, p0: i
 
 
 def run(n: int, n_train: int, n_test: int, steps: int, degree: int, lr: float, seed: int,
-        device="cuda", log_every: int = 0):
+        device="cuda", log_every: int = 0, k_eval: int = Proposal.KY):
+    """Label, train and evaluate. Labels are the 64 lowest eigenpairs; the held-out heads
+    are solved for the k_eval smallest pairs (k_eval = 53 makes the block width 64, all of
+    it from the proposal)."""
     import scsf_inputs as si  # seeded operator generators (no method arithmetic)
     device = torch.device(device)
     params = Params(k=Proposal.KY, degree=degree, tol=1e-8, max_iter=400)
@@ -114,9 +117,10 @@ def run(n: int, n_train: int, n_test: int, steps: int, degree: int, lr: float, s
     t_train = time.time() - t0
     te = slice(n_train, n_train + min(n_test, 256))
     held, _ = prop.gradient(fields[te].contiguous(), tb[te].contiguous(), Q[te].contiguous())
-    its = head_iterations(prop, ops[n_train:], fields[n_train:], n, params, device)
+    p_eval = dataclasses.replace(params, k=k_eval)
+    its = head_iterations(prop, ops[n_train:], p_eval, device)
     return {
-        "n": n, "k": Proposal.KY, "kb": params.kb, "degree": degree, "train": n_train,
+        "n": n, "k": k_eval, "kb": p_eval.kb, "degree": degree, "train": n_train,
         "test": n_test, "steps": steps, "label_s": round(t_label, 1), "train_s": round(t_train, 1),
         "heldout_loss": [round(x, 5) for x in held], "train_log": hist,
         "mean_iters_random": float(np.mean(its["random"])),
@@ -135,8 +139,11 @@ def main():
     ap.add_argument("--degree", type=int, default=20)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=77)
+    ap.add_argument("--k-eval", type=int, default=Proposal.KY,
+                    help="eigenpairs solved for at the held-out heads")
     a = ap.parse_args()
-    r = run(a.n, a.train, a.test, a.steps, a.degree, a.lr, a.seed, log_every=max(1, a.steps // 8))
+    r = run(a.n, a.train, a.test, a.steps, a.degree, a.lr, a.seed, log_every=max(1, a.steps // 8),
+            k_eval=a.k_eval)
     print(json.dumps(r))
 
 

@@ -138,24 +138,22 @@ def test_prolongation_reproduces_bilinear_functions_inside():
 
 
 def test_trained_proposal_gain_on_heldout_heads():
-    """Train on 320 plain solves (64 x 64 grids, k = 64), then solve 16 held-out
-    operators as chain heads from the Gaussian block and from the proposal. The
-    network must have learned the subspace (held-out sum of squared principal-angle
-    sines far below the 64 of an unrelated block) and the bounds; both starts must
-    reach the tolerance. The measured gain is printed; it is small on this field law
-    (the bilinear prolongation of a 32 x 32 block bounds the start error of the
-    highest wanted vectors), so the check is that the proposal costs at most one
-    iteration on average."""
+    """Train on 320 plain solves (64 x 64 grids, labels: the 64 lowest eigenpairs), then solve
+    16 held-out operators as chain heads for k = 53 (block width 64, every column from the
+    proposal; the library composes the head block) from the Gaussian block and from the
+    proposal. The network must have learned the subspace (held-out sum of squared
+    principal-angle sines far below the 64 of an unrelated block) and the bounds, both starts
+    must reach the tolerance, and the proposal must take fewer filter iterations."""
     dev = need_gpu()
     from paper_2510_23215_gb300 import proposal_train
     r = proposal_train.run(n=64, n_train=320, n_test=16, steps=800, degree=20, lr=1e-3, seed=77,
-                           device=dev)
+                           device=dev, k_eval=53)
     print("proposal gain:", {k: r[k] for k in ("heldout_loss", "mean_iters_random", "mean_iters_proposal")})
     sub, _, bounds = r["heldout_loss"]
     assert sub < 6.4
     assert bounds < 0.02
     assert r["resid_random"] <= 1e-8 and r["resid_proposal"] <= 1e-8
-    assert r["mean_iters_proposal"] <= r["mean_iters_random"] + 1.0
+    assert r["mean_iters_proposal"] < r["mean_iters_random"]
 
 
 def test_chain_seeds_head_and_far_steps_from_the_proposal():

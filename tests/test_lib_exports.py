@@ -98,3 +98,19 @@ def test_operator_descriptors_refuse_host_tensors_and_bad_shapes():
         bad._c()
     with pytest.raises(ValueError):
         scsf.Operator(99, 4)._c()
+
+
+def test_far_steps_rule_matches_numpy_quantile():
+    """scsf_far_steps (host code): the head and the steps above the quantile of the step
+    distances (numpy's default linear interpolation) restart from the proposal."""
+    import numpy as np
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(4)
+    for n, q in ((21, 0.9), (2, 0.9), (57, 0.5), (10, 1.0), (10, 0.0)):
+        d = np.concatenate([[0.0], rng.exponential(size=n - 1)])
+        far = scsf.far_steps(d, q)
+        thr = np.quantile(d[1:], q)
+        assert far[0] and far[1:] == [bool(x > thr) for x in d[1:]]
+    assert scsf.far_steps([0.0], 0.9) == [True]
+    with pytest.raises(scsf.ScsfError):
+        scsf.far_steps([0.0, 1.0], 1.5)
