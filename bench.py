@@ -6,7 +6,7 @@ operators on a 128 x 128 grid (p0 = 8), then solve them in sorted order, each pr
 warm-started from its predecessor, for the k = 100 smallest eigenpairs (tol 1e-8). The timed
 form is the mixed one (FP32 phase, then FP64 phase with the defect-corrected filter; block
 products on the tensor cores), with the sorted sequence cut into 8 chains solved
-concurrently. Beside it: the plain FP64 form at its own best degree and the same 8 chains
+concurrently, each chain head started from the learned proposal (trained before timing). Beside it: the plain FP64 form at its own best degree and the same 8 chains
 (the tuned comparison), and the paper's form as written (degree 20, one sequential chain).
 Each rank runs its own batch (weak scaling, no data-path collective).
 
@@ -171,6 +171,9 @@ def run_ours(args):
     forms = {"mixed": scsf.MIXED, "fp64": scsf.FP64}
     chosen = args.form
     ops = _workload_ops(rank)
+    prop, proposal_leg = None, None
+    if not args.no_proposal:
+        prop, proposal_leg = leg_learned_proposal(args, rank, dev)
     # host copies (pinned) for the end-to-end leg; device copies resident for the kernel leg
     h_fields = torch.from_numpy(np.stack([o.P for o in ops])).pin_memory()
     h_ax = torch.from_numpy(np.stack([o.ax for o in ops])).pin_memory()
@@ -183,15 +186,15 @@ def run_ours(args):
     st = torch.cuda.current_stream(dev)
 
     def step(fields, ax, ay, precision, chunks=1, degree=None):
-        if precision == scsf.MIXED:  # the chosen form tunes its filter degrees
+        if precision == scsf.MIXED:  # the chosen form: tuned degrees, proposal at chain heads
             params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32,
                                  tol=w["tol"], seed=7 + rank, precision=precision,
-                                 switch_tol=args.switch_tol)
+                                 switch_tol=args.switch_tol, proposal=prop)
         else:                        # the plain form: its own degree (default: the workload's)
             params = scsf.Params(k=k, degree=degree or w["degree"], tol=w["tol"], seed=7 + rank,
                                  precision=precision)
         perm = scsf.sort(fields, p0=w["p0"], start=0, ctx=ctx).cpu().tolist()
-        dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i]) for i in perm]
+        dops = [scsf.Operator(scsf.DIV_A_GRAD, n, ax=ax[i], ay=ay[i], field=fields[i]) for i in perm]
         if chunks <= 1:
             ev, rs, _, stats = scsf.solve(dops, params, ctx=ctx)
             return ev, rs, stats
@@ -388,7 +391,8 @@ def run_ours(args):
         "config": {"workload": w["name"], "grid": f"{n}x{n}", "N": n * n, "n_ops_per_gpu": n_ops,
                    "k": k, "block_width": scsf.block_width(k), "degree": w["degree"], "p0": w["p0"],
                    "tol": w["tol"],
-                   "form": {"mixed": "mixed: FP32 phase + FP64 finish",
+                   "form": {"mixed": "mixed: FP32 phase + FP64 finish" + (
+                                "; chain heads from the learned proposal" if prop else ""),
                             "fp64": "plain FP64"}[chosen] + (
                        f"; sorted sequence cut into {args.chunks} chains solved concurrently"
                        if args.chunks > 1 else "; one sequential chain"),
@@ -413,6 +417,7 @@ def run_ours(args):
         "speedup_vs_paper_form": (value / paper_form["value"]) if paper_form else None,
         "err_vs_oracle": err_vs_oracle,
         "other_configs": other_configs,
+        "learned_proposal": proposal_leg,
         "roofline": roofline,
         "roofline_filter": roofline_filter,
         "roofline_filter_dram": roofline_dram,
@@ -543,6 +548,48 @@ def leg_batched_uneven(args, rank, dev, ctx, st):
     }
 
 
+def leg_learned_proposal(args, rank, dev):
+    """The learned head proposal on the 128 x 128 -div(a grad u) law: labels from the plain
+    method (the 64 lowest eigenpairs of each training operator), Adam training of the
+    library's network, then held-out operators solved as chain heads (k = 53, block width
+    64, every column from the proposal) from the Gaussian block and from the proposal.
+    Returns the trained proposal (used at every chain head of the chosen form) and the
+    held-out comparison."""
+    import dataclasses
+    import torch
+    import paper_2510_23215_gb300 as scsf
+    from paper_2510_23215_gb300 import proposal_train as pt
+    n, n_train, n_test = 128, args.proposal_train, args.proposal_test
+    t0 = time.perf_counter()
+    train_ops = si.div_a_grad_chain(n, n_train, seed=4 + 1000 * rank)
+    test_ops = si.div_a_grad_chain(n, n_test, seed=5 + 1000 * rank)
+    params = scsf.Params(k=scsf.Proposal.KY, degree=20, tol=1e-8, max_iter=400)
+    prop = scsf.Proposal(seed=11 + rank, device=dev)
+    fields = torch.as_tensor(np.stack([o.P for o in train_ops]), device=dev)
+    Q, tb = pt.label(train_ops, n, params, dev, proposal=prop)
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pt.train(prop, fields, Q, tb, args.proposal_steps, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    tf = torch.as_tensor(np.stack([o.P for o in test_ops[:64]]), device=dev)
+    tQ, ttb = pt.label(test_ops[:64], n, params, dev, proposal=prop)
+    held, _ = prop.gradient(tf.contiguous(), ttb.contiguous(), tQ.contiguous())
+    p_eval = dataclasses.replace(params, k=53)
+    its = pt.head_iterations(prop, test_ops, p_eval, dev)
+    r, q = np.mean(its["random"]), np.mean(its["proposal"])
+    return prop, {
+        "workload": "learned_proposal_128", "n": n, "train": n_train, "test": n_test,
+        "adam_steps": args.proposal_steps, "k_eval": 53, "block_width": p_eval.kb,
+        "heldout_loss": {"subspace_sin2_sum_of_64": held[0], "bounds_sq_err": held[2]},
+        "mean_iters_random_head": float(r), "mean_iters_proposal_head": float(q),
+        "iteration_gain": float(1.0 - q / r),
+        "max_resid": max(its["resid_random"], its["resid_proposal"]),
+        "label_s": round(t_label, 1), "train_s": round(t_train, 1),
+        "note": ("bounded instance of the 5000 / 500 protocol; labels from plain solves; "
+                 "both heads reach residual 1e-8"),
+    }
+
+
 # --------------------------------------------------------------------------- CPU oracle
 def cpu_baseline(ops, sample_ops: int):
     """The CPU oracle as it stands (numpy FP64, Householder-QR ChFSI) on a bounded sample:
@@ -627,6 +674,11 @@ def main():
                     help="k = 400 leg: solved prefix of the 1000 sorted problems")
     ap.add_argument("--k400-chains", type=int, default=4, help="k = 400 leg: concurrent chains")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-chain uneven leg")
+    ap.add_argument("--no-proposal", action="store_true",
+                    help="no learned proposal (not trained, not used at chain heads)")
+    ap.add_argument("--proposal-train", type=int, default=320)
+    ap.add_argument("--proposal-test", type=int, default=32)
+    ap.add_argument("--proposal-steps", type=int, default=800)
     ap.add_argument("--batched-chains", type=int, default=64)
     ap.add_argument("--batched-concurrency", type=int, default=8)
     ap.add_argument("--n-ops", type=int, default=None,

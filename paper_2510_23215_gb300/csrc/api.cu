@@ -33,7 +33,11 @@ struct scsf_ctx {
 
 namespace scsf {
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this thread's launches (graph captures)
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
 }  // namespace scsf
 
 namespace {
@@ -464,8 +468,17 @@ struct scsf_chain {
   // captured FP32-phase filter (a11): m table-driven steps on fixed buffers
   cudaGraphExec_t g32 = nullptr;
   int g32_m = 0, g32_threads = 0;
+  // captured reduced eigensolves, keyed by (width, FP32-phase form): {key, graph, launches}
+  struct EighGraph {
+    int key;
+    cudaGraphExec_t exec;
+    int launches;
+  };
+  std::vector<EighGraph> eigh_graphs;
+  std::vector<int> eigh_seen;
   ~scsf_chain() {
     if (g32) cudaGraphExecDestroy(g32);
+    for (auto& g : eigh_graphs) cudaGraphExecDestroy(g.exec);
   }
 };
 
@@ -528,6 +541,50 @@ cudaError_t run_filter_f32_graph(scsf_chain* ch, const Stencil32& A, int m, doub
   for (int i = 0; i < m; ++i) note_launch();
   *which = (m - 1) % 3;
   return cudaSuccess;
+}
+
+// The reduced eigensolve of width ka (FP32-phase form or FP64 accuracy) on the chain's fixed
+// buffers (H in, theta and Z out). About 30 launches with arguments that only depend on the
+// width, so a chain captures them as a CUDA graph the second time a width occurs and replays
+// the graph afterwards (the first call runs plainly: it also sets function attributes, which
+// must not happen inside a capture). At most kMaxEighGraphs widths are kept per chain.
+constexpr size_t kMaxEighGraphs = 8;
+
+cudaError_t run_small_eigh(scsf_chain* ch, bool f32, int ka, cudaStream_t st) {
+  ChainBufs& b = ch->b;
+  auto direct = [&]() {
+    return f32 ? launch_small_eigh_f32(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st)
+               : launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st);
+  };
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return direct();
+  const int key = 2 * ka + (f32 ? 1 : 0);
+  for (auto& g : ch->eigh_graphs)
+    if (g.key == key) {
+      for (int i = 0; i < g.launches; ++i) note_launch();
+      return cudaGraphLaunch(g.exec, st);
+    }
+  if (std::find(ch->eigh_seen.begin(), ch->eigh_seen.end(), key) == ch->eigh_seen.end()) {
+    ch->eigh_seen.push_back(key);
+    return direct();
+  }
+  cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (err != cudaSuccess) return err;
+  const long long l0 = scsf::t_launches;
+  err = direct();
+  const int nl = (int)(scsf::t_launches - l0);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(st, &graph);
+  if (err == cudaSuccess) err = end;
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess) return err;
+  if (ch->eigh_graphs.size() >= kMaxEighGraphs) {
+    cudaGraphExecDestroy(ch->eigh_graphs.front().exec);
+    ch->eigh_graphs.erase(ch->eigh_graphs.begin());
+  }
+  ch->eigh_graphs.push_back({key, exec, nl});
+  return cudaGraphLaunch(exec, st);
 }
 
 }  // namespace
@@ -924,7 +981,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       // Q^T (A Q) is symmetric (A is): only its upper tiles are formed, then mirrored
       SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, F2, kb, b.H, kb, true));
       SCSF_CUDA(ctx, mark(3));
-      SCSF_CUDA(ctx, launch_small_eigh_f32(kb, b.H, kb, b.theta, b.Z, kb, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, run_small_eigh(ch, true, kb, st));
       SCSF_CUDA(ctx, mark(4));
       SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Z, kb, 0.f, b.V32, kb, false));
       SCSF_CUDA(ctx, mark(5));
@@ -1049,7 +1106,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       SCSF_CUDA(ctx, tn64(ka, ka, Y, kb, F2, kb, b.H, ka, true));
       SCSF_CUDA(ctx, mark(3));
       // reduced eigenproblem and rotation back
-      SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, run_small_eigh(ch, false, ka, st));
       SCSF_CUDA(ctx, mark(4));
       SCSF_CUDA(ctx, nn64(ka, ka, 1.0, Y, kb, b.Z, ka, 0.0, b.V + nl, kb, false));
       SCSF_CUDA(ctx, mark(5));
@@ -1081,7 +1138,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       SCSF_CUDA(ctx, launch_gemm_tn(ka, ka, ka, b.Rinv, ka, b.G, ka, b.H, ka, false, b.gemm_partials,
                                     st));
       SCSF_CUDA(ctx, mark(3));
-      SCSF_CUDA(ctx, launch_small_eigh(ka, b.H, ka, b.theta, b.Z, ka, b.eigh_scratch, st));
+      SCSF_CUDA(ctx, run_small_eigh(ch, false, ka, st));
       SCSF_CUDA(ctx, mark(4));
       // X = Q1 M, M = R2^{-1} Z in b.C
       SCSF_CUDA(ctx, launch_gemm_nn(ka, ka, ka, 1.0, b.Rinv, ka, b.Z, ka, 0.0, b.C, ka, false, st));

@@ -46,9 +46,9 @@ __device__ __forceinline__ double chol_scale(double g) {
 // warp 0 factors the panel's diagonal block (warp-synchronous, one column a step), one
 // thread per row below it solves its panel row against the diagonal block, and all
 // threads apply the panel's rank-32 update to the trailing lower triangle.
-// blockDim = (32, 32).
+// blockDim = (32, 32) for FP32, (32, 16) for FP64.
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
 chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __restrict__ L,
                     int* __restrict__ status, double shift_eps) {
   extern __shared__ unsigned char smraw[];
@@ -62,14 +62,15 @@ chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __rest
   __shared__ double red[32];
   __shared__ int scaled;
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  const int ny = blockDim.y, nthr = 32 * blockDim.y;  // blockDim = (32, ny)
   if (t == 0) scaled = 0;
   __syncthreads();
-  for (int i = t; i < k; i += 1024)
+  for (int i = t; i < k; i += nthr)
     if (chol_out_of_range(G[(size_t)i * ldg + i])) scaled = 1;
   __syncthreads();
   // scales are powers of two: their reciprocals are exact, so S = G isc_i isc_j is exact
   double part = 0.0;
-  for (int i = t; i < k; i += 1024) {
+  for (int i = t; i < k; i += nthr) {
     const double g = G[(size_t)i * ldg + i];
     const double d = scaled ? chol_scale(g) : 1.0;
     sc[i] = d;
@@ -81,14 +82,14 @@ chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __rest
   __syncthreads();
   if (t == 0) {
     double tr = 0.0;
-    for (int w = 0; w < 32; ++w) tr += red[w];
+    for (int w = 0; w < ny; ++w) tr += red[w];
     trace = tr;
   }
   __syncthreads();
   int attempt = 0;
   for (; attempt < 4; ++attempt) {
     const double shift = (attempt == 0) ? 0.0 : shift_eps * k * trace * pow(100.0, attempt - 1);
-    for (int i = ty; i < k; i += 32)
+    for (int i = ty; i < k; i += ny)
       for (int j = tx; j <= i; j += 32) {
         const double g = G[(size_t)i * ldg + j];
         S[i * ks + j] = (T)((scaled ? g * isc[i] * isc[j] : g) + ((i == j) ? shift : 0.0));
@@ -97,44 +98,64 @@ chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __rest
     __syncthreads();
     for (int p = 0; p < k; p += PW) {
       const int w = min(PW, k - p);
-      if (ty == 0) {  // diagonal block, lane = row within the panel
+      if (ty == 0) {  // diagonal block: lane = row within the panel, its row in registers
         const int lane = tx;
-        for (int j = 0; j < w; ++j) {
-          T piv = S[(p + j) * ks + p + j];
-          if (!(piv > T(0))) {
-            if (lane == 0 && bad == 0) bad = p + j + 1;
-            piv = T(1);
+        T row[PW];
+#pragma unroll
+        for (int c = 0; c < PW; ++c)
+          row[c] = (lane < w && c <= lane) ? S[(p + lane) * ks + p + c] : T(0);
+#pragma unroll
+        for (int j = 0; j < PW; ++j) {
+          if (j < w) {
+            T piv = __shfl_sync(0xffffffffu, row[j], j);
+            if (!(piv > T(0))) {
+              if (lane == 0 && bad == 0) bad = p + j + 1;
+              piv = T(1);
+            }
+            const T l = sqrt(piv), inv = T(1) / l;
+            if (lane == j) {
+              row[j] = l;
+              dinv[j] = inv;
+            }
+            if (lane > j) row[j] *= inv;  // L[r][j]
+            // row[c] -= L[r][j] L[c][j] for j < c <= r
+#pragma unroll
+            for (int c = j + 1; c < PW; ++c) {
+              const T lcj = __shfl_sync(0xffffffffu, row[j], c);
+              if (lane >= c) row[c] = fma(-row[j], lcj, row[c]);
+            }
           }
-          const T l = sqrt(piv), inv = T(1) / l;
-          __syncwarp();
-          if (lane == j) {
-            S[(p + j) * ks + p + j] = l;
-            dinv[j] = inv;
-          }
-          if (lane > j && lane < w) S[(p + lane) * ks + p + j] *= inv;
-          __syncwarp();
-          if (lane > j && lane < w) {
-            const T lrj = S[(p + lane) * ks + p + j];
-            for (int c = j + 1; c <= lane; ++c) S[(p + lane) * ks + p + c] -= lrj * S[(p + c) * ks + p + j];
-          }
-          __syncwarp();
         }
+        if (lane < w)
+#pragma unroll
+          for (int c = 0; c < PW; ++c)
+            if (c <= lane) S[(p + lane) * ks + p + c] = row[c];
       }
       __syncthreads();
-      // rows below the panel: L21 = A21 L11^{-T}, forward substitution along each row
-      for (int r = p + w + t; r < k; r += 1024) {
-        T* row = S + r * ks + p;
-        for (int j = 0; j < w; ++j) {
-          T v = row[j];
-          const T* lj = S + (p + j) * ks + p;
-          for (int c = 0; c < j; ++c) v -= row[c] * lj[c];
-          row[j] = v * dinv[j];
+      // rows below the panel: L21 = A21 L11^{-T}, forward substitution along each row (the
+      // row in registers, the diagonal block read as broadcasts)
+      for (int r = p + w + t; r < k; r += nthr) {
+        T x[PW];
+#pragma unroll
+        for (int c = 0; c < PW; ++c) x[c] = (c < w) ? S[r * ks + p + c] : T(0);
+#pragma unroll
+        for (int j = 0; j < PW; ++j) {
+          if (j < w) {
+            const T* lj = S + (p + j) * ks + p;
+            T v = x[j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) v = fma(-x[c], lj[c], v);
+            x[j] = v * dinv[j];
+          }
         }
+#pragma unroll
+        for (int c = 0; c < PW; ++c)
+          if (c < w) S[r * ks + p + c] = x[c];
       }
       __syncthreads();
       // trailing lower triangle: S[r][c] -= sum_q L[r][p + q] L[c][p + q]
       const int q0 = p + w;
-      for (int r = q0 + ty; r < k; r += 32) {
+      for (int r = q0 + ty; r < k; r += ny) {
         const T* lr = S + r * ks + p;
         for (int c = q0 + tx; c <= r; c += 32) {
           const T* lc = S + c * ks + p;
@@ -148,7 +169,7 @@ chol_blocked_kernel(int k, const double* __restrict__ G, int ldg, double* __rest
     if (bad == 0) break;
     __syncthreads();
   }
-  for (int i = ty; i < k; i += 32)
+  for (int i = ty; i < k; i += ny)
     for (int j = tx; j < k; j += 32)
       L[(size_t)i * k + j] = (j <= i) ? (double)S[i * ks + j] * sc[i] : 0.0;
   if (t == 0) status[0] = (bad != 0) ? 1000 : attempt;
@@ -390,7 +411,8 @@ cudaError_t launch_chol_t(int k, const double* G, int ldg, double* L, int* statu
   const size_t smem = (size_t)k * odd_stride(k) * sizeof(T);
   cudaError_t e = ensure_dynamic_smem((const void*)chol_blocked_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  chol_blocked_kernel<T><<<1, dim3(32, 32), smem, st>>>(k, G, ldg, L, status, eps);
+  // FP64 rows of the diagonal block need 64 registers each: half the threads, twice the registers
+  chol_blocked_kernel<T><<<1, dim3(32, sizeof(T) == 8 ? 16 : 32), smem, st>>>(k, G, ldg, L, status, eps);
   note_launch();
   return cudaGetLastError();
 }

@@ -173,65 +173,71 @@ __device__ __forceinline__ void jacobi_round_blocks(T* A, int ks, T* V, int ldv,
 
 #include "trd.cuh"
 
-// Norm pass of one Ogita-Aishima step (one CTA): lambda_i = s_ii / (1 - r_ii) and the
-// cluster threshold delta, from PQ = Z^T [S Z | Z] (k x 2k; P = left half, Q = right half).
-// state[0] = delta.
-__global__ void __launch_bounds__(1024)
+// Norm pass of one Ogita-Aishima step, over many CTAs: lambda_i = s_ii / (1 - r_ii), and into
+// state (zeroed before) the sums of squares of the off-diagonal of P and of R = I - Q, and
+// max |lambda_i| (as the bits of a non-negative float), from PQ = Z^T [S Z | Z] (k x 2k;
+// P = left half, Q = right half). The apply pass forms the cluster threshold from them.
+__global__ void __launch_bounds__(256)
 oa_norms_kernel(int k, const double* __restrict__ PQ, double* __restrict__ lam,
-                double* __restrict__ state, double cluster_floor) {
-  __shared__ double red[3][32];
-  const int t = threadIdx.x, nt = blockDim.x;
+                float* __restrict__ state) {
+  __shared__ float red[3][8];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int ld = 2 * k;
   // the norms only set the cluster threshold: FP32 sums (one SM's FP64 pipe is narrow)
-  float off2 = 0.f, r2 = 0.f;
-  double nrm = 0.0;
-  for (int e = t; e < k * k; e += nt) {
+  float off2 = 0.f, r2 = 0.f, nrm = 0.f;
+  for (int e = blockIdx.x * blockDim.x + t; e < k * k; e += gridDim.x * blockDim.x) {
     const int i = e / k, j = e - i * k;
     const float r = (float)(((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j]);
     const float sd = (i == j) ? 0.f : (float)PQ[i * ld + j];
     off2 = fmaf(sd, sd, off2);
     r2 = fmaf(r, r, r2);
-  }
-  for (int i = t; i < k; i += nt) {
-    const double li = PQ[i * ld + i] / PQ[i * ld + k + i];  // s_ii / (1 - r_ii)
-    lam[i] = li;
-    nrm = fmax(nrm, fabs(li));
+    if (i == j) {
+      const double li = PQ[i * ld + i] / PQ[i * ld + k + i];
+      lam[i] = li;
+      nrm = fmaxf(nrm, (float)fabs(li));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     off2 += __shfl_xor_sync(0xffffffffu, off2, o);
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-    nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+    nrm = fmaxf(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
   }
-  if ((t & 31) == 0) {
-    red[0][t >> 5] = off2;
-    red[1][t >> 5] = r2;
-    red[2][t >> 5] = nrm;
+  if (lane == 0) {
+    red[0][warp] = off2;
+    red[1][warp] = r2;
+    red[2][warp] = nrm;
   }
   __syncthreads();
   if (t == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < (nt + 31) / 32; ++w) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += red[0][w];
       b += red[1][w];
-      c = fmax(c, red[2][w]);
+      c = fmaxf(c, red[2][w]);
     }
-    // pairs closer than cluster_floor * ||S|| are left to the cluster pass: the
-    // first-order update only converges when the error is below gap/||S||
-    state[0] = fmax(2.0 * (sqrt(a) + c * sqrt(b)), cluster_floor * c);
+    atomicAdd(&state[0], a);
+    atomicAdd(&state[1], b);
+    atomicMax(reinterpret_cast<int*>(&state[2]), __float_as_int(c));
   }
 }
 
-// Element-wise part of the step on many CTAs: Eplus = I + E.
+// Element-wise part of the step on many CTAs: Eplus = I + E. Pairs closer than
+// delta = max(2 (||S - D|| + ||G|| ||R||), cluster_floor ||G||) keep E = R / 2 (left to the
+// cluster pass: the first-order update only converges when the error is below gap / ||S||).
 __global__ void oa_apply_kernel(int k, const double* __restrict__ PQ, const double* __restrict__ lam,
-                                const double* __restrict__ state, double* __restrict__ Eplus) {
+                                const float* __restrict__ state, double cluster_floor,
+                                double* __restrict__ Eplus) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= k * k) return;
+  const double c = (double)state[2];
+  const double dl =
+      fmax(2.0 * (sqrt((double)state[0]) + c * sqrt((double)state[1])), cluster_floor * c);
   const int ld = 2 * k;
   const int i = e / k, j = e - i * k;
   const double r = ((i == j) ? 1.0 : 0.0) - PQ[i * ld + k + j];
   const double li = lam[i], lj = lam[j];
   const double gap = lj - li;
-  const double v = (i != j && fabs(gap) > state[0]) ? (PQ[i * ld + j] + lj * r) / gap : 0.5 * r;
+  const double v = (i != j && fabs(gap) > dl) ? (PQ[i * ld + j] + lj * r) / gap : 0.5 * r;
   Eplus[e] = v + ((i == j) ? 1.0 : 0.0);
 }
 
@@ -299,12 +305,15 @@ cluster_jacobi_kernel(int k, const double* __restrict__ PQ, double* __restrict__
     nruns = 0;
     too_long = 0;
   }
-  // ascending positions of the diagonal (ties by index)
+  // ascending positions of the diagonal (ties by index), from a shared copy of it
+  __shared__ double dg[kMaxBlockWidth];
+  for (int i = t; i < k; i += nt) dg[i] = PQ[i * ld + i];
+  __syncthreads();
   for (int i = t; i < k; i += nt) {
-    const double li = PQ[i * ld + i];
+    const double li = dg[i];
     int r = 0;
     for (int j = 0; j < k; ++j) {
-      const double lj = PQ[j * ld + j];
+      const double lj = dg[j];
       r += (lj < li || (lj == li && j < i)) ? 1 : 0;
     }
     pos[i] = r;
@@ -345,7 +354,7 @@ cluster_jacobi_kernel(int k, const double* __restrict__ PQ, double* __restrict__
     if (t == 0) fallback[0] = 1;
     return;
   }
-  for (int i = t; i < k; i += nt) lam[i] = PQ[i * ld + i];
+  for (int i = t; i < k; i += nt) lam[i] = dg[i];
   __syncthreads();
   if (warp >= kClusterWarps) return;
   for (int c = warp; c < nruns; c += kClusterWarps) {
@@ -610,9 +619,11 @@ cudaError_t eigh_refined(int k, const EighScratch& w, int steps, double** TZout,
         cudaSuccess)
       return e;
     if (step == steps) break;
-    oa_norms_kernel<<<1, 1024, 0, st>>>(k, w.PQ, w.lam, w.state, kClusterFloor);
+    float* nst = reinterpret_cast<float*>(w.state);
+    if ((e = cudaMemsetAsync(nst, 0, 3 * sizeof(float), st)) != cudaSuccess) return e;
+    oa_norms_kernel<<<std::min(64, (k * k + 255) / 256), 256, 0, st>>>(k, w.PQ, w.lam, nst);
     note_launch();
-    oa_apply_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, w.PQ, w.lam, w.state, w.E);
+    oa_apply_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, w.PQ, w.lam, nst, kClusterFloor, w.E);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Z' = Z (I + E) into the next panel's right half
