@@ -42,8 +42,7 @@ BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one earlier ncu capture of each
 # kernel at the named shape (copied, not measured in this run); absent where not captured
 TRAFFIC_SOURCE = "one ncu capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum)"
-TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6,
-                      "gemm_nn_rotation": 15.85e6}
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
@@ -323,21 +322,35 @@ def run_ours(args):
     for name, r in iso.items():
         if name in kernels:
             kernels[name].update(r)
-    # the roofline line reports the kernel that takes the largest share of the GPU's
-    # resources in the step: the FP64 block products (Gram, triangular solve, Rayleigh-Ritz,
-    # rotation) use every SM at the FP64 ALU rate, while the single-CTA eigensolver and
-    # Cholesky kernels (longer in a serialised launch list) occupy one SM each. It is timed
-    # alone on the launching stream at the step's shape (one chain: N = 16384, k_b = 120).
-    from paper_2510_23215_gb300 import filter_bench as fb
-    rot = fb.measure_rotation(f"{n}x{scsf.block_width(k)}", dev)
-    roofline = {"bound": "alu", "kernel": "gemm_nn_kernel (FP64 block rotation X = Q M)",
-                "achieved": rot["tflops"], "peak": rot["peak_tflops"], "unit": "TFLOP/s",
-                "frac": rot["tflops"] / rot["peak_tflops"],
-                "traffic": TRAFFIC_PER_LAUNCH.get("gemm_nn_rotation"), "traffic_source": TRAFFIC_SOURCE,
-                "flops_per_launch": rot["flops_per_launch"], "avg_us_alone": rot["avg_us"],
-                "peak_source": ("FP64 ALU rate from unit counts and clocks: 152 SMs x 2 FMA/clk x "
-                                "2 flop x 2.07 GHz (MEASURED_PEAKS.json has no FP64 figure)"),
-                "note": "2 N k_b^2 flop per launch, N = 16384, k_b = 120"}
+    # the roofline line reports the kernel that takes the largest share of the GPU's resources
+    # in the step: the tensor-core block product (Gram, Rayleigh-Ritz, rotation, triangular
+    # solve, deflation), which runs on every SM; the longest kernels of a serialised launch
+    # list (Cholesky, tridiagonal reduction, cluster filters) occupy one SM or a few clusters.
+    # It is timed alone on the launching stream at the step's shape: the FP64-accurate Gram
+    # X^T X of one chain's block (N = 16384, k_b = 120, 8 base-128 digits: 36 BF16 digit-plane
+    # products of 2 N k_b^2 flop each).
+    kb = scsf.block_width(k)
+
+    def gram_roofline(rows, cols, peak):
+        g = torch.Generator(device="cpu").manual_seed(2)
+        X = torch.randn((rows, cols), generator=g, dtype=torch.float64).to(dev)
+        ms = scsf.block_gram_kernel_time(X, reps=20, ctx=ctx)
+        flops = 36 * 2.0 * rows * cols * cols
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "kernel": "oz_gemm_kernel<8> (FP64-accurate Gram, BF16 digit planes)",
+                "shape": f"N = {rows}, k_b = {cols}", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "avg_us_alone": ms * 1e3,
+                "flops_per_launch": flops,
+                "fp64_equivalent_tflops": 2.0 * rows * cols * cols / (ms * 1e-3) / 1e12}
+
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    roofline = gram_roofline(n * n, kb, bf16_peak)
+    roofline.update({
+        "traffic": TRAFFIC_PER_LAUNCH.get("oz_gemm_gram_16384x120"), "traffic_source": TRAFFIC_SOURCE,
+        "peak_source": f"MEASURED_PEAKS.json bf16_tflops (burst; the kernel is timed alone) ({peak_kind})",
+        "note": ("algorithmic flops = 36 digit-plane products x 2 N k_b^2; the kernel also pays the "
+                 "per-64-row readout of exact integer level sums and pads k_b to its 128 x 32 tiles")})
+    roofline_k400 = gram_roofline(65536, 480, bf16_peak)
     # the filters, resident in cluster shared memory: per step they move no DRAM data (ncu:
     # 8 MB per 100-step launch), so their bound is on-chip; reported per step
     res = kernels.get("cheb_step_f32", {})
@@ -419,6 +432,7 @@ def run_ours(args):
         "other_configs": other_configs,
         "learned_proposal": proposal_leg,
         "roofline": roofline,
+        "roofline_tensor_k400_shape": roofline_k400,
         "roofline_filter": roofline_filter,
         "roofline_filter_dram": roofline_dram,
         "kernels": kernels,

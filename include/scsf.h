@@ -89,13 +89,15 @@ scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, i
  * memory where they sort (a host framework that owns all device memory through
  * its own fixed pool, or a latency-critical loop that must not enter the
  * allocator). The paper has no counterpart: this is a deployment convenience.
- * Same arguments, results and validation as scsf_sort; the scratch lives in a
- * static device array of scsf_sort_noalloc_capacity() bytes (8 MiB) that every
- * GPU loading this library reserves until the process exits. Sizes with
- * scsf_sort_workspace_size(n_ops, p0) above the capacity (n_ops > 8184 at
- * p0 = 8) return SCSF_ERR_NO_MEMORY. The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. The call allocates nothing
+ * Same arguments, results and validation as scsf_sort (invalid arguments return
+ * SCSF_ERR_INVALID_ARG first); the scratch lives in a static device array of
+ * scsf_sort_noalloc_capacity() bytes (8 MiB). scsf_create reserves it on its device
+ * (it looks up the array's device address, cudaGetSymbolAddress, which loads the
+ * module holding it), so create the context before a memory pool takes the rest of
+ * the device; if that failed, the first call on the device does the lookup again
+ * (make it before any stream capture). The array stays until the process exits.
+ * Valid sizes with scsf_sort_workspace_size(n_ops, p0) above the capacity
+ * (n_ops > 8184 at p0 = 8) return SCSF_ERR_NO_MEMORY. The call allocates nothing
  * (no cudaMalloc/cudaFree, no allocating library routine). All calls on a
  * device share the one array and each call rewrites what it reads, so calls
  * that overlap on the GPU (other streams, other threads) race: serialise them. */
@@ -453,6 +455,13 @@ scsf_status scsf_block_rotate_ex(scsf_ctx* ctx, const double* X, int ldx, int ro
                                  const double* M, int ldm, int n, double alpha, double beta,
                                  int method, int slices, double* Y, int ldy, void* scratch,
                                  size_t scratch_bytes);
+/* Profiling: average device time (ms, host out) of the tensor-core kernel of the symmetric Gram
+ * product X^T X with 8 digits (X [rows][m], ldx), the digit planes prepared once and `reps`
+ * launches of the kernel alone bracketed by CUDA events on the context's stream. Same
+ * scratch as scsf_block_product_scratch(rows, m, 8); the Gram matrix itself is not returned. */
+scsf_status scsf_block_gram_kernel_time(scsf_ctx* ctx, const double* X, int ldx, int rows, int m,
+                                        int reps, void* scratch, size_t scratch_bytes,
+                                        float* ms_host);
 size_t scsf_small_eigh_scratch(int k);
 scsf_status scsf_small_eigh(scsf_ctx* ctx, const double* S, int k, double* evals, double* Z,
                             void* scratch, size_t scratch_bytes);

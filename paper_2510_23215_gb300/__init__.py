@@ -51,7 +51,7 @@ EXPORTED_SYMBOLS = [
     "scsf_proposal_targets", "scsf_proposal_prolong",
     "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist", "scsf_block_rotate",
     "scsf_block_product_scratch", "scsf_block_gram", "scsf_block_rotate_ex",
-    "scsf_chain_restart", "scsf_far_steps",
+    "scsf_chain_restart", "scsf_far_steps", "scsf_block_gram_kernel_time",
 ]
 
 
@@ -191,6 +191,9 @@ def library() -> ctypes.CDLL:
     L.scsf_block_rotate_ex.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, dbl, dbl, i32, i32, vp,
                                        i32, vp, sz]
     L.scsf_block_rotate_ex.restype = ctypes.c_int
+    L.scsf_block_gram_kernel_time.argtypes = [vp, vp, i32, i32, i32, i32, vp, sz,
+                                              ctypes.POINTER(ctypes.c_float)]
+    L.scsf_block_gram_kernel_time.restype = ctypes.c_int
     L.scsf_chain_restart.argtypes = [vp]
     L.scsf_chain_restart.restype = ctypes.c_int
     L.scsf_far_steps.argtypes = [ctypes.POINTER(dbl), i64, dbl, ctypes.POINTER(i32)]
@@ -557,6 +560,18 @@ def block_gram(A: torch.Tensor, B: Optional[torch.Tensor] = None, symmetric: boo
                                       1 if symmetric else 0, method, slices, C.data_ptr(), n,
                                       ws.data_ptr(), ws.numel()))
     return C
+
+
+def block_gram_kernel_time(X: torch.Tensor, reps: int = 20, ctx: Optional[Context] = None) -> float:
+    """Average device time (ms) of the tensor-core Gram kernel (8 digits) for X^T X alone."""
+    _check(X, "X")
+    c = _ctx(ctx, X.device)
+    rows, m = int(X.shape[0]), int(X.shape[1])
+    ws = _product_scratch(rows, m, 8, X.device)
+    out = ctypes.c_float()
+    c.check(library().scsf_block_gram_kernel_time(c.handle, X.data_ptr(), m, rows, m, reps,
+                                                  ws.data_ptr(), ws.numel(), ctypes.byref(out)))
+    return float(out.value)
 
 
 def block_rotate(X: torch.Tensor, M: torch.Tensor, Y: Optional[torch.Tensor] = None,

@@ -623,6 +623,9 @@ scsf_status scsf_create(scsf_ctx** out, int device, void* cuda_stream) {
     delete ctx;
     return SCSF_ERR_CUDA;
   }
+  // reserve the allocation-free sort's static scratch on this device now, while the caller
+  // is still setting up (a failure here is retried, and reported, by scsf_sort_noalloc)
+  noalloc_prepare(device);
   ctx->pinned_count = kPinnedDoubles;
   *out = ctx;
   return SCSF_OK;
@@ -643,11 +646,12 @@ size_t scsf_sort_workspace_size(int64_t n_ops, int p0) {
   return sort_workspace_bytes(n_ops, p0);
 }
 
-scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
-                           int start, void* workspace, size_t workspace_bytes, int32_t* perm_out,
-                           double* dist_out) {
-  if (!ctx) return SCSF_ERR_INVALID_ARG;
-  if (!fields || !perm_out || !workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+}  // extern "C"
+
+namespace scsf {
+scsf_status validate_sort_args(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                               int start, const int32_t* perm_out) {
+  if (!fields || !perm_out) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
   if (n_ops < 1 || n_ops > 65536) return fail(ctx, SCSF_ERR_INVALID_ARG, "n_ops out of [1, 65536]");
   if (p < 1 || p > 1024 || p0 < 1 || p0 > p)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= p0 <= p <= 1024");
@@ -655,6 +659,19 @@ scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, i
     return fail(ctx, SCSF_ERR_INVALID_ARG, "p * p0 too large for one CTA's shared memory");
   if (p0 > 64) return fail(ctx, SCSF_ERR_INVALID_ARG, "p0 > 64 is not supported");
   if (start < 0 || start >= n_ops) return fail(ctx, SCSF_ERR_INVALID_ARG, "start out of range");
+  return SCSF_OK;
+}
+}  // namespace scsf
+
+extern "C" {
+
+scsf_status scsf_sort_dist(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                           int start, void* workspace, size_t workspace_bytes, int32_t* perm_out,
+                           double* dist_out) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  const scsf_status v = validate_sort_args(ctx, fields, n_ops, p, p0, start, perm_out);
+  if (v != SCSF_OK) return v;
+  if (!workspace) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
   if (workspace_bytes < sort_workspace_bytes(n_ops, p0))
     return fail(ctx, SCSF_ERR_NO_MEMORY, "sort workspace too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1553,6 +1570,25 @@ scsf_status scsf_block_gram(scsf_ctx* ctx, const double* A, int lda, const doubl
   else
     SCSF_CUDA(ctx, launch_gemm_tn(rows, m, n, A, lda, B, ldb, C, ldc, symmetric != 0,
                                   static_cast<double*>(rest), st));
+  return product_finish(ctx, err);
+}
+
+scsf_status scsf_block_gram_kernel_time(scsf_ctx* ctx, const double* X, int ldx, int rows, int m,
+                                        int reps, void* scratch, size_t scratch_bytes,
+                                        float* ms_host) {
+  if (!ctx) return SCSF_ERR_INVALID_ARG;
+  if (!X || !ms_host) return fail(ctx, SCSF_ERR_INVALID_ARG, "null pointer");
+  int* err;
+  void* rest;
+  size_t rest_bytes;
+  scsf_status s = product_setup(ctx, rows, m, m, SCSF_PRODUCT_TENSOR, 8, scratch, scratch_bytes,
+                                &err, &rest, &rest_bytes);
+  if (s != SCSF_OK) return s;
+  if (ldx < m || reps < 1) return fail(ctx, SCSF_ERR_INVALID_ARG, "need ldx >= m and reps >= 1");
+  SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
+  SCSF_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  SCSF_CUDA(ctx, time_gemm_tn_oz(rows, m, X, ldx, 8, rest, rest_bytes, err, reps, ctx->stream,
+                                 ms_host));
   return product_finish(ctx, err);
 }
 

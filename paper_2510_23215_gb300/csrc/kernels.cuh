@@ -20,6 +20,11 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
 
 // Stores `msg` as the context's last error and returns `status`.
 scsf_status set_error(scsf_ctx* ctx, scsf_status status, const std::string& msg);
+// Range and pointer checks of the sort entry points (SCSF_OK or SCSF_ERR_INVALID_ARG).
+scsf_status validate_sort_args(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
+                               int start, const int32_t* perm_out);
+// Looks up (and so reserves) the allocation-free sort's static scratch on `device` (current).
+cudaError_t noalloc_prepare(int device);
 
 // ---- operator assembly (stencil.cu) -------------------------------------
 // Builds d/we/wn for -div(a grad u) (ax, ay) or -Lap u + V u (v), and writes
@@ -172,6 +177,11 @@ size_t oz_scratch_bytes(int rows, int kmax, int slices);
 cudaError_t launch_gemm_tn_oz(int rows, int m, int n, const double* A, int lda, const double* B,
                               int ldb, double* C, int ldc, bool symmetric, int slices,
                               void* scratch, size_t scratch_bytes, int* err, cudaStream_t st);
+// Times the tensor-core kernel of the symmetric Gram product A^T A (8 digits) alone: the digit
+// planes are prepared once, then `reps` launches are bracketed by CUDA events on `st`.
+cudaError_t time_gemm_tn_oz(int rows, int m, const double* A, int lda, int slices, void* scratch,
+                            size_t scratch_bytes, int* err, int reps, cudaStream_t st,
+                            float* ms_out);
 cudaError_t launch_gemm_tn_oz_f32(int rows, int m, int n, const float* A, int lda, const float* B,
                                   int ldb, double* C, int ldc, bool symmetric, void* scratch,
                                   size_t scratch_bytes, int* err, cudaStream_t st);

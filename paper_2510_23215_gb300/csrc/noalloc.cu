@@ -6,8 +6,9 @@
 // a latency-critical loop that must not enter the CUDA allocator. For them
 // this entry point keeps its scratch (the truncated-DFT features and the
 // visited flags) in a file-scope device array instead of a caller workspace.
-// The array is reserved on every GPU that loads the library and stays there
-// until the process exits.
+// The array is reserved on a GPU when the first context is created there (scsf_create looks
+// up its device address, which loads the library's module that holds it), or, if that failed,
+// at the first call of this entry point on that GPU; it stays until the process exits.
 #include <mutex>
 #include <string>
 
@@ -43,6 +44,15 @@ cudaError_t scratch_address(int device, void** out) {
 
 }  // namespace
 
+namespace scsf {
+cudaError_t noalloc_prepare(int device) {
+  void* p = nullptr;
+  const cudaError_t e = scratch_address(device, &p);
+  if (e != cudaSuccess) cudaGetLastError();  // not sticky: the entry point retries
+  return e;
+}
+}  // namespace scsf
+
 extern "C" {
 
 size_t scsf_sort_noalloc_capacity(void) { return kNoallocScratchBytes; }
@@ -50,7 +60,10 @@ size_t scsf_sort_noalloc_capacity(void) { return kNoallocScratchBytes; }
 scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops, int p, int p0,
                               int start, int32_t* perm_out) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
-  if (n_ops >= 1 && p0 >= 1 && scsf::sort_workspace_bytes(n_ops, p0) > kNoallocScratchBytes)
+  // the same range and pointer checks as scsf_sort first, then the static capacity
+  const scsf_status v = scsf::validate_sort_args(ctx, fields, n_ops, p, p0, start, perm_out);
+  if (v != SCSF_OK) return v;
+  if (scsf::sort_workspace_bytes(n_ops, p0) > kNoallocScratchBytes)
     return scsf::set_error(ctx, SCSF_ERR_NO_MEMORY,
                            "n_ops * p0 * p0 * 16 bytes (+ n_ops) exceeds the 8 MiB static scratch "
                            "of scsf_sort_noalloc; use scsf_sort with a caller workspace");
@@ -62,7 +75,7 @@ scsf_status scsf_sort_noalloc(scsf_ctx* ctx, const double* fields, int64_t n_ops
   if (e != cudaSuccess)
     return scsf::set_error(ctx, SCSF_ERR_CUDA,
                            std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  // scsf_sort validates the remaining arguments and enqueues on the context's stream.
+  // enqueued on the context's stream like scsf_sort
   return scsf_sort(ctx, fields, n_ops, p, p0, start, scratch, kNoallocScratchBytes, perm_out);
 }
 

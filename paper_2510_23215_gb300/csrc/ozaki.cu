@@ -896,6 +896,53 @@ cudaError_t launch_gemm_tn_oz(int rows, int m, int n, const double* A, int lda, 
   return cudaErrorInvalidValue;
 }
 
+cudaError_t time_gemm_tn_oz(int rows, int m, const double* A, int lda, int slices, void* scratch,
+                            size_t scratch_bytes, int* err, int reps, cudaStream_t st,
+                            float* ms_out) {
+  if (slices != 8 || m <= 0 || rows <= 0 || reps < 1) return cudaErrorInvalidValue;
+  constexpr int S = 8;
+  const OzPlan p = plan_tn(rows, m, m, true, true, sm_count());
+  Carve cv(scratch, scratch_bytes);
+  OzScratch s;
+  carve_tn(cv, p, m, m, true, S, s);
+  if (!cv.ok) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(s.cmax, 0, sizeof(unsigned long long) * 2 * (size_t)m, st);
+  if (e != cudaSuccess) return e;
+  oz_colmax_kernel<double><<<dim3((m + 31) / 32, std::min(128, std::max(1, (rows + 7) / 8))), 256, 0,
+                             st>>>(rows, m, A, lda, s.cmax);
+  note_launch();
+  oz_split_cols_kernel<double, S><<<dim3(p.Ma / 32, p.Kp / 64), 256, 0, st>>>(rows, m, A, lda, s.cmax,
+                                                                              p.Ma, p.Kp, s.pa, s.ea);
+  note_launch();
+  OzArgs a{};
+  a.sym = 1;
+  a.m = m;
+  a.n = m;
+  a.ea = s.ea;
+  a.eb = s.ea;
+  a.mode = 0;
+  a.part = s.part;
+  a.alpha = 1.0;
+  a.err = err;
+  if ((e = launch_oz_gemm<S>(p, s.pa, s.pa, a, st)) != cudaSuccess) return e;  // warm
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_oz_gemm<S>(p, s.pa, s.pa, a, st);
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) *ms_out = ms / reps;
+  return e;
+}
+
 cudaError_t launch_gemm_tn_oz_f32(int rows, int m, int n, const float* A, int lda, const float* B,
                                   int ldb, double* C, int ldc, bool symmetric, void* scratch,
                                   size_t scratch_bytes, int* err, cudaStream_t st) {

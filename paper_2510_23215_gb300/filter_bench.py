@@ -14,8 +14,10 @@ A filter of degree m launches m stencil steps; the per-step device time is taken
     python -m paper_2510_23215_gb300.filter_bench --kernel dc --shape 128x120 --degree 3 --once
     python -m paper_2510_23215_gb300.filter_bench --kernel rot --shape 128x120
     python -m paper_2510_23215_gb300.filter_bench --kernel plate --shape 100x120 --once
+    python -m paper_2510_23215_gb300.filter_bench --kernel gram --shape 128x120 --once
 
-``--once`` runs one filter of the given degree and exits (a short command for profilers).
+``--once`` runs one filter of the given degree (``gram``: one tensor-core Gram product X^T X,
+8 digits, N = n^2 rows) and exits (a short command for profilers).
 """
 from __future__ import annotations
 
@@ -115,7 +117,7 @@ def measure(kernel: str, shape: str, device, degree: int = 20) -> dict:
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--kernel", choices=["f32", "dc", "rot", "plate"], default="f32")
+    ap.add_argument("--kernel", choices=["f32", "dc", "rot", "plate", "gram"], default="f32")
     ap.add_argument("--shape", default="128x120")
     ap.add_argument("--degree", type=int, default=20)
     ap.add_argument("--once", action="store_true")
@@ -123,6 +125,21 @@ def main():
     dev = torch.device("cuda", 0)
     if a.kernel == "rot":
         print(json.dumps(measure_rotation(a.shape, dev)))
+        return
+    if a.kernel == "gram":
+        from . import block_gram, block_gram_kernel_time
+        n, kb = (int(v) for v in a.shape.split("x"))
+        g = torch.Generator(device="cpu").manual_seed(2)
+        X = torch.randn((n * n, kb), generator=g, dtype=torch.float64).to(dev)
+        if a.once:
+            block_gram(X, symmetric=True)
+            torch.cuda.synchronize(dev)
+            print("ok")
+            return
+        ms = block_gram_kernel_time(X, reps=20)
+        flops = 36 * 2.0 * n * n * kb * kb
+        print(json.dumps({"kernel": "gram", "shape": a.shape, "avg_us": ms * 1e3,
+                          "bf16_tflops": flops / (ms * 1e-3) / 1e12}))
         return
     if a.once:
         run, _ = setup(a.kernel, a.shape, dev)

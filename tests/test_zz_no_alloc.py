@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import scsf_inputs as si
+from oracle import sort as osort
 from tests.gpu_util import host, need_gpu
 
 torch = pytest.importorskip("torch")
@@ -45,6 +46,41 @@ def test_noalloc_sort_matches_workspace_sort_on_two_calls_in_a_row():
         st, perm = _noalloc(ctx, fields, p0, start)
         assert st == scsf.OK, scsf.library().scsf_last_error(ctx.handle)
         assert host(perm).tolist() == ref.tolist()
+        # and directly against the CPU oracle's greedy chain (Alg. 2)
+        oracle_perm, _ = osort.scsf_sort(fields_np, p0, start)
+        assert host(perm).tolist() == list(oracle_perm)
+    ctx.close()
+
+
+def test_noalloc_sort_allocates_nothing():
+    """A warmed-up call changes neither torch's reserved pool nor the device's free memory."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ctx = scsf.Context(0)
+    fields = torch.as_tensor(np.stack([o.P for o in si.div_a_grad_chain(64, 50, seed=3)]), device=dev)
+    perm = torch.empty(50, dtype=torch.int32, device=dev)
+    L = scsf.library()
+    args = (ctx.handle, ctypes.c_void_p(fields.data_ptr()), 50, 64, 8, 0, ctypes.c_void_p(perm.data_ptr()))
+    assert L.scsf_sort_noalloc(*args) == scsf.OK  # warm: kernels loaded
+    torch.cuda.synchronize()
+    reserved, (free0, _) = torch.cuda.memory_reserved(dev), torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        assert L.scsf_sort_noalloc(*args) == scsf.OK
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_reserved(dev) == reserved
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    ctx.close()
+
+
+def test_noalloc_sort_checks_arguments_before_capacity():
+    """Calls scsf_sort would reject get SCSF_ERR_INVALID_ARG here too, not the capacity error."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ctx = scsf.Context(0)
+    for n_ops, p, p0 in ((70000, 8, 8), (16, 8, 12), (16, 100, 70)):
+        fields = torch.zeros((n_ops, p, p), dtype=torch.float64, device=dev)
+        st, _ = _noalloc(ctx, fields, p0, 0)
+        assert st == scsf.ERR_INVALID_ARG, (n_ops, p, p0, st)
     ctx.close()
 
 
