@@ -24,6 +24,7 @@ import tempfile
 import threading
 import time
 
+BOUNDS = {"gershgorin": 0, "lanczos": 1}  # scsf_bound values
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -42,7 +43,8 @@ BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one earlier ncu capture of each
 # kernel at the named shape (copied, not measured in this run); absent where not captured
 TRAFFIC_SOURCE = "one ncu capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum)"
-TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6}
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6,
+                      "oz_gemm_gram_16384x120": 33.66e6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
@@ -188,7 +190,8 @@ def run_ours(args):
         if precision == scsf.MIXED:  # the chosen form: tuned degrees, proposal at chain heads
             params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32,
                                  tol=w["tol"], seed=7 + rank, precision=precision,
-                                 switch_tol=args.switch_tol, proposal=prop)
+                                 switch_tol=args.switch_tol, proposal=prop,
+                                 column_degree=bool(args.column_degree), bound=BOUNDS[args.bound])
         else:                        # the plain form: its own degree (default: the workload's)
             params = scsf.Params(k=k, degree=degree or w["degree"], tol=w["tol"], seed=7 + rank,
                                  precision=precision)
@@ -414,6 +417,8 @@ def run_ours(args):
                    "degrees": ({"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}
                                if chosen == "mixed" else {"fp64": w["degree"]}),
                    "switch_tol": args.switch_tol if chosen == "mixed" else None,
+                   "column_degree": bool(args.column_degree) if chosen == "mixed" else None,
+                   "bound": args.bound,
                    "field_law": "a = exp(0.5 f/8), f = sum of 8x8 cosine modes, N(0,1) coefficients",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": f"replicas over chains x{ws}"},
@@ -479,7 +484,8 @@ def leg_lapv256_k400(args, rank, dev, ctx, st, hbm_peak):
     fields = torch.as_tensor(np.stack([o.P for o in ops]), device=dev)
     vs = torch.as_tensor(np.stack([o.V for o in ops]), device=dev)
     params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32, tol=1e-8,
-                         seed=5 + rank, precision=scsf.MIXED)
+                         seed=5 + rank, precision=scsf.MIXED,
+                         column_degree=bool(args.column_degree), bound=BOUNDS[args.bound])
 
     def step(count, n_chains):
         perm = scsf.sort(fields, p0=8, ctx=ctx).cpu().tolist()[:count]
@@ -541,7 +547,9 @@ def leg_batched_uneven(args, rank, dev, ctx, st):
             dops = [scsf.Operator(scsf.DIV_A_GRAD, sp.n, ax=ax[i], ay=ay[i]) for i in perm]
             chains.append((dops, scsf.Params(k=sp.k, nex=_nex_mult4(sp.k), degree=args.degree_fp64,
                                              degree_fp32=args.degree_fp32, tol=1e-8, seed=sp.seed,
-                                             precision=scsf.MIXED)))
+                                             precision=scsf.MIXED,
+                                             column_degree=bool(args.column_degree),
+                                             bound=BOUNDS[args.bound])))
         res = scsf.solve_batched(chains, concurrency=args.batched_concurrency, ctx=ctx)
         return res
 
@@ -676,6 +684,10 @@ def main():
                     help="skip the paper's form (degree 20, one sequential chain)")
     ap.add_argument("--degree-fp32", type=int, default=60, help="mixed form: FP32-phase degree")
     ap.add_argument("--degree-fp64", type=int, default=100, help="mixed form: FP64-phase degree")
+    ap.add_argument("--column-degree", type=int, choices=[0, 1], default=1,
+                    help="mixed form: per-column-group degrees in the FP64 phase")
+    ap.add_argument("--bound", choices=sorted(BOUNDS), default="gershgorin",
+                    help="upper end of the filter interval: Gershgorin or Lanczos estimate")
     ap.add_argument("--switch-tol", type=float, default=0.0,
                     help="mixed form: wanted residual at which the FP32 phase hands over (0: off)")
     ap.add_argument("--chunks", type=int, default=8,

@@ -202,7 +202,22 @@ typedef struct {
                         n a multiple of 32, k_b >= 64 and op->field set at heads           */
   const float* proposal; /* use_proposal: the network's FP32 parameters (device,
                         scsf_proposal_param_count() floats), read at every head           */
+  int bound;         /* scsf_bound: the upper end beta of the filter's damped interval      */
+  int column_degree; /* SCSF_MIXED, FP64 phase: 1 gives each group of 4 active columns its
+                        own degree m_g <= degree from its previous residual r_j and Ritz
+                        value theta_j, m_j = ceil(ln(8 r_j / tol) / ln rho_j) + 2 with
+                        rho_j = |t_j| + sqrt(t_j^2 - 1), t_j = (theta_j - c) / e, clamped to
+                        [8, degree], m_g the largest m_j of the group (the per-vector degree
+                        of Winkelmann et al., ChASE, 2019); 0: every column takes degree    */
 } scsf_params;
+
+/* beta, the upper end of the damped interval [alpha, beta] (Sec. 2.2), must lie above the
+ * spectrum. SCSF_BOUND_GERSHGORIN: the Gershgorin bound of the assembled operator (rigorous).
+ * SCSF_BOUND_LANCZOS: 16 FP32 Lanczos steps from a seeded start per problem; beta = the largest
+ * Ritz value of the Lanczos tridiagonal plus the norm of the last Lanczos residual, widened by
+ * 0.2 % and never above the Gershgorin bound (the estimate of Sec. 3.2; Zhou and Li 2011).
+ * A tighter beta widens the filter's amplification of the wanted end. */
+typedef enum { SCSF_BOUND_GERSHGORIN = 0, SCSF_BOUND_LANCZOS = 1 } scsf_bound;
 
 typedef struct {
   int iters;             /* outer iterations (Alg. 3 repeat loop)            */
@@ -238,6 +253,8 @@ typedef struct {
    * least 3 * max_iter doubles, iteration i writes {max, median residual of the
    * wanted unlocked pairs, pairs locked so far} to history[3 i .. 3 i + 2]. */
   double* history;
+  double beta;           /* upper end of the damped interval used (scsf_params.bound)   */
+  double beta_gershgorin;/* the Gershgorin bound of the operator                         */
 } scsf_stats;
 
 /* Enables (1) or disables (0) per-phase CUDA-event timing in scsf_stats. */
@@ -427,6 +444,17 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
                                 const double* theta, int ncols, int degree, double lambda,
                                 double c, double e, double* Y, int ldy, void* scratch,
                                 size_t scratch_bytes);
+/* scsf_cheb_filter_dc with a degree per group of 4 columns: columns [4 g, 4 g + 4) are
+ * filtered to degree group_degrees[g] (host array of ceil(ncols / 4) ints, each in
+ * [1, degree]), Y_j = X_j y_{m_g}(theta_j) + Z_{m_g, j}, exactly the degree-m_g filter of
+ * those columns. Needs the cluster-resident filter (the operator's bands and the degree's
+ * step table in one cluster's shared memory): SCSF_ERR_INVALID_ARG otherwise. Same scratch as
+ * scsf_cheb_filter_dc. */
+scsf_status scsf_cheb_filter_dc_grouped(scsf_ctx* ctx, const scsf_operator* op, const double* X,
+                                        int ldx, const double* theta, int ncols, int degree,
+                                        const int* group_degrees, double lambda, double c,
+                                        double e, double* Y, int ldy, void* scratch,
+                                        size_t scratch_bytes);
 /* Rotation of a block by a small matrix, Y = X M (Alg. 3, rotation X = Q Z; also the
  * triangular solve X R^{-1} of Cholesky QR): X FP64 [rows][k] (ldx), M FP64 [k][n] (ldm),
  * Y FP64 [rows][n] (ldy), all device, Y must not overlap X or M; 1 <= k, n <= 512. */

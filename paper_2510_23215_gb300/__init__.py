@@ -25,7 +25,8 @@ __all__ = [
     "ScsfError", "Operator", "Params", "Context", "Chain", "library", "lib_path",
     "sort", "solve", "cheb_filter", "assemble_bounds", "small_eigh", "block_width",
     "FP64", "MIXED", "DIV_A_GRAD", "LAP_PLUS_V", "EXPORTED_SYMBOLS", "launch_count",
-    "PRODUCT_TENSOR", "PRODUCT_FP64", "block_gram", "block_rotate",
+    "PRODUCT_TENSOR", "PRODUCT_FP64", "block_gram", "block_rotate", "BOUND_GERSHGORIN",
+    "BOUND_LANCZOS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -35,6 +36,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ER
 DIV_A_GRAD, LAP_PLUS_V, CSR, PLATE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 PRODUCT_TENSOR, PRODUCT_FP64 = 0, 1
+BOUND_GERSHGORIN, BOUND_LANCZOS = 0, 1
 
 EXPORTED_SYMBOLS = [
     "scsf_create", "scsf_destroy", "scsf_last_error", "scsf_version",
@@ -52,6 +54,7 @@ EXPORTED_SYMBOLS = [
     "scsf_cheb_filter_dc_scratch", "scsf_cheb_filter_dc", "scsf_sort_dist", "scsf_block_rotate",
     "scsf_block_product_scratch", "scsf_block_gram", "scsf_block_rotate_ex",
     "scsf_chain_restart", "scsf_far_steps", "scsf_block_gram_kernel_time",
+    "scsf_cheb_filter_dc_grouped",
 ]
 
 
@@ -74,7 +77,8 @@ class _CParams(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("degree_fp32", ctypes.c_int),
                 ("switch_tol", ctypes.c_double), ("products", ctypes.c_int),
-                ("use_proposal", ctypes.c_int), ("proposal", ctypes.c_void_p)]
+                ("use_proposal", ctypes.c_int), ("proposal", ctypes.c_void_p),
+                ("bound", ctypes.c_int), ("column_degree", ctypes.c_int)]
 
 
 class _CStats(ctypes.Structure):
@@ -90,7 +94,8 @@ class _CStats(ctypes.Structure):
                 ("filter32_elems", ctypes.c_double), ("t_filter32_ms", ctypes.c_double),
                 ("filter_dc_steps", ctypes.c_int), ("filter_dc_elems", ctypes.c_double),
                 ("t_filter_dc_ms", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)),
+                ("beta", ctypes.c_double), ("beta_gershgorin", ctypes.c_double)]
 
 
 class _CBatchChain(ctypes.Structure):
@@ -180,6 +185,10 @@ def library() -> ctypes.CDLL:
     L.scsf_cheb_filter_dc.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, vp, i32, i32, dbl,
                                       dbl, dbl, vp, i32, vp, sz]
     L.scsf_cheb_filter_dc.restype = ctypes.c_int
+    L.scsf_cheb_filter_dc_grouped.argtypes = [vp, ctypes.POINTER(_COperator), vp, i32, vp, i32, i32,
+                                              ctypes.POINTER(ctypes.c_int), dbl, dbl, dbl, vp, i32,
+                                              vp, sz]
+    L.scsf_cheb_filter_dc_grouped.restype = ctypes.c_int
     L.scsf_sort_noalloc_capacity.argtypes = []
     L.scsf_sort_noalloc_capacity.restype = sz
     L.scsf_sort_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp]
@@ -327,13 +336,16 @@ class Params:
     switch_tol: float = 0.0  # MIXED: leave the FP32 phase at this wanted residual (0: off)
     products: int = PRODUCT_TENSOR  # block products on the tensor cores (or PRODUCT_FP64)
     proposal: Optional["Proposal"] = None  # chain heads start from this learned proposal
+    bound: int = BOUND_GERSHGORIN  # upper end of the filter interval (or BOUND_LANCZOS)
+    column_degree: bool = False  # MIXED: per-column-group degrees in the FP64 phase
 
     def _c(self) -> _CParams:
         use = self.proposal is not None
         return _CParams(self.k, self.nex, self.degree, self.tol, self.max_iter, self.precision,
                         self.seed & 0xFFFFFFFFFFFFFFFF, self.degree_fp32, self.switch_tol,
                         self.products, 1 if use else 0,
-                        self.proposal.params.data_ptr() if use else None)
+                        self.proposal.params.data_ptr() if use else None, self.bound,
+                        1 if self.column_degree else 0)
 
     @property
     def kb(self) -> int:
@@ -701,9 +713,12 @@ def cheb_filter_f32(op: Operator, X: torch.Tensor, degree: int, lam: float, c: f
 
 
 def cheb_filter_dc(op: Operator, X: torch.Tensor, theta: torch.Tensor, degree: int, lam: float,
-                   c: float, e: float, ctx: Optional[Context] = None) -> torch.Tensor:
+                   c: float, e: float, ctx: Optional[Context] = None,
+                   group_degrees: Optional[Sequence[int]] = None) -> torch.Tensor:
     """Alg. 1 on an FP64 block through the defect-corrected form (FP32 remainder
-    recurrence driven by the residual block of (X, theta))."""
+    recurrence driven by the residual block of (X, theta)). With group_degrees (one int in
+    [1, degree] per group of 4 columns), columns [4g, 4g+4) are filtered to degree
+    group_degrees[g] (scsf_cheb_filter_dc_grouped)."""
     _check(X, "X")
     _check(theta, "theta")
     cx = _ctx(ctx, X.device)
@@ -717,9 +732,18 @@ def cheb_filter_dc(op: Operator, X: torch.Tensor, theta: torch.Tensor, degree: i
         raise ValueError("unsupported filter shape")
     ws = _workspace(nbytes, X.device)
     cop = op._c()
-    cx.check(L.scsf_cheb_filter_dc(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols, theta.data_ptr(),
-                                   ncols, degree, lam, c, e, Y.data_ptr(), ncols, ws.data_ptr(),
-                                   ws.numel()))
+    if group_degrees is None:
+        cx.check(L.scsf_cheb_filter_dc(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols,
+                                       theta.data_ptr(), ncols, degree, lam, c, e, Y.data_ptr(),
+                                       ncols, ws.data_ptr(), ws.numel()))
+        return Y
+    g = list(int(x) for x in group_degrees)
+    if len(g) != (ncols + 3) // 4:
+        raise ValueError("group_degrees needs one entry per group of 4 columns")
+    garr = (ctypes.c_int * len(g))(*g)
+    cx.check(L.scsf_cheb_filter_dc_grouped(cx.handle, ctypes.byref(cop), X.data_ptr(), ncols,
+                                           theta.data_ptr(), ncols, degree, garr, lam, c, e,
+                                           Y.data_ptr(), ncols, ws.data_ptr(), ws.numel()))
     return Y
 
 

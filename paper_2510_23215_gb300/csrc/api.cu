@@ -45,7 +45,8 @@ namespace {
 // FP32-phase filters of up to this degree replay a captured graph (scalars in a device table)
 constexpr int kMaxGraphSteps = 1024;
 constexpr size_t kPinnedCoefOffset = 4 * kMaxBlockWidth + 64;  // doubles before the float table
-constexpr size_t kPinnedDoubles = kPinnedCoefOffset + (3 * kMaxGraphSteps + 1) / 2;
+constexpr size_t kPinnedGdegOffset = kPinnedCoefOffset + (3 * kMaxGraphSteps + 1) / 2;
+constexpr size_t kPinnedDoubles = kPinnedGdegOffset + kMaxBlockWidth / 8 + 1;  // + group degrees
 
 scsf_status fail(scsf_ctx* ctx, scsf_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -123,7 +124,8 @@ Stencil with_csr(Stencil A, const scsf_operator& op) {
 struct ChainBufs {
   double *V, *B0, *B1, *B2;        // N x kb blocks (row-major, ld = kb)
   double *d, *we, *wn;             // stencil coefficients
-  double *asm_partials, *bounds;   // Gershgorin reduction
+  double *asm_partials, *bounds;   // Gershgorin reduction (+ the Lanczos estimate in bounds[2])
+  float* lanczos;                  // Lanczos vectors (3 N)
   double *G, *Rinv, *H, *Z, *C;    // kb x kb small matrices
   double *theta, *res2;            // kb, 2*kb
   double *gemm_partials, *res_partials;
@@ -136,7 +138,8 @@ struct ChainBufs {
   float *V32, *B32[3], *d32, *we32, *wn32, *partials32;
   float* coef32;  // [kMaxGraphSteps][3] scalars of the captured FP32 filter
   float* ytab;  // [degree][kb] scalar filter values at the Ritz values
-  double* ym;   // [2][kb] recurrence state; y_m in the second row
+  double* ym;   // [3][kb] recurrence state (y_{m-1}, y_m), then y at each column's own degree
+  int* gdeg;    // per group of 4 active columns its degree (column_degree)
   // FP64 stencil chains: the thin-plate operator assembled as CSR (13 slots a row)
   int *prp, *pci;
   double* pval;
@@ -163,7 +166,8 @@ void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, bo
   b.we = c.template take<double>(N);
   b.wn = c.template take<double>(N);
   b.asm_partials = c.template take<double>(2 * (size_t)assemble_blocks_rows((long long)N));
-  b.bounds = c.template take<double>(2);
+  b.bounds = c.template take<double>(4);  // {lo, hi (Gershgorin), Lanczos estimate}
+  b.lanczos = c.template take<float>(lanczos_scratch_bytes((long long)N) / sizeof(float));
   b.G = c.template take<double>(kk);
   b.Rinv = c.template take<double>(kk);
   b.H = c.template take<double>(kk);
@@ -203,11 +207,13 @@ void carve_chain(Cv& c, size_t N, int kb, bool mixed, int degree, bool plate, bo
   b.B32[0] = b.B32[1] = b.B32[2] = nullptr;
   b.ytab = nullptr;
   b.ym = nullptr;
+  b.gdeg = nullptr;
   b.coef32 = nullptr;
   if (mixed) {
     b.coef32 = c.template take<float>(3 * (size_t)kMaxGraphSteps);
     b.ytab = c.template take<float>((size_t)std::max(degree, 1) * kb);
-    b.ym = c.template take<double>(2 * (size_t)kb);
+    b.ym = c.template take<double>(3 * (size_t)kb);
+    b.gdeg = c.template take<int>((size_t)(kb + 3) / 4);
     b.V32 = c.template take<float>(blk);
     for (auto& p : b.B32) p = c.template take<float>(blk);
     b.d32 = c.template take<float>(N);
@@ -311,7 +317,7 @@ template <typename Cv>
 void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3], double** d,
                      double** we, double** wn, float** d32, float** we32, float** wn32,
                      double** part, double** bnd, double** rpart, double** res2, float** ytab,
-                     double** ym, float** coef) {
+                     double** ym, float** coef, int** gdeg) {
   const size_t N = (size_t)n * n;
   *R = cv.template take<float>(N * ncols);
   for (int i = 0; i < 3; ++i) z[i] = cv.template take<float>(N * ncols);
@@ -326,8 +332,9 @@ void carve_filter_dc(Cv& cv, int n, int ncols, int degree, float** R, float* z[3
   *rpart = cv.template take<double>((size_t)resid_blocks(n) * 2 * ncols);
   *res2 = cv.template take<double>(2 * (size_t)ncols);
   *ytab = cv.template take<float>((size_t)std::max(degree, 1) * ncols);
-  *ym = cv.template take<double>(2 * (size_t)ncols);
+  *ym = cv.template take<double>(3 * (size_t)ncols);
   *coef = cv.template take<float>(3 * (size_t)std::max(degree, 1));
+  *gdeg = cv.template take<int>((size_t)(ncols + 3) / 4);
 }
 
 // Defect-corrected filter of the FP64 phase (mixed form): X (FP64, ncols active
@@ -344,11 +351,33 @@ struct DcDeflate {
   float* partials = nullptr;   // gemm_tn_f32 partial sums
 };
 
+// Degree of one column under the per-column rule (Winkelmann et al., ChASE, 2019): the
+// scaled filter of degree d leaves column j's error components from [alpha, beta] at most
+// 1 / |C_d(t_j)| <= 2 rho_j^-d of their size relative to the column, t_j = (theta_j - c) / e,
+// rho_j = |t_j| + sqrt(t_j^2 - 1), so d = ln(8 r_j / tol) / ln rho_j steps bring a residual
+// r_j to tol / 4; two steps of margin, clamped to [8, m]. Columns inside the damped interval
+// (the guard columns near alpha) and columns without a finite residual take m.
+int column_degree(double theta, double r, double c, double e, double tol, int m) {
+  constexpr int kMinDegree = 8;
+  const int lo = std::min(kMinDegree, m);
+  const double t = (theta - c) / e;
+  if (!(t < -1.0) || !std::isfinite(r)) return m;
+  if (!(r > 0.125 * tol)) return lo;
+  const double rho = -t + std::sqrt(t * t - 1.0);
+  if (!(rho > 1.0 + 1e-12)) return m;
+  const double d = std::ceil(std::log(8.0 * r / tol) / std::log(rho)) + 2.0;
+  if (!(d < (double)m)) return m;
+  return std::max(lo, (int)d);
+}
+
 cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const float* R, int ldr,
                           const double* theta, int ncols, int degree, double lam, double c,
                           double e, float* const zb[3], int ldz, float* ytab, double* ystate,
                           double* Y, int ldy, cudaStream_t st, const DcDeflate* defl = nullptr,
-                          float* coef_dev = nullptr, float* coef_host = nullptr) {
+                          float* coef_dev = nullptr, float* coef_host = nullptr,
+                          const int* gdeg = nullptr, bool* grouped = nullptr) {
+  // gdeg (device): per group of 4 columns its degree <= degree, honoured by the resident
+  // filter only (the per-step fallback runs every column to degree); *grouped says which ran.
   // coefficients of step i (Y_i -> Y_{i+1}): s1 A Y_i + s2 Y_i + s3 Y_{i-1}
   std::vector<double> s1(degree), s2(degree), s3(degree);
   const double sigma1 = e / (lam - c);
@@ -373,7 +402,9 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
       P.s2[q] = s2[i0 + q];
       P.s3[q] = s3[i0 + q];
     }
-    if ((err = launch_dc_ytab(theta, ncols, P, ytab, ystate, st)) != cudaSuccess) return err;
+    if ((err = launch_dc_ytab(theta, ncols, P, ytab, ystate, st, gdeg,
+                              gdeg ? ystate + 2 * ncols : nullptr)) != cudaSuccess)
+      return err;
   }
   int cur = 0;
   bool resident = false;
@@ -386,7 +417,8 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
     err = cudaMemcpyAsync(coef_dev, coef_host, 3 * (size_t)degree * sizeof(float),
                           cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess) return err;
-    err = launch_dc_filter_resident(A, R, ldr, ncols, ytab, coef_dev, degree, zb[0], ldz, st);
+    err = launch_dc_filter_resident(A, R, ldr, ncols, ytab, coef_dev, degree, zb[0], ldz, st,
+                                    gdeg);
     if (err == cudaSuccess) resident = true;
     else if (err != cudaErrorNotSupported) return err;
     else cudaGetLastError();
@@ -415,7 +447,10 @@ cudaError_t run_filter_dc(const Stencil32& A, const double* X, int ldx, const fl
                              zb[cur], ldz, false, st);
     if (err != cudaSuccess) return err;
   }
-  return launch_dc_combine(A.n * A.n, ncols, X, ldx, ystate + ncols, zb[cur], ldz, Y, ldy, st);
+  // y at each column's own degree (computed with the table) where the groups stopped early
+  const double* ym = (resident && gdeg) ? ystate + 2 * ncols : ystate + ncols;
+  if (grouped) *grouped = resident && gdeg;
+  return launch_dc_combine(A.n * A.n, ncols, X, ldx, ym, zb[cur], ldz, Y, ldy, st);
 }
 
 // Launch width of the FP32 filter step per (n, k_b): the first chain of a shape times
@@ -732,6 +767,8 @@ scsf_status chain_create(scsf_ctx* ctx, const scsf_params* params, int n, long l
   if (params->products != SCSF_PRODUCT_TENSOR && params->products != SCSF_PRODUCT_FP64)
     return fail(ctx, SCSF_ERR_INVALID_ARG,
                 "products must be SCSF_PRODUCT_TENSOR or SCSF_PRODUCT_FP64");
+  if (params->bound != SCSF_BOUND_GERSHGORIN && params->bound != SCSF_BOUND_LANCZOS)
+    return fail(ctx, SCSF_ERR_INVALID_ARG, "bound must be SCSF_BOUND_GERSHGORIN or _LANCZOS");
   if (params->use_proposal &&
       (!params->proposal || n < 32 || n % 32 != 0 || kb < 64))
     return fail(ctx, SCSF_ERR_INVALID_ARG,
@@ -857,9 +894,15 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   } else
     SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, b.d, b.we, b.wn,
                                    b.asm_partials, b.bounds, st));
-  SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  const bool lanczos = ch->p.bound == SCSF_BOUND_LANCZOS;
+  if (lanczos)  // capped at the Gershgorin bound on the device
+    SCSF_CUDA(ctx, launch_lanczos_bound(A, 16, ch->p.seed ^ 0x5bd1e995ull, b.lanczos, INFINITY,
+                                        b.bounds + 2, st));
+  SCSF_CUDA(ctx, cudaMemcpyAsync(h, b.bounds, (lanczos ? 3 : 2) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));
-  const double lo = h[0], hi = h[1];
+  const double lo = h[0], hi_g = h[1];
+  const double hi = (lanczos && std::isfinite(h[2]) && h[2] < hi_g) ? h[2] : hi_g;
   // the bounds kernels keep a NaN, and an infinite coefficient makes hi infinite
   if (!std::isfinite(lo) || !std::isfinite(hi))
     return fail(ctx, SCSF_ERR_INVALID_ARG,
@@ -929,6 +972,11 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   const double* dc_theta = nullptr;
   int dc_steps = 0;
   double dc_elems = 0.0, t_filter_dc = 0.0;
+  // per-column degrees of the defect-corrected filter: the previous residual and Ritz value
+  // of active column j are r_h[prev_off + j], theta_h[prev_off + j] once have_prev is set
+  const bool coldeg = mixed && ch->p.column_degree != 0;
+  bool have_prev = false;
+  int prev_off = 0;
 
   // the tall block products (rows = N): tensor-core digit-split products or CUDA-core FMAs
   const bool tc = ch->p.products == SCSF_PRODUCT_TENSOR;
@@ -1058,6 +1106,17 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
                                            b.V32, kb));
       have_R = true;
       dc_theta = b.theta;
+      if (coldeg) {  // the FP64 residuals of the FP32 phase's pairs seed the degree rule
+        SCSF_CUDA(ctx, cudaMemcpyAsync(h + kMaxBlockWidth, b.res2, 2 * kb * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+        SCSF_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int j = 0; j < kb; ++j) {
+          const double rr = h[kMaxBlockWidth + j], aa = h[kMaxBlockWidth + kb + j];
+          r_h[j] = (aa > 0.0) ? std::sqrt(rr / aa) : INFINITY;
+        }
+        have_prev = true;
+        prev_off = 0;
+      }
     }
   }
 
@@ -1080,12 +1139,30 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       defl.nl = nl;
       defl.C = b.C;
       defl.partials = b.partials32;
+      const bool per_col = coldeg && have_prev && m <= kMaxGraphSteps;
+      double col_elems = 0.0;
+      if (per_col) {
+        int* hg = reinterpret_cast<int*>(ctx->pinned + kPinnedGdegOffset);
+        for (int g = 0; 4 * g < ka; ++g) {
+          int dg = 1;
+          const int j1 = std::min(4 * g + 4, ka);
+          for (int j = 4 * g; j < j1; ++j)
+            dg = std::max(dg, column_degree(theta_h[prev_off + j], r_h[prev_off + j], c, e,
+                                            ch->p.tol, m));
+          hg[g] = dg;
+          col_elems += (double)dg * N * (j1 - 4 * g);
+        }
+        SCSF_CUDA(ctx, cudaMemcpyAsync(b.gdeg, hg, ((ka + 3) / 4) * sizeof(int),
+                                       cudaMemcpyHostToDevice, st));
+      }
+      bool grouped = false;
       SCSF_CUDA(ctx, run_filter_dc(A32, b.V + nl, kb, b.V32 + nl, kb, dc_theta, ka, m, lam, c, e,
                                    b.B32, kb, b.ytab, b.ym, bufs[0], kb, st, &defl,
                                    (m <= kMaxGraphSteps) ? b.coef32 : nullptr,
-                                   reinterpret_cast<float*>(ctx->pinned + kPinnedCoefOffset)));
+                                   reinterpret_cast<float*>(ctx->pinned + kPinnedCoefOffset),
+                                   per_col ? b.gdeg : nullptr, &grouped));
       dc_steps += m;
-      dc_elems += (double)m * N * ka;
+      dc_elems += grouped ? col_elems : (double)m * N * ka;
     } else {
       SCSF_CUDA(ctx, run_filter(A, b.V + nl, kb, ka, m, lam, c, e, bufs, lds, &which, st));
       filter_steps += m;
@@ -1210,6 +1287,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     nl += nconv;
     have_R = mixed;
     dc_theta = b.theta + nconv;
+    have_prev = coldeg;
+    prev_off = nconv;
     if (nl >= k) {
       converged = true;
       break;
@@ -1280,6 +1359,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     stats->filter_dc_steps = dc_steps;
     stats->filter_dc_elems = dc_elems;
     stats->t_filter_dc_ms = t_filter_dc;
+    stats->beta = beta;
+    stats->beta_gershgorin = hi_g;
   }
   if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
   return SCSF_OK;
@@ -1449,15 +1530,19 @@ size_t scsf_cheb_filter_dc_scratch(int n, int ncols, int degree) {
   SizeCarve sc;
   float *R, *z[3], *d32, *we32, *wn32, *ytab, *coef;
   double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
+  int* gdeg;
   carve_filter_dc(sc, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
-                  &rpart, &res2, &ytab, &ym, &coef);
+                  &rpart, &res2, &ytab, &ym, &coef, &gdeg);
   return sc.used + 256;
 }
 
-scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
-                                const double* theta, int ncols, int degree, double lambda,
-                                double c, double e, double* Y, int ldy, void* scratch,
-                                size_t scratch_bytes) {
+namespace {
+
+// scsf_cheb_filter_dc, and with group_degrees (host) its per-column-group form.
+scsf_status cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                           const double* theta, int ncols, int degree, const int* group_degrees,
+                           double lambda, double c, double e, double* Y, int ldy, void* scratch,
+                           size_t scratch_bytes) {
   if (!ctx) return SCSF_ERR_INVALID_ARG;
   if (!op_ok(op) || !X || !Y || !theta || !scratch)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "bad argument");
@@ -1467,16 +1552,25 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   if (ncols < 1 || ncols > kMaxBlockWidth || ldx < ncols || ldy < ncols || degree < 1 ||
       !(e > 0.0) || lambda == c)
     return fail(ctx, SCSF_ERR_INVALID_ARG, "need 1 <= ncols <= 512, ld >= ncols, valid filter parameters");
+  const int groups = (ncols + 3) / 4;
+  if (group_degrees) {
+    for (int g = 0; g < groups; ++g)
+      if (group_degrees[g] < 1 || group_degrees[g] > degree)
+        return fail(ctx, SCSF_ERR_INVALID_ARG, "group degrees must lie in [1, degree]");
+  }
   const int n = op->n;
   Carve cv(scratch, scratch_bytes);
   float *R, *z[3], *d32, *we32, *wn32, *ytab, *coef;
   double *d, *we, *wn, *part, *bnd, *rpart, *res2, *ym;
+  int* gdeg;
   carve_filter_dc(cv, n, ncols, degree, &R, z, &d, &we, &wn, &d32, &we32, &wn32, &part, &bnd,
-                  &rpart, &res2, &ytab, &ym, &coef);
+                  &rpart, &res2, &ytab, &ym, &coef, &gdeg);
   if (!cv.ok) return fail(ctx, SCSF_ERR_NO_MEMORY, "scratch too small");
   SCSF_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const size_t N = (size_t)n * n;
+  if (group_degrees)
+    SCSF_CUDA(ctx, cudaMemcpyAsync(gdeg, group_degrees, groups * sizeof(int), cudaMemcpyHostToDevice, st));
   SCSF_CUDA(ctx, launch_assemble(op->kind, n, op->ax, op->ay, op->v, d, we, wn, part, bnd, st));
   SCSF_CUDA(ctx, launch_to_f32(d, d32, N, st));
   SCSF_CUDA(ctx, launch_to_f32(we, we32, N, st));
@@ -1485,10 +1579,35 @@ scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const do
   const Stencil32 A32{d32, we32, wn32, n};
   SCSF_CUDA(ctx, launch_residual_norms(A, X, ldx, ncols, theta, rpart, res2, st, R, ncols));
   std::vector<float> hcoef(3 * (size_t)degree);
+  bool grouped = false;
   SCSF_CUDA(ctx, run_filter_dc(A32, X, ldx, R, ncols, theta, ncols, degree, lambda, c, e, z, ncols,
-                               ytab, ym, Y, ldy, st, nullptr, coef, hcoef.data()));
+                               ytab, ym, Y, ldy, st, nullptr,
+                               coef, hcoef.data(), group_degrees ? gdeg : nullptr, &grouped));
   SCSF_CUDA(ctx, cudaStreamSynchronize(st));  // hcoef is the source of an asynchronous copy
+  if (group_degrees && !grouped)
+    return fail(ctx, SCSF_ERR_INVALID_ARG,
+                "per-group degrees need the cluster-resident filter (grid too large for shared memory)");
   return SCSF_OK;
+}
+
+}  // namespace
+
+scsf_status scsf_cheb_filter_dc(scsf_ctx* ctx, const scsf_operator* op, const double* X, int ldx,
+                                const double* theta, int ncols, int degree, double lambda,
+                                double c, double e, double* Y, int ldy, void* scratch,
+                                size_t scratch_bytes) {
+  return cheb_filter_dc(ctx, op, X, ldx, theta, ncols, degree, nullptr, lambda, c, e, Y, ldy,
+                        scratch, scratch_bytes);
+}
+
+scsf_status scsf_cheb_filter_dc_grouped(scsf_ctx* ctx, const scsf_operator* op, const double* X,
+                                        int ldx, const double* theta, int ncols, int degree,
+                                        const int* group_degrees, double lambda, double c,
+                                        double e, double* Y, int ldy, void* scratch,
+                                        size_t scratch_bytes) {
+  if (!group_degrees) return ctx ? fail(ctx, SCSF_ERR_INVALID_ARG, "null group_degrees") : SCSF_ERR_INVALID_ARG;
+  return cheb_filter_dc(ctx, op, X, ldx, theta, ncols, degree, group_degrees, lambda, c, e, Y, ldy,
+                        scratch, scratch_bytes);
 }
 
 scsf_status scsf_block_rotate(scsf_ctx* ctx, const double* X, int ldx, int rows, int k,

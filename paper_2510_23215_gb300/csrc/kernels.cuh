@@ -123,9 +123,11 @@ cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0,
 // The whole defect-corrected remainder recurrence (Z_m, FP32, into out with ld ldo) in one
 // launch, resident in cluster shared memory like the FP32 filter. coef: device [m][3] step
 // scalars; ytab: device [m][ncols]. cudaErrorNotSupported: use the per-step kernels.
+// gdeg (device, optional): per 4-column group its own degree (<= m): the group's Z stops
+// after that many steps (per-column degrees, the column split of Alg. 1).
 cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ldr, int ncols,
                                       const float* ytab, const float* coef, int m, float* out,
-                                      int ldo, cudaStream_t st);
+                                      int ldo, cudaStream_t st, const int* gdeg = nullptr);
 // The step with {s1, s2, s3} read from device memory at coef (for captured graphs; the
 // caller counts the launch). prev is read whenever non-null.
 cudaError_t launch_cheb_step_f32_tab(const Stencil32& A, const float* cur, int ldc,
@@ -146,8 +148,10 @@ struct DcSteps {
   int i0, count;
   double s1[kDcChunk], s2[kDcChunk], s3[kDcChunk];
 };
+// gdeg (optional, per 4-column group its degree d): ysel[c] = y_d(theta_c) in FP64.
 cudaError_t launch_dc_ytab(const double* theta, int ncols, const DcSteps& P, float* ytab,
-                           double* state, cudaStream_t st);
+                           double* state, cudaStream_t st, const int* gdeg = nullptr,
+                           double* ysel = nullptr);
 // out = s1 (A cur) + s2 cur + s3 prev + s1 R diag(ycol); cur == nullptr means Z_0 = 0.
 cudaError_t launch_cheb_step_dc(const Stencil32& A, const float* cur, const float* prev, int ld,
                                 const float* R, int ldr, const float* ycol, float* out,
@@ -193,6 +197,13 @@ cudaError_t launch_gemm_nn_oz(int rows, int k, int n, double alpha, const double
 cudaError_t launch_gemm_nn_oz_f32(int rows, int k, int n, float alpha, const float* A, int lda,
                                   const double* M, int ldm, float beta, float* C, int ldc,
                                   void* scratch, size_t scratch_bytes, int* err, cudaStream_t st);
+
+// ---- spectrum upper bound by Lanczos (bound.cu) ---------------------------
+// K (<= 32) FP32 Lanczos steps in one CTA; out[0] = min(theta_max(T_K) + |beta_K| with a small
+// relative margin, cap). vecs: lanczos_scratch_bytes(N) of device scratch.
+size_t lanczos_scratch_bytes(long long N);
+cudaError_t launch_lanczos_bound(const Stencil& A, int steps, unsigned long long seed, float* vecs,
+                                 double cap, double* out, cudaStream_t st);
 
 // ---- random head block (rng.cu) -----------------------------------------
 cudaError_t launch_philox_normal(double* out, int rows, int cols, int ld, uint64_t seed,

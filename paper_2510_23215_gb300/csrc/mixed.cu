@@ -185,7 +185,10 @@ template <int kClu>
 __global__ void __launch_bounds__(1024)
 dc_filter_cluster_kernel(Stencil32 A, const float* __restrict__ R, int ldr, int ncols,
                          const float* __restrict__ ytab, const float* __restrict__ coef, int m,
-                         float* __restrict__ out, int ldo) {
+                         float* __restrict__ out, int ldo, const int* __restrict__ gdeg) {
+  // per-column-group degree (all CTAs of a cluster share blockIdx.y, so the step count, and
+  // with it the number of cluster barriers, is uniform within the cluster)
+  if (gdeg) m = min(m, max(gdeg[blockIdx.y], 1));
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int n = A.n;
@@ -297,20 +300,25 @@ size_t cluster_filter_smem(int n) {
 // One thread per column: y_i(theta_j) for the steps [i0, i0 + count) of the filter,
 // y_{i+1} = (s1_i theta + s2_i) y_i + s3_i y_{i-1} with the filter's own (host-computed)
 // coefficients. y_i goes to ytab row i (FP32); state [2][ncols] carries (y_{i-1}, y_i)
-// in FP64 from chunk to chunk, and after the last chunk state[1] holds y_m.
+// in FP64 from chunk to chunk, and after the last chunk state[1] holds y_m. With per-group
+// degrees (gdeg), ysel[j] = y_d (FP64) at the degree d of column j's group.
 __global__ void dc_ytab_kernel(const double* __restrict__ theta, int ncols, DcSteps P,
-                               float* __restrict__ ytab, double* __restrict__ state) {
+                               float* __restrict__ ytab, double* __restrict__ state,
+                               const int* __restrict__ gdeg, double* __restrict__ ysel) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncols) return;
   const double t = theta[j];
+  const int d = gdeg ? gdeg[j / 4] : -1;
   double yp = (P.i0 == 0) ? 0.0 : state[j];
   double y = (P.i0 == 0) ? 1.0 : state[ncols + j];
   for (int q = 0; q < P.count; ++q) {
     ytab[(size_t)(P.i0 + q) * ncols + j] = (float)y;
+    if (P.i0 + q == d) ysel[j] = y;
     const double yn = fma(fma(P.s1[q], t, P.s2[q]), y, P.s3[q] * yp);
     yp = y;
     y = yn;
   }
+  if (P.i0 + P.count == d) ysel[j] = y;
   state[j] = yp;
   state[ncols + j] = y;
 }
@@ -707,9 +715,9 @@ cudaError_t launch_gemm_nn_f32(int rows, int k, int n, float alpha, const float*
 }
 
 cudaError_t launch_dc_ytab(const double* theta, int ncols, const DcSteps& P, float* ytab,
-                           double* state, cudaStream_t st) {
-  if (ncols < 1 || P.count < 1 || P.count > kDcChunk) return cudaErrorInvalidValue;
-  dc_ytab_kernel<<<(ncols + 127) / 128, 128, 0, st>>>(theta, ncols, P, ytab, state);
+                           double* state, cudaStream_t st, const int* gdeg, double* ysel) {
+  if (ncols < 1 || P.count < 1 || P.count > kDcChunk || (gdeg && !ysel)) return cudaErrorInvalidValue;
+  dc_ytab_kernel<<<(ncols + 127) / 128, 128, 0, st>>>(theta, ncols, P, ytab, state, gdeg, ysel);
   note_launch();
   return cudaGetLastError();
 }
@@ -790,7 +798,7 @@ cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0,
 
 cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ldr, int ncols,
                                       const float* ytab, const float* coef, int m, float* out,
-                                      int ldo, cudaStream_t st) {
+                                      int ldo, cudaStream_t st, const int* gdeg) {
   if (ncols < 1 || m < 1) return cudaErrorNotSupported;
   const int n = A.n;
   constexpr size_t kMaxSmem = 227 * 1024;
@@ -822,9 +830,11 @@ cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ld
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (clu == 4)
-    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<4>, A, R, ldr, ncols, ytab, coef, m, out, ldo);
+    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<4>, A, R, ldr, ncols, ytab, coef, m, out, ldo,
+                           gdeg);
   else
-    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<8>, A, R, ldr, ncols, ytab, coef, m, out, ldo);
+    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<8>, A, R, ldr, ncols, ytab, coef, m, out, ldo,
+                           gdeg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cudaErrorNotSupported;

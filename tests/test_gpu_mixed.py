@@ -76,6 +76,50 @@ def test_filter_dc_near_eigenvectors_reaches_fp64_accuracy(n, ncols, degree, noi
     assert np.max(np.abs(host(Y) - ref)) <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("n,ncols,degree,noise,tol", [(24, 37, 20, 1e-6, 1e-9),
+                                                       (20, 50, 60, 1e-9, 1e-9),
+                                                       (17, 13, 13, None, 2e-5)])
+def test_filter_dc_grouped_matches_oracle_per_group(n, ncols, degree, noise, tol):
+    """Per-group degrees: columns [4g, 4g+4) come out as the degree-m_g filter of those
+    columns (the oracle's Alg. 1 run per group), ragged last group included; near Ritz pairs
+    at FP64 accuracy, from random blocks (noise None) at the FP32 filter's level."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op, A, lam, c, e = _filter_setup(n, n + 11)
+    rng = np.random.default_rng(12)
+    if noise is None:
+        X = si.gaussian_block(n * n, ncols, seed=13)
+        theta = rng.uniform(lam, 2 * c, ncols)
+    else:
+        w, V = np.linalg.eigh(A.toarray())
+        X = V[:, :ncols] + noise * rng.standard_normal((n * n, ncols))
+        theta = np.einsum("ij,ij->j", X, A @ X) / np.einsum("ij,ij->j", X, X)
+    groups = (ncols + 3) // 4
+    gdeg = rng.integers(1, degree + 1, groups)
+    gdeg[0], gdeg[-1] = 1, degree
+    Y = host(scsf.cheb_filter_dc(to_dev([op], dev)[0], torch.as_tensor(X, device=dev),
+                                 torch.as_tensor(theta, device=dev), degree, lam, c, e,
+                                 group_degrees=gdeg.tolist()))
+    refs = [chebyshev.chebyshev_filter(A, X[:, 4 * g:4 * g + 4], int(gdeg[g]), lam, c, e)
+            for g in range(groups)]
+    # the block's scale, as for the uniform degree (damped groups are far below it)
+    scale = max(np.max(np.abs(r)) for r in refs)
+    for g in range(groups):
+        bound = tol * scale if noise is not None else tol * int(gdeg[g]) * scale
+        assert np.max(np.abs(Y[:, 4 * g:4 * g + 4] - refs[g])) <= bound, g
+
+
+def test_filter_dc_grouped_rejects_bad_degrees():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op, A, lam, c, e = _filter_setup(12, 5)
+    X = torch.as_tensor(si.gaussian_block(144, 8, seed=1), device=dev)
+    th = torch.zeros(8, dtype=torch.float64, device=dev)
+    for bad in ([0, 4], [4, 5], [4]):
+        with pytest.raises((scsf.ScsfError, ValueError)):
+            scsf.cheb_filter_dc(to_dev([op], dev)[0], X, th, 4, lam, c, e, group_degrees=bad)
+
+
 def _check(op, evals, resid, evecs, k, ref_vals, ref_vecs=None):
     A = operators.assemble(op)
     assert np.max(resid) <= RES_TOL
@@ -142,3 +186,28 @@ def test_mixed_rejects_block_width_not_multiple_of_four():
     import paper_2510_23215_gb300 as scsf
     with pytest.raises(scsf.ScsfError):
         scsf.Chain(scsf.Params(k=10, nex=3, precision=scsf.MIXED), 16, device=dev)
+
+
+def test_mixed_column_degree_filters_fewer_elements_same_pairs():
+    """Per-column degrees in the FP64 phase (scsf_params.column_degree): the same eigenpairs
+    to the tolerance as the uniform degree, with fewer defect-corrected filter elements."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    ops = si.div_a_grad_chain(48, 6, seed=21)
+    res = {}
+    for coldeg in (False, True):
+        p = scsf.Params(k=40, degree=40, degree_fp32=24, tol=1e-10, precision=scsf.MIXED,
+                        column_degree=coldeg)
+        ev, rs, vec, stats = scsf.solve(to_dev(ops, dev), p, want_vectors=True)
+        res[coldeg] = (host(ev), host(rs), host(vec), stats)
+    ev, rs, vec, stats = res[True]
+    for j, op in enumerate(ops):
+        A = operators.assemble(op)
+        w, V = dense.smallest_eigenpairs(A, 40)
+        assert np.max(rs[j]) <= 1e-10
+        assert np.max(operators.relative_residuals(A, vec[j], ev[j])) <= 1.05e-10
+        assert compare.orthonormality_error(vec[j]) <= 1e-12
+        assert compare.max_rel_eig_error(w, ev[j]) <= EIG_RTOL
+    e_uni = sum(s["filter_dc_elems"] for s in res[False][3])
+    e_col = sum(s["filter_dc_elems"] for s in res[True][3])
+    assert e_col < e_uni

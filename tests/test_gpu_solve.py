@@ -211,3 +211,38 @@ def test_non_finite_operator_coefficients_are_rejected():
         assert err.value.status == scsf.ERR_INVALID_ARG
     lo, hi = scsf.assemble_bounds(to_dev([div], dev)[0])
     assert np.isnan(lo) or np.isnan(hi)
+
+
+@pytest.mark.parametrize("kind", ["div", "lapv", "plate"])
+def test_lanczos_upper_bound_encloses_spectrum_and_keeps_results(kind):
+    """Sec. 3.2's Lanczos estimate of the spectrum's upper end (16 steps, largest Ritz value
+    plus the last residual norm): it lies above lambda_max (dense definition) and below the
+    Gershgorin bound, and the solve returns the same pairs with no more outer iterations."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    if kind == "div":
+        ops = si.div_a_grad_chain(40, 3, seed=12)
+    elif kind == "lapv":
+        ops = si.lap_plus_v_chain(40, 3, seed=13)
+    else:
+        ops = si.plate_chain(30, 2, seed=14)
+    tol = 1e-7 if kind == "plate" else 1e-8
+    out = {}
+    for bound in (scsf.BOUND_GERSHGORIN, scsf.BOUND_LANCZOS):
+        p = scsf.Params(k=16, degree=20, tol=tol, max_iter=300, seed=3, bound=bound)
+        out[bound] = scsf.solve(to_dev(ops, dev), p)
+    ev_g, rs_g, _, st_g = out[scsf.BOUND_GERSHGORIN]
+    ev_l, rs_l, _, st_l = out[scsf.BOUND_LANCZOS]
+    for j, op in enumerate(ops):
+        A = operators.assemble(op)
+        lmax = float(np.linalg.eigvalsh(A.toarray() if hasattr(A, "toarray") else A)[-1])
+        assert st_l[j]["beta"] >= lmax
+        assert st_l[j]["beta"] <= st_l[j]["beta_gershgorin"]
+        assert st_g[j]["beta"] == st_g[j]["beta_gershgorin"]
+        assert compare.max_rel_eig_error(host(ev_g)[j], host(ev_l)[j]) <= 1e-10
+    assert float(rs_l.max()) <= tol
+    iters_g = sum(s["iters"] for s in st_g)
+    iters_l = sum(s["iters"] for s in st_l)
+    print(f"{kind}: outer iterations Gershgorin {iters_g}, Lanczos {iters_l}; "
+          f"beta / lambda_max {[round(s['beta'] / s['beta_gershgorin'], 3) for s in st_l]}")
+    assert iters_l <= iters_g
