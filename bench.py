@@ -425,6 +425,9 @@ def run_ours(args):
         "eigenpairs_per_step": pairs / args.steps / ws,
         "iters_per_op_mean": float(np.mean([s["iters"] for s in all_stats])),
         "iters_fp32_per_op_mean": float(np.mean([s["iters_fp32"] for s in all_stats])),
+        "chol_shifts_per_op_mean": {"fp32": float(np.mean([s["chol_shifts_fp32"] for s in all_stats])),
+                                    "fp64": float(np.mean([s["chol_shifts"] for s in all_stats]))},
+        "filter_dc_elems_per_op_mean": float(np.mean([s["filter_dc_elems"] for s in all_stats])),
         "phase_ms_per_step": phase_ms,
         "phase_note": ("per-phase CUDA-event time of one extra instrumented step, summed over "
                        "the concurrent chains' streams"),

@@ -255,6 +255,8 @@ typedef struct {
   double* history;
   double beta;           /* upper end of the damped interval used (scsf_params.bound)   */
   double beta_gershgorin;/* the Gershgorin bound of the operator                         */
+  int chol_shifts;       /* shifted Cholesky QR restarts (S + s I) in FP64-phase iterations */
+  int chol_shifts_fp32;  /* the same in the mixed form's FP32 phase                       */
 } scsf_stats;
 
 /* Enables (1) or disables (0) per-phase CUDA-event timing in scsf_stats. */

@@ -95,7 +95,8 @@ class _CStats(ctypes.Structure):
                 ("filter_dc_steps", ctypes.c_int), ("filter_dc_elems", ctypes.c_double),
                 ("t_filter_dc_ms", ctypes.c_double),
                 ("history", ctypes.POINTER(ctypes.c_double)),
-                ("beta", ctypes.c_double), ("beta_gershgorin", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("beta_gershgorin", ctypes.c_double),
+                ("chol_shifts", ctypes.c_int), ("chol_shifts_fp32", ctypes.c_int)]
 
 
 class _CBatchChain(ctypes.Structure):

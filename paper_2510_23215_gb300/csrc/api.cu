@@ -962,6 +962,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
   };
   bool converged = false;
   bool fp32_first = true;  // first Cholesky QR factor in FP32
+  int chol_shifts32 = 0, chol_shifts64 = 0;  // shifted Cholesky restarts per phase
   int it32 = 0, filter32_steps = 0;
   double felems32 = 0.0, t_filter32 = 0.0;
   // defect-corrected filter of the mixed form's FP64 phase: residual block in b.V32
@@ -1063,6 +1064,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
         std::memcpy(st3, h + 3 * kMaxBlockWidth, sizeof(st3));
         if (tc && st3[2] != 0)
           return fail(ctx, SCSF_ERR_TIMEOUT, "a tensor-core block product gave up waiting");
+        chol_shifts32 += (st3[0] % 1000) + (st3[1] % 1000);
       }
       if (timing) {
         float ms = 0.f;
@@ -1266,6 +1268,7 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       return fail(ctx, SCSF_ERR_TIMEOUT, "a tensor-core block product gave up waiting");
     // an FP32 first factor that needed a shift preconditions too weakly for one FP64 pass
     // to reach FP64 orthogonality: take the first factor in FP64 for the rest of this problem
+    chol_shifts64 += (chol_status[0] % 1000) + (chol_status[1] % 1000);
     if (fp32_first && chol_status[0] > 0) fp32_first = false;
     if (chol_status[0] >= 1000 || chol_status[1] >= 1000)
       return fail(ctx, SCSF_ERR_BREAKDOWN, "Cholesky QR broke down even with a shift");
@@ -1361,6 +1364,8 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
     stats->t_filter_dc_ms = t_filter_dc;
     stats->beta = beta;
     stats->beta_gershgorin = hi_g;
+    stats->chol_shifts_fp32 = chol_shifts32;
+    stats->chol_shifts = chol_shifts64;
   }
   if (!converged) return fail(ctx, SCSF_ERR_NOT_CONVERGED, "max_iter reached before convergence");
   return SCSF_OK;

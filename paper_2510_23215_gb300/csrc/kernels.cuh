@@ -76,7 +76,8 @@ cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A
                            cudaStream_t st);
 // Cholesky QR factor (chol.cu): G = L L^T (FP32 or FP64, shifted restarts on
 // breakdown) and Rinv = (L^T)^{-1} (upper, ld k, one warp per column).
-// L: k x k scratch. status[0]: shifted restarts used, 1000 = failed. Up to
+// L: k x k scratch (the FP32 path up to kSmallBlockWidth leaves it untouched).
+// status[0]: shifted restarts used, 1000 = failed. Up to
 // kSmallBlockWidth the factor runs in one CTA's shared memory; wider matrices take a
 // blocked factorisation in wide_scratch (chol_wide_scratch_bytes(k)) and synchronise
 // the stream once per attempt.

@@ -119,7 +119,9 @@ def test_block_rotate_matches_numpy(rows, k, n):
     assert np.max(np.abs(Y - ref)) <= 1e-13 * k * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("rows,k,lo_exp", [(5000, 120, -30), (3001, 200, -30), (700, 7, 0)])
+@pytest.mark.parametrize("rows,k,lo_exp", [(5000, 120, -30), (3001, 200, -30), (700, 7, 0),
+                                           (600, 1, 0), (2000, 127, -10), (2000, 128, -10),
+                                           (3000, 160, -30), (900, 33, -3)])
 def test_cholqr2_orthonormal_and_reproduces_x(rows, k, lo_exp):
     """Cholesky QR2 (Alg. 3, orthonormalisation) on X = Z diag(s) with Z Gaussian and column
     scales s down to 1e-30 (a Gram entry of 1e-60 is below FP32's range, so the FP32 first
@@ -142,3 +144,23 @@ def test_cholqr2_orthonormal_and_reproduces_x(rows, k, lo_exp):
     Qr, Rr = np.linalg.qr(Z)
     Qr = Qr * np.sign(np.diag(Rr))[None, :]
     assert np.max(np.abs(Q - Qr)) <= 1e-11
+
+
+@pytest.mark.parametrize("k", [24, 120, 150])
+def test_cholqr2_shifted_restart_on_dependent_columns(k):
+    """Nine columns within 1e-7 of each other: the FP32 first factor's pivots for eight of them
+    are rounding noise, one of which is not positive, so it restarts on S + s I (shifted
+    Cholesky QR); the FP64 second pass then needs no shift, Q spans X (Q R = X with
+    R = Q^T X upper triangular) and is orthonormal to the level that one FP64 pass reaches on
+    the shifted first factor's condition number."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(k)
+    X = rng.standard_normal((4000, k))
+    X[:, 1:9] = X[:, [0]] + 1e-7 * rng.standard_normal((4000, 8))
+    Q, shifts = scsf.cholqr2(torch.as_tensor(X, device=dev))
+    Q = host(Q)
+    assert shifts[0] >= 1 and shifts[1] == 0
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) <= 1e-4
+    R = Q.T @ X
+    assert np.max(np.abs(Q @ np.triu(R) - X)) <= 1e-8 * np.max(np.abs(X))
