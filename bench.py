@@ -43,7 +43,7 @@ BYTES_PER_ELEM = {"cheb_step_f64": 24.0, "cheb_step_f32": 12.0, "cheb_step_dc": 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one earlier ncu capture of each
 # kernel at the named shape (copied, not measured in this run); absent where not captured
 TRAFFIC_SOURCE = "one ncu capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum)"
-TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "cheb_filter_f32_cluster": 8.08e6,
+TRAFFIC_PER_LAUNCH = {"cheb_step_f32_256x256_kb480": 353.1e6, "strip_filter_f32_128x120": 8.08e6,
                       "oz_gemm_gram_16384x120": 33.66e6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
@@ -360,11 +360,11 @@ def run_ours(args):
     roofline_filter = None
     if res.get("avg_us_alone"):
         fl = 14.0 * res["elems_per_launch"]  # flop per (node, column) per step
-        roofline_filter = {"bound": "alu", "kernel": "cheb_filter_f32_cluster_kernel (per step)",
+        roofline_filter = {"bound": "alu", "kernel": "strip_filter_cluster_kernel<4, FP32> (per step)",
                            "achieved": fl / (res["avg_us_alone"] * 1e-6) / 1e12,
                            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": fl / (res["avg_us_alone"] * 1e-6) / 1e12 / FP32_PEAK_TFLOPS,
-                           "traffic": TRAFFIC_PER_LAUNCH.get("cheb_filter_f32_cluster"),
+                           "traffic": TRAFFIC_PER_LAUNCH.get("strip_filter_f32_128x120"),
                            "note": ("14 flop per (node, column) per step; traffic is per launch of "
                                     "100 steps; limited by shared-memory issue and cluster "
                                     "barriers, not by DRAM")}

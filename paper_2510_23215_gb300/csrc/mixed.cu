@@ -289,6 +289,168 @@ size_t cluster_filter_smem(int n) {
   return 2 * hrm * n * sizeof(float4) + (3 * (hrm - 2) + 1) * (size_t)n * sizeof(float);
 }
 
+// Register-resident strips for both cluster-resident filters. The cluster's bands split the
+// grid rows as above; inside a band every thread owns a vertical strip of kStripV rows of one
+// grid column and keeps, in registers, the current recurrence level of its 4-column float4
+// entries and their stencil coefficients. A step then reads from shared memory only the row
+// above and the row below the strip, the horizontal neighbours and the level before (which
+// the new level overwrites in place): 2 + 3 kStripV float4 loads per kStripV entries, against
+// 6 float4 and 5 coefficient loads per entry when everything lives in shared memory.
+// kDc: the defect-corrected remainder Z (Z_0 = 0, driven by s1 R diag(y_i), R in shared
+// memory); otherwise the filter itself from Y_0 = X. Halos are exchanged through DSMEM after
+// each step as in the kernels above; rows outside the grid stay zero (zero coefficients).
+constexpr int kStripV = 4;
+
+template <int kClu, bool kDc>
+__global__ void __launch_bounds__(1024)
+strip_filter_cluster_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int ncols,
+                            const float* __restrict__ ytab, const float* __restrict__ coef, int m,
+                            float* __restrict__ out, int ldo, const int* __restrict__ gdeg) {
+  if (kDc && gdeg) m = min(m, max(gdeg[blockIdx.y], 1));  // uniform within the cluster
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = A.n;
+  const int r0 = band_begin<kClu>(rank, n), r1 = band_begin<kClu>(rank + 1, n);
+  const int rows = r1 - r0;
+  const int hrm = (n + kClu - 1) / kClu + 2;  // local rows incl. halos (same on every rank)
+  const int c0 = 4 * blockIdx.y;
+  const int t = threadIdx.x, nt = blockDim.x;
+  extern __shared__ float4 sm4[];
+  float4* L0 = sm4;
+  float4* L1 = sm4 + (size_t)hrm * n;
+  float4* Rb = sm4 + 2 * (size_t)hrm * n;           // kDc: own rows x n
+  float4* yt = Rb + (size_t)(hrm - 2) * n;           // kDc: m step values
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = t; e < hrm * n; e += nt) {
+    L0[e] = z4;
+    L1[e] = z4;
+  }
+  __syncthreads();
+  if (!kDc) {  // Y_0: own rows and both halo rows; local row lr <-> global r0 - 1 + lr
+    for (int e = t; e < (rows + 2) * n; e += nt) {
+      const int lr = e / n, j = e - lr * n, gi = r0 - 1 + lr;
+      if (gi >= 0 && gi < n) L0[e] = ld4(X + (size_t)(gi * n + j) * ldx + c0);
+    }
+  } else {
+    for (int e = t; e < rows * n; e += nt) {
+      const float* rr = X + (size_t)(r0 * n + e) * ldx + c0;
+      Rb[e] = make_float4(rr[0], (c0 + 1 < ncols) ? rr[1] : 0.f, (c0 + 2 < ncols) ? rr[2] : 0.f,
+                          (c0 + 3 < ncols) ? rr[3] : 0.f);
+    }
+    for (int i = t; i < m; i += nt) {
+      const float* y = ytab + (size_t)i * ncols + c0;
+      yt[i] = make_float4(y[0], (c0 + 1 < ncols) ? y[1] : 0.f, (c0 + 2 < ncols) ? y[2] : 0.f,
+                          (c0 + 3 < ncols) ? y[3] : 0.f);
+    }
+  }
+  // this thread's strip: column j, own rows q0 .. q0 + kStripV - 1 (those below rows unused)
+  const int j = t % n, q0 = (t / n) * kStripV;
+  const bool active = q0 < rows;
+  float4 cur[kStripV];
+  float cd[kStripV], cs[kStripV], ce[kStripV], cw[kStripV], cn0 = 0.f;
+#pragma unroll
+  for (int v = 0; v < kStripV; ++v) {
+    const int q = q0 + v, gi = r0 + q, I = gi * n + j;
+    const bool own = active && q < rows;
+    cd[v] = own ? A.d[I] : 0.f;
+    cs[v] = (own && gi < n - 1) ? A.we[I] : 0.f;      // coupling to the row below
+    ce[v] = (own && j < n - 1) ? A.wn[I] : 0.f;       // to the right
+    cw[v] = (own && j > 0) ? A.wn[I - 1] : 0.f;       // to the left
+    if (v == 0) cn0 = (own && gi > 0) ? A.we[I - n] : 0.f;  // to the row above the strip
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < kStripV; ++v)
+    cur[v] = (!kDc && active && q0 + v < rows) ? L0[(size_t)(q0 + v + 1) * n + j] : z4;
+  float4* C = L0;
+  float4* P = L1;
+  const int rows_above = (rank > 0) ? r0 - band_begin<kClu>(rank - 1, n) : 0;
+  for (int s = 0; s < m; ++s) {
+    const float s1 = coef[3 * s], s2 = coef[3 * s + 1], s3 = coef[3 * s + 2];
+    if (active) {
+      const float4 ys = kDc ? yt[s] : z4;
+      float4 up = C[(size_t)q0 * n + j];  // the row above the strip (a halo for q0 = 0)
+      float cn = cn0;                     // coupling to it
+#pragma unroll
+      for (int v = 0; v < kStripV; ++v) {
+        const int q = q0 + v;
+        if (q < rows) {
+          const size_t at = (size_t)(q + 1) * n + j;
+          const float4 y = cur[v];
+          const float4 dn = (v + 1 < kStripV && q + 1 < rows) ? cur[(v + 1) % kStripV] : C[at + n];
+          const float4 ea = C[at + 1], we = C[at - 1];  // in bounds; zero weight off the grid
+          float4 acc = make_float4(cs[v] * dn.x, cs[v] * dn.y, cs[v] * dn.z, cs[v] * dn.w);
+          acc = fma4(cn, up, acc);
+          acc = fma4(ce[v], ea, acc);
+          acc = fma4(cw[v], we, acc);
+          const float diag = fmaf(s1, cd[v], s2);
+          const float4 pv = P[at];  // the level before (zero at the first step)
+          float4 r = make_float4(fmaf(-s1, acc.x, fmaf(diag, y.x, s3 * pv.x)),
+                                 fmaf(-s1, acc.y, fmaf(diag, y.y, s3 * pv.y)),
+                                 fmaf(-s1, acc.z, fmaf(diag, y.z, s3 * pv.z)),
+                                 fmaf(-s1, acc.w, fmaf(diag, y.w, s3 * pv.w)));
+          if (kDc) {
+            const float4 rv = Rb[at - n];
+            r = make_float4(fmaf(s1 * rv.x, ys.x, r.x), fmaf(s1 * rv.y, ys.y, r.y),
+                            fmaf(s1 * rv.z, ys.z, r.z), fmaf(s1 * rv.w, ys.w, r.w));
+          }
+          P[at] = r;
+          cur[v] = r;
+          up = y;
+          cn = cs[v];  // the next row's coupling upwards is this row's coupling downwards
+        }
+      }
+    }
+    cluster.sync();  // every band of the new level is final
+    if (rank > 0) {
+      const float4* upr = cluster.map_shared_rank(P, rank - 1);
+      for (int jj = t; jj < n; jj += nt) P[jj] = upr[(size_t)rows_above * n + jj];
+    }
+    if (rank < kClu - 1) {
+      const float4* dnr = cluster.map_shared_rank(P, rank + 1);
+      for (int jj = t; jj < n; jj += nt) P[(size_t)(rows + 1) * n + jj] = dnr[(size_t)n + jj];
+    }
+    __syncthreads();
+    float4* tmp = C;
+    C = P;
+    P = tmp;
+  }
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < kStripV; ++v) {
+      const int q = q0 + v;
+      if (q < rows) {
+        float* o = out + (size_t)((r0 + q) * n + j) * ldo + c0;
+        const bool vec = (ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+        if (!kDc || (vec && c0 + 3 < ncols)) {
+          st4(o, cur[v]);
+        } else {
+          o[0] = cur[v].x;
+          if (c0 + 1 < ncols) o[1] = cur[v].y;
+          if (c0 + 2 < ncols) o[2] = cur[v].z;
+          if (c0 + 3 < ncols) o[3] = cur[v].w;
+        }
+      }
+    }
+  }
+  // no CTA may leave while a neighbour can still read its shared memory
+  cluster.sync();
+}
+
+// Threads of a strip launch (0: the band does not fit one CTA's 1024 threads).
+template <int kClu>
+int strip_threads(int n) {
+  const int hmax = (n + kClu - 1) / kClu;
+  const int th = n * ((hmax + kStripV - 1) / kStripV);
+  return (th <= 1024) ? ((th + 31) / 32) * 32 : 0;
+}
+
+template <int kClu>
+size_t strip_smem(int n, bool dc, int m) {
+  const size_t hrm = (size_t)(n + kClu - 1) / kClu + 2;
+  return (2 * hrm * n + (dc ? (hrm - 2) * n + (size_t)m : 0)) * sizeof(float4);
+}
+
 // ---- defect-corrected filter ------------------------------------------------
 // The filter's three-term recurrence Y_{i+1} = s1 A Y_i + s2 Y_i + s3 Y_{i-1} started
 // from Y_0 = X splits exactly as Y_i = X diag(y_i) + Z_i: y_i(theta_j) is the same
@@ -751,10 +913,64 @@ cudaError_t launch_dc_combine(int rows, int ncols, const double* X, int ldx, con
   return cudaGetLastError();
 }
 
+// The strip kernel at cluster size 4, else 8, where a band fits one CTA's threads and the
+// buffers its shared memory; cudaErrorNotSupported otherwise (or when the device cannot place
+// the cluster shape), for the caller's fallback.
+template <bool kDc>
+cudaError_t launch_strip_filter(const Stencil32& A, const float* X, int ldx, int ncols,
+                                const float* ytab, const float* coef, int m, float* out, int ldo,
+                                const int* gdeg, cudaStream_t st) {
+  const int n = A.n;
+  constexpr size_t kMaxSmem = 227 * 1024;
+  int clu = 0, threads = 0;
+  size_t smem = 0;
+  if (n >= 8 && (threads = strip_threads<4>(n)) > 0 && (smem = strip_smem<4>(n, kDc, m)) <= kMaxSmem) {
+    clu = 4;
+  } else if (n >= 16 && (threads = strip_threads<8>(n)) > 0 &&
+             (smem = strip_smem<8>(n, kDc, m)) <= kMaxSmem) {
+    clu = 8;
+  } else {
+    return cudaErrorNotSupported;
+  }
+  const void* fn = (clu == 4) ? (const void*)strip_filter_cluster_kernel<4, kDc>
+                              : (const void*)strip_filter_cluster_kernel<8, kDc>;
+  cudaError_t e = ensure_dynamic_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clu, (ncols + 3) / 4, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = clu;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (clu == 4)
+    e = cudaLaunchKernelEx(&cfg, strip_filter_cluster_kernel<4, kDc>, A, X, ldx, ncols, ytab, coef, m,
+                           out, ldo, gdeg);
+  else
+    e = cudaLaunchKernelEx(&cfg, strip_filter_cluster_kernel<8, kDc>, A, X, ldx, ncols, ytab, coef, m,
+                           out, ldo, gdeg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0, int ld0, float* out,
                                             int ldo, int ncols, int m, const float* coef,
                                             cudaStream_t st) {
   if (ncols % 4 || ld0 % 4 || ldo % 4 || m < 1) return cudaErrorNotSupported;
+  {
+    const cudaError_t es = launch_strip_filter<false>(A, Y0, ld0, ncols, nullptr, coef, m, out, ldo,
+                                                       nullptr, st);
+    if (es != cudaErrorNotSupported) return es;
+  }
   const int n = A.n;
   constexpr size_t kMaxSmem = 227 * 1024;
   int clu = 0;
@@ -800,6 +1016,10 @@ cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ld
                                       const float* ytab, const float* coef, int m, float* out,
                                       int ldo, cudaStream_t st, const int* gdeg) {
   if (ncols < 1 || m < 1) return cudaErrorNotSupported;
+  {
+    const cudaError_t es = launch_strip_filter<true>(A, R, ldr, ncols, ytab, coef, m, out, ldo, gdeg, st);
+    if (es != cudaErrorNotSupported) return es;
+  }
   const int n = A.n;
   constexpr size_t kMaxSmem = 227 * 1024;
   int clu = 0;
