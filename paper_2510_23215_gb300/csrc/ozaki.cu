@@ -290,9 +290,16 @@ oz_colmax_kernel(int rows, int m, const T* __restrict__ X, int ld,
   const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   unsigned long long best = 0;
-  if (i < m)
-    for (int r = blockIdx.y * 8 + ty; r < rows; r += 8 * gridDim.y)
-      best = max(best, oz_key(X[(size_t)r * ld + i]));
+  if (i < m) {
+    const int step = 8 * gridDim.y;
+    int r = blockIdx.y * 8 + ty;
+    for (; r + 3 * step < rows; r += 4 * step) {  // four independent loads in flight
+      const T x0 = X[(size_t)r * ld + i], x1 = X[(size_t)(r + step) * ld + i];
+      const T x2 = X[(size_t)(r + 2 * step) * ld + i], x3 = X[(size_t)(r + 3 * step) * ld + i];
+      best = max(max(best, max(oz_key(x0), oz_key(x1))), max(oz_key(x2), oz_key(x3)));
+    }
+    for (; r < rows; r += step) best = max(best, oz_key(X[(size_t)r * ld + i]));
+  }
   red[ty][lane] = best;
   __syncthreads();
   if (ty == 0) {
@@ -597,17 +604,20 @@ __global__ void oz_reduce_kernel(int m, int n, int splits, bool sym, const __int
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * n) return;
   const int i = e / n, j = e - (e / n) * n;
-  int si = i, sj = j;
-  if (sym && i > j) {
-    si = j;
-    sj = i;
-  }
+  if (sym && i > j) return;  // written with its mirror by (j, i)
+  const __int128* src = part + (size_t)i * n + j;
+  const size_t stride = (size_t)m * n;
   __int128 T = 0;
-  for (int s = 0; s < splits; ++s) T += part[(size_t)s * m * n + (size_t)si * n + sj];
-  const int Ea = ea[si], Eb = eb[sj];
-  C[(size_t)i * ldc + j] = (Ea == OZ_NONFINITE || Eb == OZ_NONFINITE)
-                               ? __longlong_as_double(0x7FF8000000000000ll)
-                               : oz_to_double(T, Ea + Eb - 7 * (S + 1));
+  int s = 0;
+  for (; s + 4 <= splits; s += 4)  // four independent loads in flight
+    T += (src[s * stride] + src[(s + 1) * stride]) + (src[(s + 2) * stride] + src[(s + 3) * stride]);
+  for (; s < splits; ++s) T += src[s * stride];
+  const int Ea = ea[i], Eb = eb[j];
+  const double v = (Ea == OZ_NONFINITE || Eb == OZ_NONFINITE)
+                       ? __longlong_as_double(0x7FF8000000000000ll)
+                       : oz_to_double(T, Ea + Eb - 7 * (S + 1));
+  C[(size_t)i * ldc + j] = v;
+  if (sym && i < j) C[(size_t)j * ldc + i] = v;
 }
 
 // ---- host side ------------------------------------------------------------------------
