@@ -4,8 +4,9 @@
 // eigenvectors. It seeds chain heads (Sec. 3.2 starts them from random blocks);
 // the Chebyshev filter and the FP64 residual check still decide every result.
 //
-// Network (all kernels here; weights stored in BF16, FP32 master copy for Adam,
-// FP32 accumulation everywhere):
+// Network (all kernels here; weights stored in BF16, FP32 master copy for Adam, every
+// matrix product on the tensor cores with FP32 accumulation, FP32 activations split into two
+// BF16 parts):
 //   pool   : mean of log a over 4x4 node blocks of the s x s field -> S x S, S = 32
 //   lift   : in = (pooled, x, y) -> v0 = in Wl + bl                    (3 -> W)
 //   layer l: a_l = Re(G (R_l (F v_{l-1}))) + v_{l-1} Wp_l + bp_l,
@@ -70,59 +71,120 @@ struct Layout {
 };
 const Layout kLay;
 
-// ---- generic strided-batched GEMM ---------------------------------------
+// ---- strided-batched GEMM ------------------------------------------------
 // C[z] = alpha * op(A[z]) op(B[z]) + beta * C[z]; op(X) = X or X^T (ta/tb).
 // A: element (r, c) of op(A) (rows x K) is A[r*lda + c] (ta = 0) or A[c*lda + r].
+// On the tensor cores: mma.sync m16n8k16, BF16 operands, FP32 accumulation. An FP32 operand
+// x enters as hi + lo with hi = bf16(x), lo = bf16(x - hi) (16 significant bits) and each
+// product takes hi*hi + hi*lo + lo*hi (the dropped lo*lo term is 2^-16 of the kept ones); a
+// BF16 operand (the weights) has lo = 0 and costs no extra product. Tile 64 x 64 x 32 per
+// CTA of four warps, each warp a 32 x 32 block of 2 x 4 MMA tiles.
+constexpr int kTcBM = 64, kTcBN = 64, kTcBK = 32;
+
+__device__ __forceinline__ void bf16_split(float x, float& hi, float& lo) {
+  hi = __bfloat162float(__float2bfloat16_rn(x));
+  lo = x - hi;
+}
+__device__ __forceinline__ uint32_t bf16_pack(float e0, float e1) {  // e0 in the low half
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(e0)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(e1)) << 16);
+}
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 template <typename TA, typename TB>
-__global__ void __launch_bounds__(256)
-bgemm_kernel(int rows, int cols, int K, float alpha, const TA* __restrict__ A, int lda,
-             long long sA, bool ta, const TB* __restrict__ B, int ldb, long long sB, bool tb,
-             float beta, float* __restrict__ C, int ldc, long long sC) {
-  __shared__ float As[32][33];
-  __shared__ float Bs[32][33];
+__global__ void __launch_bounds__(128)
+bgemm_tc_kernel(int rows, int cols, int K, float alpha, const TA* __restrict__ A, int lda,
+                long long sA, bool ta, const TB* __restrict__ B, int ldb, long long sB, bool tb,
+                float beta, float* __restrict__ C, int ldc, long long sC) {
+  constexpr bool kSplitA = sizeof(TA) == 4, kSplitB = sizeof(TB) == 4;
+  __shared__ float As[kTcBM][kTcBK + 4];  // op(A) tile [m][k]
+  __shared__ float Bs[kTcBN][kTcBK + 4];  // op(B) tile, transposed: [n][k]
   const int z = blockIdx.z;
   A += z * sA;
   B += z * sB;
   C += z * sC;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = t; e < 1024; e += 256) {
+  const int r0 = blockIdx.y * kTcBM, c0 = blockIdx.x * kTcBN;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, q = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[mi][ni][c] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kTcBK) {
+    for (int e = t; e < kTcBM * kTcBK; e += 128) {
       const int i = e >> 5, j = e & 31;
-      // As[i][j] = op(A)[r0 + i][k0 + j]
       const int r = r0 + i, kk = k0 + j;
-      float a = 0.f;
-      if (r < rows && kk < K) a = (float)(ta ? A[(size_t)kk * lda + r] : A[(size_t)r * lda + kk]);
-      As[i][j] = a;
-      // Bs[i][j] = op(B)[k0 + i][c0 + j]
-      const int kb = k0 + i, cc = c0 + j;
-      float b = 0.f;
-      if (kb < K && cc < cols) b = (float)(tb ? B[(size_t)cc * ldb + kb] : B[(size_t)kb * ldb + cc]);
-      Bs[i][j] = b;
+      As[i][j] = (r < rows && kk < K)
+                     ? (float)(ta ? A[(size_t)kk * lda + r] : A[(size_t)r * lda + kk]) : 0.f;
+      const int cc = c0 + i;
+      Bs[i][j] = (kk < K && cc < cols)
+                     ? (float)(tb ? B[(size_t)cc * ldb + kk] : B[(size_t)kk * ldb + cc]) : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float a0 = As[2 * ty][kk], a1 = As[2 * ty + 1][kk];
-      const float b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
-      acc[0][0] = fmaf(a0, b0, acc[0][0]);
-      acc[0][1] = fmaf(a0, b1, acc[0][1]);
-      acc[1][0] = fmaf(a1, b0, acc[1][0]);
-      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+#pragma unroll
+    for (int ks = 0; ks < kTcBK; ks += 16) {
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const float* r_lo = &As[wm + 16 * mi + g][ks + 2 * q];
+        const float* r_hi = &As[wm + 16 * mi + g + 8][ks + 2 * q];
+        const float x[8] = {r_lo[0], r_lo[1], r_hi[0], r_hi[1], r_lo[8], r_lo[9], r_hi[8], r_hi[9]};
+        float h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bf16_split(x[u], h[u], l[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ah[mi][u] = bf16_pack(h[2 * u], h[2 * u + 1]);
+          al[mi][u] = kSplitA ? bf16_pack(l[2 * u], l[2 * u + 1]) : 0u;
+        }
+      }
+      uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const float* col = &Bs[wn + 8 * ni + g][ks + 2 * q];
+        const float y[4] = {col[0], col[1], col[8], col[9]};
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bf16_split(y[u], h[u], l[u]);
+        bh[ni][0] = bf16_pack(h[0], h[1]);
+        bh[ni][1] = bf16_pack(h[2], h[3]);
+        bl[ni][0] = kSplitB ? bf16_pack(l[0], l[1]) : 0u;
+        bl[ni][1] = kSplitB ? bf16_pack(l[2], l[3]) : 0u;
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          mma_16816(acc[mi][ni], ah[mi], bh[ni]);
+          if (kSplitA) mma_16816(acc[mi][ni], al[mi], bh[ni]);
+          if (kSplitB) mma_16816(acc[mi][ni], ah[mi], bl[ni]);
+        }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int r = r0 + 2 * ty + u, c = c0 + 2 * tx + v;
-      if (r < rows && c < cols) {
-        float* p = C + (size_t)r * ldc + c;
-        *p = (beta == 0.f) ? alpha * acc[u][v] : fmaf(alpha, acc[u][v], beta * (*p));
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int r = r0 + wm + 16 * mi + g + ((c & 2) ? 8 : 0);
+        const int cc = c0 + wn + 8 * ni + 2 * q + (c & 1);
+        if (r < rows && cc < cols) {
+          float* p = C + (size_t)r * ldc + cc;
+          *p = (beta == 0.f) ? alpha * acc[mi][ni][c] : fmaf(alpha, acc[mi][ni][c], beta * (*p));
+        }
       }
-    }
 }
 
 template <typename TA, typename TB>
@@ -130,9 +192,9 @@ cudaError_t bgemm(int batch, int rows, int cols, int K, float alpha, const TA* A
                   long long sA, bool ta, const TB* B, int ldb, long long sB, bool tb, float beta,
                   float* C, int ldc, long long sC, cudaStream_t st) {
   if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
-  dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
-  bgemm_kernel<TA, TB><<<grid, 256, 0, st>>>(rows, cols, K, alpha, A, lda, sA, ta, B, ldb, sB, tb,
-                                             beta, C, ldc, sC);
+  dim3 grid((cols + kTcBN - 1) / kTcBN, (rows + kTcBM - 1) / kTcBM, batch);
+  bgemm_tc_kernel<TA, TB><<<grid, 128, 0, st>>>(rows, cols, K, alpha, A, lda, sA, ta, B, ldb, sB,
+                                                tb, beta, C, ldc, sC);
   note_launch();
   return cudaGetLastError();
 }
