@@ -352,7 +352,8 @@ def run_ours(args):
         "traffic": TRAFFIC_PER_LAUNCH.get("oz_gemm_gram_16384x120"), "traffic_source": TRAFFIC_SOURCE,
         "peak_source": f"MEASURED_PEAKS.json bf16_tflops (burst; the kernel is timed alone) ({peak_kind})",
         "note": ("algorithmic flops = 36 digit-plane products x 2 N k_b^2; the kernel also pays the "
-                 "per-64-row readout of exact integer level sums and pads k_b to its 128 x 32 tiles")})
+                 "readout of exact integer level sums every 4 chunks of 64 rows and pads k_b to its "
+                 "128 x 32 tiles")})
     roofline_k400 = gram_roofline(65536, 480, bf16_peak)
     # the filters, resident in cluster shared memory: per step they move no DRAM data (ncu:
     # 8 MB per 100-step launch), so their bound is on-chip; reported per step

@@ -11,10 +11,10 @@
 // digits: x = 2^E sum_p d_p 128^-p with d_1 in [0, 128] and d_p in [-64, 63] for p > 1
 // (rounded at the last digit). Digits are small integers, exact in BF16. The product
 // of two digit planes is a BF16 matrix product whose partial sums are integers of at most
-// 2.36e6 over a K-chunk of 64 rows, so tcgen05.mma accumulates them EXACTLY in FP32 tensor
-// memory. Plane pairs (p, q) with p + q <= S + 1 are kept and summed per "level" p + q;
-// the tensor-memory level sums are read out after every 64-row chunk and added as
-// integers, and the output is assembled from the exact integer level sums as a
+// 2.36e6 over a K-chunk of 64 rows, so tcgen05.mma accumulates OZ_GROUP = 4 chunks (below
+// 9.5e6 < 2^24) EXACTLY in FP32 tensor memory. Plane pairs (p, q) with p + q <= S + 1 are
+// kept and summed per "level" p + q; the tensor-memory level sums are read out after every
+// 4 chunks and added as integers, and the output is assembled from the exact integer level sums as a
 // correctly rounded FP64 value (no FP64 arithmetic on the way; GB300's FP64 pipe is
 // 1/60 of its FP32 rate). With S = 7 (28 BF16 products) the result carries ~49 bits of
 // each operand, i.e. an error of a few 1e-15 of |a_i| |b_j| per term; S = 4 (10 products)
@@ -26,7 +26,7 @@
 //            into an 11-stage shared-memory ring, completion on mbarriers;
 //   warp 9   allocates tensor memory and issues tcgen05.mma (M = 128, N = 32, K = 16)
 //            from one thread, level sums double-buffered in tensor memory (2 x S x 32
-//            columns), tcgen05.commit releases ring stages and hands chunks to readout;
+//            columns), tcgen05.commit releases ring stages and hands every 4 chunks to readout;
 //   warps 0-7 read the level sums (tcgen05.ld 32x32b.x16, lane quarter = warp % 4,
 //            column half = warp / 4), add them as integers, and write the tile.
 // Every wait is bounded (clock64 limit); a CTA that gives up sets a shared abort flag that
@@ -53,7 +53,7 @@ constexpr int OZ_STAGE = OZ_A_BYTES + OZ_B_BYTES;   // 20 KiB, multiple of 1024
 constexpr int OZ_RING = 11;
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_SMEM = OZ_RING * OZ_STAGE + 1024;  // + alignment slack
-constexpr uint32_t OZ_MAGIC = 0x4B400000u;          // bits of 1.5 * 2^23
+constexpr int OZ_GROUP = 4;  // 64-row chunks summed in tensor memory between readouts
 constexpr int OZ_MAX_CHUNKS_PER_CTA = 512;          // keeps int32 level sums below 2^31
 constexpr int OZ_NONFINITE = 0x7fff;                // exponent marker: the row/column has NaN/Inf
 constexpr long long OZ_SPIN_CYCLES = 2000000000ll;  // ~1 s at 2 GHz per wait
@@ -478,13 +478,17 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) {
       bool ok = true;
       for (int tl = 0; tl < nloc && ok; ++tl) {
-        const int tb = tl & 1;
-        if (tl >= 2 && !oz_wait(smem_u32(&acce_bar[tb]), ((tl >> 1) - 1) & 1, abort_v)) {
+        // OZ_GROUP chunks accumulate in one tensor-memory buffer before it is read out
+        const int grp = tl / OZ_GROUP, tb = grp & 1;
+        const bool first = tl % OZ_GROUP == 0;
+        const bool last = tl % OZ_GROUP == OZ_GROUP - 1 || tl == nloc - 1;
+        if (first && grp >= 2 &&
+            !oz_wait(smem_u32(&acce_bar[tb]), ((grp >> 1) - 1) & 1, abort_v)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        uint32_t started = 0;
+        uint32_t started = first ? 0u : ~0u;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           if (!ok) break;
@@ -514,7 +518,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         if (!ok) break;
         for (int j = 0; j < S; ++j) umma_commit(smem_u32(&empty_bar[(tl * S + j) % OZ_RING]));
-        umma_commit(smem_u32(&accf_bar[tb]));
+        if (last) umma_commit(smem_u32(&accf_bar[tb]));
       }
       // no MMA may still write tensor memory when it is released
       umma_commit(smem_u32(&drain_bar));
@@ -530,10 +534,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[l][c] = 0u;
     bool ok = true;
-    for (int tl = 0; tl < nloc; ++tl) {
-      const int tb = tl & 1;
+    const int ngrp = (nloc + OZ_GROUP - 1) / OZ_GROUP;
+    for (int gi = 0; gi < ngrp; ++gi) {
+      const int tb = gi & 1;
       int got = 0;
-      if (lane == 0) got = oz_wait(smem_u32(&accf_bar[tb]), (tl >> 1) & 1, abort_v) ? 1 : 0;
+      if (lane == 0) got = oz_wait(smem_u32(&accf_bar[tb]), (gi >> 1) & 1, abort_v) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) {
         ok = false;
@@ -548,7 +553,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                   v);
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-          acc[l][c] += __float_as_uint(__uint_as_float(v[c]) + 12582912.0f);
+          acc[l][c] += (uint32_t)__float2int_rn(__uint_as_float(v[c]));  // an exact integer
       }
       tc_fence_before();
       __syncwarp();
@@ -557,7 +562,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (ok) {
       const int i = mt * OZ_BM + 32 * quarter + lane;
       const int jb = nt * OZ_BN + 16 * half;
-      const uint32_t bias = (uint32_t)nloc * OZ_MAGIC;
       if (i < args.m) {
         const int Ea = args.ea[i];
 #pragma unroll
@@ -567,7 +571,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           __int128 T = 0;
 #pragma unroll
           for (int l = 0; l < S; ++l)
-            T += (__int128)(int)(acc[l][c] - bias) * ((__int128)1 << (7 * (S - 1 - l)));
+            T += (__int128)(int)acc[l][c] * ((__int128)1 << (7 * (S - 1 - l)));
           if (args.mode == 0) {
             args.part[(size_t)blockIdx.y * args.m * args.n + (size_t)i * args.n + j] = T;
           } else {
