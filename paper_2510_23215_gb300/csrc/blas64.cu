@@ -163,6 +163,41 @@ gemm_nn_kernel(int rows, int K, int n, double alpha, const double* __restrict__ 
     }
 }
 
+// Small outputs (the k_b x k_b products of the eigensolve's refinement): 8 x 8 tiles of 64
+// threads, one output each, so a 120 x 120 result spreads over 225 CTAs instead of 64 (the
+// FP64 pipe, 2 FMA per clock per SM, is the bound, and it is per SM).
+__global__ void __launch_bounds__(64)
+gemm_nn_small_kernel(int rows, int K, int n, double alpha, const double* __restrict__ A, int lda,
+                     const double* __restrict__ M, int ldm, double beta, double* C, int ldc,
+                     bool upper) {
+  constexpr int T = 8, BK = 32;
+  __shared__ double As[T][BK + 1];
+  __shared__ double Ms[BK][T + 1];
+  const int r0 = blockIdx.y * T, j0 = blockIdx.x * T;
+  const int t = threadIdx.x, ty = t >> 3, tx = t & 7;
+  double acc = 0.0;
+  const int k_end = upper ? min(K, j0 + T) : K;
+  for (int k0 = 0; k0 < k_end; k0 += BK) {
+    for (int e = t; e < T * BK; e += 64) {
+      const int rr = e / BK, kk = e - rr * BK;
+      const int r = r0 + rr, kc = k0 + kk;
+      As[rr][kk] = (r < rows && kc < K) ? A[(size_t)r * lda + kc] : 0.0;
+      const int k2 = e / T, jj = e - k2 * T;
+      const int kc2 = k0 + k2, j = j0 + jj;
+      Ms[k2][jj] = (kc2 < K && j < n) ? M[(size_t)kc2 * ldm + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) acc = fma(As[ty][kk], Ms[kk][tx], acc);
+    __syncthreads();
+  }
+  const int r = r0 + ty, j = j0 + tx;
+  if (r < rows && j < n) {
+    double* c = C + (size_t)r * ldc + j;
+    *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * (*c));
+  }
+}
+
 __global__ void copy2d_kernel(int rows, int cols, const double* __restrict__ in, int ld_in,
                               double* __restrict__ out, int ld_out) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -214,11 +249,15 @@ cudaError_t launch_gemm_nn(int rows, int k, int n, double alpha, const double* A
     gemm_nn_kernel<32, 32><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
                                                  upper);
   note_launch();
-  } else {
+  } else if ((long long)((rows + 15) / 16) * ((n + 15) / 16) >= 152) {
     dim3 grid((n + 15) / 16, (rows + 15) / 16);
     gemm_nn_kernel<16, 16><<<grid, 256, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc,
                                                  upper);
   note_launch();
+  } else {
+    dim3 grid((n + 7) / 8, (rows + 7) / 8);
+    gemm_nn_small_kernel<<<grid, 64, 0, st>>>(rows, k, n, alpha, A, lda, M, ldm, beta, C, ldc, upper);
+    note_launch();
   }
   return cudaGetLastError();
 }

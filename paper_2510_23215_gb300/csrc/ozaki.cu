@@ -143,6 +143,9 @@ constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(O
                               ((uint32_t)(OZ_BM >> 4) << 24);
 
 // Bounded wait; a timeout or an abort raised by another role returns false.
+// kSleep: back off between tries (the readout and producer warps); the MMA issuer, on the
+// critical path, retries at once (mbarrier.try_wait itself suspends for a while).
+template <bool kSleep = true>
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -153,7 +156,7 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, volatile 
       *abort_flag = 1;
       return false;
     }
-    __nanosleep(20);
+    if (kSleep) __nanosleep(20);
   }
 }
 // Bounded wait that ignores the abort flag (draining own copies / MMAs before exit).
@@ -483,7 +486,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const bool first = tl % OZ_GROUP == 0;
         const bool last = tl % OZ_GROUP == OZ_GROUP - 1 || tl == nloc - 1;
         if (first && grp >= 2 &&
-            !oz_wait(smem_u32(&acce_bar[tb]), ((grp >> 1) - 1) & 1, abort_v)) {
+            !oz_wait<false>(smem_u32(&acce_bar[tb]), ((grp >> 1) - 1) & 1, abort_v)) {
           ok = false;
           break;
         }
@@ -493,7 +496,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int j = 0; j < S; ++j) {
           if (!ok) break;
           const int g = tl * S + j;
-          if (!oz_wait(smem_u32(&full_bar[g % OZ_RING]), (g / OZ_RING) & 1, abort_v)) {
+          if (!oz_wait<false>(smem_u32(&full_bar[g % OZ_RING]), (g / OZ_RING) & 1, abort_v)) {
             ok = false;
             break;
           }
