@@ -8,6 +8,10 @@
 // node row (16-byte aligned, coalesced across the row). Small k x k matrices
 // stay FP64 so the shared Cholesky and eigensolve kernels serve both phases.
 #include <algorithm>
+#include <condition_variable>
+#include <map>
+#include <mutex>
+#include <set>
 
 #include <cooperative_groups.h>
 
@@ -913,31 +917,20 @@ cudaError_t launch_dc_combine(int rows, int ncols, const double* X, int ldx, con
   return cudaGetLastError();
 }
 
-// The strip kernel at cluster size 4, else 8, where a band fits one CTA's threads and the
-// buffers its shared memory; cudaErrorNotSupported otherwise (or when the device cannot place
-// the cluster shape), for the caller's fallback.
-template <bool kDc>
-cudaError_t launch_strip_filter(const Stencil32& A, const float* X, int ldx, int ncols,
-                                const float* ytab, const float* coef, int m, float* out, int ldo,
-                                const int* gdeg, cudaStream_t st) {
-  const int n = A.n;
-  constexpr size_t kMaxSmem = 227 * 1024;
-  int clu = 0, threads = 0;
-  size_t smem = 0;
-  if (n >= 8 && (threads = strip_threads<4>(n)) > 0 && (smem = strip_smem<4>(n, kDc, m)) <= kMaxSmem) {
-    clu = 4;
-  } else if (n >= 16 && (threads = strip_threads<8>(n)) > 0 &&
-             (smem = strip_smem<8>(n, kDc, m)) <= kMaxSmem) {
-    clu = 8;
-  } else {
-    return cudaErrorNotSupported;
-  }
-  const void* fn = (clu == 4) ? (const void*)strip_filter_cluster_kernel<4, kDc>
-                              : (const void*)strip_filter_cluster_kernel<8, kDc>;
+// ---- the resident filters: variants and the shape tuner ------------------------------
+namespace {
+
+// Variant v of a resident filter: v & 1 selects the cluster size (4 or 8 CTAs), v >> 1 the
+// kernel (0: register strips, 1: both levels in shared memory). cudaErrorNotSupported when the
+// band does not fit (threads or shared memory) or the device cannot place the cluster shape.
+constexpr int kResidentVariants = 4;
+
+cudaError_t launch_cluster(const void* fn, int clu, int groups, int threads, size_t smem,
+                           cudaStream_t st, void** args) {
   cudaError_t e = ensure_dynamic_smem(fn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clu, (ncols + 3) / 4, 1);
+  cfg.gridDim = dim3(clu, groups, 1);
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -948,12 +941,7 @@ cudaError_t launch_strip_filter(const Stencil32& A, const float* X, int ldx, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (clu == 4)
-    e = cudaLaunchKernelEx(&cfg, strip_filter_cluster_kernel<4, kDc>, A, X, ldx, ncols, ytab, coef, m,
-                           out, ldo, gdeg);
-  else
-    e = cudaLaunchKernelEx(&cfg, strip_filter_cluster_kernel<8, kDc>, A, X, ldx, ncols, ytab, coef, m,
-                           out, ldo, gdeg);
+  e = cudaLaunchKernelExC(&cfg, fn, args);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cudaErrorNotSupported;
@@ -962,105 +950,145 @@ cudaError_t launch_strip_filter(const Stencil32& A, const float* X, int ldx, int
   return cudaGetLastError();
 }
 
+template <bool kDc>
+cudaError_t launch_resident_variant(int v, const Stencil32& A, const float* X, int ldx, int ncols,
+                                    const float* ytab, const float* coef, int m, float* out,
+                                    int ldo, const int* gdeg, cudaStream_t st) {
+  constexpr size_t kMaxSmem = 227 * 1024;
+  const int n = A.n, clu = (v & 1) ? 8 : 4, groups = (ncols + 3) / 4;
+  if (n < 2 * clu) return cudaErrorNotSupported;
+  Stencil32 a = A;
+  const float* x = X;
+  const float* yt = ytab;
+  const float* cf = coef;
+  float* o = out;
+  const int* gd = gdeg;
+  if ((v >> 1) == 0) {  // register strips
+    const int threads = (clu == 4) ? strip_threads<4>(n) : strip_threads<8>(n);
+    const size_t smem = (clu == 4) ? strip_smem<4>(n, kDc, m) : strip_smem<8>(n, kDc, m);
+    if (threads == 0 || smem > kMaxSmem) return cudaErrorNotSupported;
+    void* args[] = {&a, &x, &ldx, &ncols, &yt, &cf, &m, &o, &ldo, &gd};
+    const void* fn = (clu == 4) ? (const void*)strip_filter_cluster_kernel<4, kDc>
+                                : (const void*)strip_filter_cluster_kernel<8, kDc>;
+    return launch_cluster(fn, clu, groups, threads, smem, st, args);
+  }
+  if (kDc) {
+    const size_t smem = (clu == 4) ? cluster_dc_smem<4>(n, m) : cluster_dc_smem<8>(n, m);
+    if (smem > kMaxSmem) return cudaErrorNotSupported;
+    void* args[] = {&a, &x, &ldx, &ncols, &yt, &cf, &m, &o, &ldo, &gd};
+    const void* fn = (clu == 4) ? (const void*)dc_filter_cluster_kernel<4>
+                                : (const void*)dc_filter_cluster_kernel<8>;
+    return launch_cluster(fn, clu, groups, 1024, smem, st, args);
+  }
+  const size_t smem = (clu == 4) ? cluster_filter_smem<4>(n) : cluster_filter_smem<8>(n);
+  if (smem > kMaxSmem) return cudaErrorNotSupported;
+  void* args[] = {&a, &x, &ldx, &o, &ldo, &m, &cf};
+  const void* fn = (clu == 4) ? (const void*)cheb_filter_f32_cluster_kernel<4>
+                              : (const void*)cheb_filter_f32_cluster_kernel<8>;
+  return launch_cluster(fn, clu, groups, 1024, smem, st, args);
+}
+
+// Shape tuner: the first call for a (filter, n, column groups) shape on a stream that is not
+// being captured times every applicable variant once on the call's own buffers (CUDA events on
+// the caller's stream; every variant computes the same recurrence and writes only `out`),
+// keeps the fastest for the process and finishes with it; later calls run the cached choice
+// (a call that finds the shape being tuned by another thread waits for the choice; under
+// stream capture an untuned shape runs the first variant that applies). The choice is per
+// process, so solves of the same shape in a process use the same kernel.
+struct ResidentShape {
+  bool dc;
+  int n, groups;
+  bool operator<(const ResidentShape& o) const {
+    return dc != o.dc ? dc < o.dc : n != o.n ? n < o.n : groups < o.groups;
+  }
+};
+
+template <bool kDc>
+cudaError_t launch_resident_tuned(const Stencil32& A, const float* X, int ldx, int ncols,
+                                  const float* ytab, const float* coef, int m, float* out,
+                                  int ldo, const int* gdeg, cudaStream_t st) {
+  static std::mutex mu;
+  static std::condition_variable cv;
+  static std::map<ResidentShape, int> best;  // -1: no variant applies
+  static std::set<ResidentShape> busy;
+  const ResidentShape key{kDc, A.n, (ncols + 3) / 4};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+  bool tune = false;
+  {
+    std::unique_lock<std::mutex> g(mu);
+    if (!capturing) cv.wait(g, [&] { return busy.count(key) == 0; });
+    auto it = best.find(key);
+    if (it != best.end()) {
+      const int v = it->second;
+      g.unlock();
+      if (v < 0) return cudaErrorNotSupported;
+      return launch_resident_variant<kDc>(v, A, X, ldx, ncols, ytab, coef, m, out, ldo, gdeg, st);
+    }
+    if (!capturing) {
+      busy.insert(key);
+      tune = true;
+    }
+  }
+  if (!tune) {  // first applicable variant
+    for (int v = 0; v < kResidentVariants; ++v) {
+      const cudaError_t e =
+          launch_resident_variant<kDc>(v, A, X, ldx, ncols, ytab, coef, m, out, ldo, gdeg, st);
+      if (e != cudaErrorNotSupported) return e;
+    }
+    return cudaErrorNotSupported;
+  }
+  int pick = -1;
+  float pick_ms = INFINITY;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaSuccess;
+  if ((err = cudaEventCreate(&e0)) == cudaSuccess && (err = cudaEventCreate(&e1)) == cudaSuccess) {
+    for (int v = 0; v < kResidentVariants && err == cudaSuccess; ++v) {
+      for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {  // best of two
+        if ((err = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        const cudaError_t lv =
+            launch_resident_variant<kDc>(v, A, X, ldx, ncols, ytab, coef, m, out, ldo, gdeg, st);
+        if (lv == cudaErrorNotSupported) break;
+        if ((err = lv) != cudaSuccess) break;
+        float ms = INFINITY;
+        if ((err = cudaEventRecord(e1, st)) != cudaSuccess ||
+            (err = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (err = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+          break;
+        if (ms < pick_ms) {
+          pick_ms = ms;
+          pick = v;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    busy.erase(key);
+    if (err == cudaSuccess) best[key] = pick;
+  }
+  cv.notify_all();
+  if (err != cudaSuccess) return err;
+  if (pick < 0) return cudaErrorNotSupported;
+  return launch_resident_variant<kDc>(pick, A, X, ldx, ncols, ytab, coef, m, out, ldo, gdeg, st);
+}
+
+}  // namespace
+
 cudaError_t launch_cheb_filter_f32_resident(const Stencil32& A, const float* Y0, int ld0, float* out,
                                             int ldo, int ncols, int m, const float* coef,
                                             cudaStream_t st) {
   if (ncols % 4 || ld0 % 4 || ldo % 4 || m < 1) return cudaErrorNotSupported;
-  {
-    const cudaError_t es = launch_strip_filter<false>(A, Y0, ld0, ncols, nullptr, coef, m, out, ldo,
-                                                       nullptr, st);
-    if (es != cudaErrorNotSupported) return es;
-  }
-  const int n = A.n;
-  constexpr size_t kMaxSmem = 227 * 1024;
-  int clu = 0;
-  size_t smem = 0;
-  if (n >= 8 && cluster_filter_smem<4>(n) <= kMaxSmem) {
-    clu = 4;
-    smem = cluster_filter_smem<4>(n);
-  } else if (n >= 16 && cluster_filter_smem<8>(n) <= kMaxSmem) {
-    clu = 8;
-    smem = cluster_filter_smem<8>(n);
-  } else {
-    return cudaErrorNotSupported;
-  }
-  const void* fn = (clu == 4) ? (const void*)cheb_filter_f32_cluster_kernel<4>
-                              : (const void*)cheb_filter_f32_cluster_kernel<8>;
-  cudaError_t e = ensure_dynamic_smem(fn, smem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clu, ncols / 4, 1);
-  cfg.blockDim = dim3(1024, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = clu;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (clu == 4)
-    e = cudaLaunchKernelEx(&cfg, cheb_filter_f32_cluster_kernel<4>, A, Y0, ld0, out, ldo, m, coef);
-  else
-    e = cudaLaunchKernelEx(&cfg, cheb_filter_f32_cluster_kernel<8>, A, Y0, ld0, out, ldo, m, coef);
-  if (e != cudaSuccess) {  // a cluster shape the device cannot place: per-step launches instead
-    cudaGetLastError();
-    return cudaErrorNotSupported;
-  }
-  note_launch();
-  return cudaGetLastError();
+  return launch_resident_tuned<false>(A, Y0, ld0, ncols, nullptr, coef, m, out, ldo, nullptr, st);
 }
 
 cudaError_t launch_dc_filter_resident(const Stencil32& A, const float* R, int ldr, int ncols,
                                       const float* ytab, const float* coef, int m, float* out,
                                       int ldo, cudaStream_t st, const int* gdeg) {
   if (ncols < 1 || m < 1) return cudaErrorNotSupported;
-  {
-    const cudaError_t es = launch_strip_filter<true>(A, R, ldr, ncols, ytab, coef, m, out, ldo, gdeg, st);
-    if (es != cudaErrorNotSupported) return es;
-  }
-  const int n = A.n;
-  constexpr size_t kMaxSmem = 227 * 1024;
-  int clu = 0;
-  size_t smem = 0;
-  if (n >= 8 && cluster_dc_smem<4>(n, m) <= kMaxSmem) {
-    clu = 4;
-    smem = cluster_dc_smem<4>(n, m);
-  } else if (n >= 16 && cluster_dc_smem<8>(n, m) <= kMaxSmem) {
-    clu = 8;
-    smem = cluster_dc_smem<8>(n, m);
-  } else {
-    return cudaErrorNotSupported;
-  }
-  const void* fn = (clu == 4) ? (const void*)dc_filter_cluster_kernel<4>
-                              : (const void*)dc_filter_cluster_kernel<8>;
-  cudaError_t e = ensure_dynamic_smem(fn, smem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clu, (ncols + 3) / 4, 1);
-  cfg.blockDim = dim3(1024, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = clu;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (clu == 4)
-    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<4>, A, R, ldr, ncols, ytab, coef, m, out, ldo,
-                           gdeg);
-  else
-    e = cudaLaunchKernelEx(&cfg, dc_filter_cluster_kernel<8>, A, R, ldr, ncols, ytab, coef, m, out, ldo,
-                           gdeg);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cudaErrorNotSupported;
-  }
-  note_launch();
-  return cudaGetLastError();
+  return launch_resident_tuned<true>(A, R, ldr, ncols, ytab, coef, m, out, ldo, gdeg, st);
 }
 
 }  // namespace scsf
