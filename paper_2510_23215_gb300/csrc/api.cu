@@ -1035,21 +1035,30 @@ scsf_status scsf_chain_step(scsf_chain* ch, const scsf_operator* op, double* eva
       float* Y = b.B32[which];
       float* F1 = b.B32[(which + 1) % 3];
       float* F2 = b.B32[(which + 2) % 3];
-      for (int pass = 0; pass < 2; ++pass) {
-        SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, Y, kb, b.G, kb, true));
-        SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + pass, st,
-                                        b.chol_wide));
-        SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true));
-        std::swap(Y, F1);
-      }
+      // Cholesky QR2 with the second factor folded into the small matrices, as in the FP64
+      // phase: Q1 = Y R1^{-1}; Q1^T Q1 = R2^T R2; H = R2^{-T} (Q1^T A Q1) R2^{-1};
+      // X = Q1 (R2^{-1} Z) -- the same H and X as with Q = Q1 R2^{-1}, one tall product fewer.
+      SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, Y, kb, b.G, kb, true));
+      SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status, st, b.chol_wide));
+      SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Rinv, kb, 0.f, F1, kb, true));
+      std::swap(Y, F1);  // Y = Q1
+      SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, Y, kb, b.G, kb, true));
+      SCSF_CUDA(ctx, launch_chol_rinv(kb, b.G, kb, true, b.C, b.Rinv, b.status + 1, st,
+                                      b.chol_wide));
       SCSF_CUDA(ctx, mark(2));
       SCSF_CUDA(ctx, launch_cheb_step_f32(A32, Y, kb, nullptr, 0, F2, kb, kb, 1.f, 0.f, 0.f, st));
-      // Q^T (A Q) is symmetric (A is): only its upper tiles are formed, then mirrored
+      // Q1^T (A Q1) is symmetric (A is): only its upper tiles are formed, then mirrored
       SCSF_CUDA(ctx, tn32(kb, kb, Y, kb, F2, kb, b.H, kb, true));
+      // H = R2^{-T} (H1 R2^{-1}) with T = H1 R2^{-1} in b.G
+      SCSF_CUDA(ctx, launch_gemm_nn(kb, kb, kb, 1.0, b.H, kb, b.Rinv, kb, 0.0, b.G, kb, true, st));
+      SCSF_CUDA(ctx, launch_gemm_tn(kb, kb, kb, b.Rinv, kb, b.G, kb, b.H, kb, false, b.gemm_partials,
+                                    st));
       SCSF_CUDA(ctx, mark(3));
       SCSF_CUDA(ctx, run_small_eigh(ch, true, kb, st));
       SCSF_CUDA(ctx, mark(4));
-      SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.Z, kb, 0.f, b.V32, kb, false));
+      // X = Q1 M, M = R2^{-1} Z in b.C
+      SCSF_CUDA(ctx, launch_gemm_nn(kb, kb, kb, 1.0, b.Rinv, kb, b.Z, kb, 0.0, b.C, kb, false, st));
+      SCSF_CUDA(ctx, nn32(kb, kb, 1.f, Y, kb, b.C, kb, 0.f, b.V32, kb, false));
       SCSF_CUDA(ctx, mark(5));
       SCSF_CUDA(ctx, launch_residual_norms_f32(A32, b.V32, kb, kb, b.theta, b.res_partials, b.res2, st));
       SCSF_CUDA(ctx, mark(6));
