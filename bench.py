@@ -487,8 +487,8 @@ def leg_lapv256_k400(args, rank, dev, ctx, st, hbm_peak):
     ops = si.lap_plus_v_chain(n, n_ops, seed=2 + 1000 * rank)
     fields = torch.as_tensor(np.stack([o.P for o in ops]), device=dev)
     vs = torch.as_tensor(np.stack([o.V for o in ops]), device=dev)
-    params = scsf.Params(k=k, degree=args.degree_fp64, degree_fp32=args.degree_fp32, tol=1e-8,
-                         seed=5 + rank, precision=scsf.MIXED,
+    params = scsf.Params(k=k, degree=args.k400_degree_fp64, degree_fp32=args.k400_degree_fp32,
+                         tol=1e-8, seed=5 + rank, precision=scsf.MIXED,
                          column_degree=bool(args.column_degree), bound=BOUNDS[args.bound])
 
     def step(count, n_chains):
@@ -519,7 +519,8 @@ def leg_lapv256_k400(args, rank, dev, ctx, st, hbm_peak):
                    "n_ops_sorted": n_ops, "solved_prefix": prefix, "chains": chains,
                    "law": "V = 10 f, f = sum of 12 x 12 cosine modes, N(0,1) coefficients",
                    "form": "mixed (FP32 phase + FP64 finish), block products on tensor cores",
-                   "degrees": {"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}},
+                   "degrees": {"fp32_phase": args.k400_degree_fp32,
+                               "fp64_phase": args.k400_degree_fp64}},
         "iters_per_op_mean": float(np.mean([x["iters"] for x in stats])),
         "roofline_filter_in_run": {
             "bound": "hbm", "kernel": "cheb_step_f32_kernel (per-step FP32 filter, blocks > L2)",
@@ -686,8 +687,11 @@ def main():
                     help="plain FP64 comparison: concurrent chains")
     ap.add_argument("--no-paper-form", action="store_true",
                     help="skip the paper's form (degree 20, one sequential chain)")
-    ap.add_argument("--degree-fp32", type=int, default=60, help="mixed form: FP32-phase degree")
-    ap.add_argument("--degree-fp64", type=int, default=100, help="mixed form: FP64-phase degree")
+    ap.add_argument("--degree-fp32", type=int, default=80, help="mixed form: FP32-phase degree")
+    ap.add_argument("--degree-fp64", type=int, default=130, help="mixed form: FP64-phase degree")
+    ap.add_argument("--k400-degree-fp32", type=int, default=60,
+                    help="k = 400 leg: FP32-phase degree (its filter streams through DRAM)")
+    ap.add_argument("--k400-degree-fp64", type=int, default=100, help="k = 400 leg: FP64-phase degree")
     ap.add_argument("--column-degree", type=int, choices=[0, 1], default=1,
                     help="mixed form: per-column-group degrees in the FP64 phase")
     ap.add_argument("--bound", choices=sorted(BOUNDS), default="gershgorin",
