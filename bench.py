@@ -550,8 +550,9 @@ def leg_batched_uneven(args, rank, dev, ctx, st):
         for sp, f, ax, ay in items:
             perm = scsf.sort(f, p0=8, ctx=ctx).cpu().tolist()
             dops = [scsf.Operator(scsf.DIV_A_GRAD, sp.n, ax=ax[i], ay=ay[i]) for i in perm]
-            chains.append((dops, scsf.Params(k=sp.k, nex=_nex_mult4(sp.k), degree=args.degree_fp64,
-                                             degree_fp32=args.degree_fp32, tol=1e-8, seed=sp.seed,
+            chains.append((dops, scsf.Params(k=sp.k, nex=_nex_mult4(sp.k),
+                                             degree=args.batched_degree_fp64,
+                                             degree_fp32=args.batched_degree_fp32, tol=1e-8, seed=sp.seed,
                                              precision=scsf.MIXED,
                                              column_degree=bool(args.column_degree),
                                              bound=BOUNDS[args.bound])))
@@ -571,7 +572,8 @@ def leg_batched_uneven(args, rank, dev, ctx, st):
         "config": {"chains": len(data), "ops_per_chain": 32, "n_range": [64, 192],
                    "k_range": [32, 256], "concurrency": args.batched_concurrency,
                    "form": "mixed, one batched call (worker threads, one stream each)",
-                   "degrees": {"fp32_phase": args.degree_fp32, "fp64_phase": args.degree_fp64}},
+                   "degrees": {"fp32_phase": args.batched_degree_fp32,
+                               "fp64_phase": args.batched_degree_fp64}},
     }
 
 
@@ -691,6 +693,9 @@ def main():
     ap.add_argument("--degree-fp64", type=int, default=100,
                     help="mixed form: FP64-phase degree (130 measured faster but let the FP32 first "
                          "Cholesky factor lose FP64 orthonormality: 1e-11)")
+    ap.add_argument("--batched-degree-fp32", type=int, default=60,
+                    help="64-chain leg: FP32-phase degree (its grids and k are smaller)")
+    ap.add_argument("--batched-degree-fp64", type=int, default=100, help="64-chain leg: FP64-phase degree")
     ap.add_argument("--k400-degree-fp32", type=int, default=60,
                     help="k = 400 leg: FP32-phase degree (its filter streams through DRAM)")
     ap.add_argument("--k400-degree-fp64", type=int, default=100, help="k = 400 leg: FP64-phase degree")

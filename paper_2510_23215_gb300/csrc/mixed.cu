@@ -991,7 +991,8 @@ cudaError_t launch_resident_variant(int v, const Stencil32& A, const float* X, i
 // Shape tuner: the first call for a (filter, n, column groups) shape on a stream that is not
 // being captured times every applicable variant once on the call's own buffers (CUDA events on
 // the caller's stream; every variant computes the same recurrence and writes only `out`),
-// keeps the fastest for the process and finishes with it; later calls run the cached choice
+// keeps the fastest (the default, the first variant that applies, unless another is 10 %
+// faster) for the process and finishes with it; later calls run the cached choice
 // (a call that finds the shape being tuned by another thread waits for the choice; under
 // stream capture an untuned shape runs the first variant that applies). The choice is per
 // process, so solves of the same shape in a process use the same kernel.
@@ -1055,7 +1056,9 @@ cudaError_t launch_resident_tuned(const Stencil32& A, const float* X, int ldx, i
             (err = cudaEventSynchronize(e1)) != cudaSuccess ||
             (err = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
           break;
-        if (ms < pick_ms) {
+        // the first variant that applies is the default; another replaces it only when 10 %
+        // faster, so that timing noise (other streams share the GPU) does not flip choices
+        if (pick < 0 ? true : (v == pick ? ms < pick_ms : ms < 0.9f * pick_ms)) {
           pick_ms = ms;
           pick = v;
         }
