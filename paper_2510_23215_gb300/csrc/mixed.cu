@@ -617,14 +617,18 @@ residual_norms_f32_kernel(Stencil32 A, const float* __restrict__ X, int ldx, int
   }
 }
 
-__global__ void colsum_reduce_kernel(const double* __restrict__ partials, int nb, int ncols,
-                                     double* __restrict__ out2) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// out2[t] = sum over the nb per-block partials, t < 2 ncols: one warp per output, the lanes
+// striding over the blocks (many loads in flight), then a fixed-order shuffle tree.
+__global__ void colsum_reduce_kernel(const double* __restrict__ partials, int nb,
+                                     int ncols, double* __restrict__ out2) {
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (t >= 2 * ncols) return;
   const int which = t / ncols, c = t - which * ncols;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partials[((size_t)b * 2 + which) * ncols + c];
-  out2[t] = s;
+  for (int b = lane; b < nb; b += 32) s += partials[((size_t)b * 2 + which) * ncols + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out2[t] = s;
 }
 
 // C = A^T B (FP32 products, FP32 per-chunk sums, FP64 final sum), 64 x 64 tiles,
@@ -844,7 +848,7 @@ cudaError_t launch_residual_norms_f32(const Stencil32& A, const float* X, int ld
   const dim3 grid(nb, (ncols + kSmallBlockWidth - 1) / kSmallBlockWidth);
   residual_norms_f32_kernel<<<grid, dim3(32, kRows32), 0, st>>>(A, X, ldx, ncols, theta, partials);
   note_launch();
-  colsum_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
+  colsum_reduce_kernel<<<(2 * ncols + 3) / 4, 128, 0, st>>>(partials, nb, ncols, out2);
   note_launch();
   return cudaGetLastError();
 }

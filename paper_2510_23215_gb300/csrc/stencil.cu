@@ -292,14 +292,18 @@ residual_norms_kernel(Stencil A, const double* __restrict__ X, int ldx, int ncol
   }
 }
 
+// out2[t] = sum over the nb per-block partials, t < 2 ncols: one warp per output, the lanes
+// striding over the blocks (many loads in flight), then a fixed-order shuffle tree.
 __global__ void column_partials_reduce_kernel(const double* __restrict__ partials, int nb,
                                               int ncols, double* __restrict__ out2) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (t >= 2 * ncols) return;
   const int which = t / ncols, c = t - which * ncols;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partials[((size_t)b * 2 + which) * ncols + c];
-  out2[t] = s;
+  for (int b = lane; b < nb; b += 32) s += partials[((size_t)b * 2 + which) * ncols + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out2[t] = s;
 }
 
 }  // namespace
@@ -367,7 +371,7 @@ cudaError_t launch_residual_norms(const Stencil& A, const double* X, int ldx, in
   residual_norms_kernel<<<grid, dim3(32, kRowsPerBlock), 0, st>>>(A, X, ldx, ncols, theta,
                                                                   partials, R32, ldr);
   note_launch();
-  column_partials_reduce_kernel<<<(2 * ncols + 127) / 128, 128, 0, st>>>(partials, nb, ncols, out2);
+  column_partials_reduce_kernel<<<(2 * ncols + 3) / 4, 128, 0, st>>>(partials, nb, ncols, out2);
   note_launch();
   return cudaGetLastError();
 }
