@@ -95,12 +95,16 @@ cudaError_t launch_gather_cols(int rows, int ncols, const double* in, int ld_in,
 cudaError_t launch_normalize_signs(int rows, int ncols, double* V, int ldv, cudaStream_t st);
 
 // ---- reduced eigensolve (eig.cu) ----------------------------------------
+// All eigenpairs of the symmetric k x k S (ascending, FP64 accuracy): probe of the diagonal
+// trailing block, FP32 tridiagonal start (Householder, multisection, inverse iteration),
+// Ogita-Aishima FP64 refinement, cluster-local FP64 Jacobi, sort.
 size_t small_eigh_scratch_bytes(int k);
 cudaError_t launch_small_eigh(int k, const double* S, int lds, double* evals, double* Z, int ldz,
                               void* scratch, cudaStream_t st);
 
-// FP32 decomposition only (FP32 Jacobi + sort), for the FP32 phase: eigenvector
-// accuracy ~1e-6 relative, enough while residuals are far above the FP64 target.
+// The FP32 phase's variant: the same start with one refinement step and no round-robin
+// fallback; eigenvector accuracy ~1e-7 relative, enough while residuals are far above the
+// FP64 target.
 cudaError_t launch_small_eigh_f32(int k, const double* S, int lds, double* evals, double* Z,
                                   int ldz, void* scratch, cudaStream_t st);
 

@@ -21,7 +21,7 @@
 // gives FP32-class products for the mixed form's FP32 phase.
 //
 // Kernel (one CTA per SM, 320 threads):
-//   warp 8   TMA producer: for every 64-row chunk, S stages of {A digit plane tile
+//   warp 8   TMA producer: for each 64-row chunk, S stages of {A digit plane tile
 //            128 x 64, B digit plane tile 32 x 64} (BF16, K-major, 128-byte swizzle)
 //            into an 11-stage shared-memory ring, completion on mbarriers;
 //   warp 9   allocates tensor memory and issues tcgen05.mma (M = 128, N = 32, K = 16)

@@ -120,6 +120,31 @@ def test_filter_dc_grouped_rejects_bad_degrees():
             scsf.cheb_filter_dc(to_dev([op], dev)[0], X, th, 4, lam, c, e, group_degrees=bad)
 
 
+@pytest.mark.parametrize("n", [128, 180])
+def test_resident_filter_variants_match_oracle(n):
+    """The cluster-resident filters at a grid where the register-strip kernel applies (128) and
+    one where a band needs more than 1024 threads, so only the shared-memory kernels apply
+    (180): both the FP32 filter and the defect-corrected one against the oracle's Alg. 1, twice
+    (the second call runs the shape tuner's cached choice)."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    op, A, lam, c, e = _filter_setup(n, n + 21)
+    ncols, degree = 8, 6
+    X = si.gaussian_block(n * n, ncols, seed=n)
+    ref = chebyshev.chebyshev_filter(A, X.astype(np.float32).astype(np.float64), degree, lam, c, e)
+    dop = to_dev([op], dev)[0]
+    for _ in range(2):
+        Y = host(scsf.cheb_filter_f32(dop, torch.as_tensor(X, dtype=torch.float32, device=dev),
+                                      degree, lam, c, e)).astype(np.float64)
+        assert np.max(np.abs(Y - ref)) <= 2e-5 * degree * np.max(np.abs(ref))
+    theta = np.random.default_rng(n).uniform(lam, 2 * c, ncols)
+    ref_dc = chebyshev.chebyshev_filter(A, X, degree, lam, c, e)
+    for _ in range(2):
+        Y = host(scsf.cheb_filter_dc(dop, torch.as_tensor(X, device=dev),
+                                     torch.as_tensor(theta, device=dev), degree, lam, c, e))
+        assert np.max(np.abs(Y - ref_dc)) <= 2e-5 * degree * np.max(np.abs(ref_dc))
+
+
 def _check(op, evals, resid, evecs, k, ref_vals, ref_vecs=None):
     A = operators.assemble(op)
     assert np.max(resid) <= RES_TOL
