@@ -105,6 +105,40 @@ def test_rotation_matches_exact_product(rows, k, n):
     assert np.max(np.abs(Y - ref)[nz] / norms[nz]) <= 1e-14
 
 
+@pytest.mark.parametrize("rows,m,n,sym", [(5000, 120, 120, True), (3001, 40, 72, False)])
+def test_four_digit_gram_is_fp32_class(rows, m, n, sym):
+    """The FP32 phase's products keep 4 base-128 digits per operand (28 bits against a
+    row or column maximum): against the exactly rounded product the error stays at the
+    FP32 level, normwise below 1e-7 of |a_i| |b_j| (Gaussian columns scaled over 1e-6..1e3);
+    a wrong digit, level or tile would show as an error of order one."""
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    A = _block(rows, m, 11, np.logspace(-6, 3, m))
+    B = A if sym else _block(rows, n, 12, np.logspace(2, -4, n))
+    C = host(scsf.block_gram(torch.as_tensor(A, device=dev),
+                             None if sym else torch.as_tensor(B, device=dev),
+                             symmetric=sym, slices=4))
+    ref = products.exact_tn(A, B)
+    norms = np.outer(np.linalg.norm(A, axis=0), np.linalg.norm(B, axis=0))
+    err = np.max(np.abs(C - ref) / norms)
+    print(f"4 digits: normwise {err:.2e}")
+    assert err <= 1e-7
+    assert err >= 1e-12  # really the short split, not the 8-digit one
+
+
+def test_four_digit_rotation_is_fp32_class():
+    dev = need_gpu()
+    import paper_2510_23215_gb300 as scsf
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((4099, 120)) * np.logspace(-3, 3, 4099)[:, None]
+    M = rng.standard_normal((120, 120))
+    Y = host(scsf.block_rotate(torch.as_tensor(X, device=dev), torch.as_tensor(M, device=dev),
+                               slices=4))
+    ref = products.exact_nn(X, M)
+    norms = np.outer(np.linalg.norm(X, axis=1), np.linalg.norm(M, axis=0))
+    assert np.max(np.abs(Y - ref) / norms) <= 1e-7
+
+
 def test_rotation_alpha_beta_update():
     """Y <- Y - V C (deflation against locked columns)."""
     dev = need_gpu()
