@@ -690,9 +690,9 @@ def main():
     ap.add_argument("--no-paper-form", action="store_true",
                     help="skip the paper's form (degree 20, one sequential chain)")
     ap.add_argument("--degree-fp32", type=int, default=80, help="mixed form: FP32-phase degree")
-    ap.add_argument("--degree-fp64", type=int, default=100,
+    ap.add_argument("--degree-fp64", type=int, default=110,
                     help="mixed form: FP64-phase degree (130 measured faster but let the FP32 first "
-                         "Cholesky factor lose FP64 orthonormality: 1e-11)")
+                         "Cholesky factor lose FP64 orthonormality: 1e-11; 110 keeps 2e-15)")
     ap.add_argument("--batched-degree-fp32", type=int, default=60,
                     help="64-chain leg: FP32-phase degree (its grids and k are smaller)")
     ap.add_argument("--batched-degree-fp64", type=int, default=100, help="64-chain leg: FP64-phase degree")
